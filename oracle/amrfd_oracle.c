@@ -1,0 +1,390 @@
+/*
+ * amrfd_oracle.c -- plain CPU FP64 oracle of the conservative finite-difference
+ * update of Porth et al., "MPI-AMRVAC for solar and astrophysics" (ApJS 2014).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by tests/, the bench's CPU-baseline leg and
+ * the smoke check to decide what the right answer is. It is slow on purpose:
+ * single-threaded, separate arrays, ghost cells filled explicitly, every stage
+ * and every L(U^(k)) stored, no blocking or fusion. Built with
+ * -O2 -ffp-contract=off so that each expression is evaluated exactly as written.
+ *
+ * What each function follows:
+ *   conservation law and the point-wise FD flux difference ....... Sec. 2.1
+ *   time operator L(U) = -sum_j dF_j/dx_j (no sources here) ...... Sec. 2.1
+ *   global Lax-Friedrichs splitting F^{+-} = (F +- c_max U)/2 .... Sec. 2.2
+ *   interface flux = R_L(F^+) + R_R(F^-) ......................... Sec. 2.2
+ *   MP5 reconstruction R ...... Suresh & Huynh (1997), cited in Sec. 2.2
+ *   s-stage SSPRK in Shu-Osher form .............................. Sec. 2.3
+ *   SSPRK(5,4) coefficient table (printed, used verbatim) ........ Sec. 2.3
+ *   RK3 of Gottlieb & Shu (1998), cited in Sec. 2.3 (Shu-Osher SSPRK3)
+ *   ideal-gas total energy E = p/(gamma-1) + rho v^2/2 + B^2/2 ... Sec. 3, 4.3
+ *   ideal MHD fluxes (B_0 = 0, eta = eta_h = 0) .................. Sec. 4.1, 4.3
+ *   GLM "glm3" (psi flux terms, no div B sources), psi damping ... Sec. 4.2
+ *   fast magnetosonic speed in the time-step criterion ........... Sec. 4.4
+ *   active / passive blocks: only active blocks advance ........... App. C
+ *
+ * Readings where the paper is silent (every one is restated in the design
+ * notes): MP5 constants alpha = 4, eps = 1e-10; c_max is per direction, per
+ * RK stage, over the domain's active interior cells; GLM speed c_h = max_d of
+ * those speeds on U^n, frozen for the step, and c_max_d >= c_h; psi is damped
+ * after the step by exp(-dt c_h / c_r); the multi-D CFL step uses
+ * dt = CFL / max_cells sum_d max(c_d, c_h)/dx_d; outflow = zero-gradient copy;
+ * non-physical states are flagged, never clamped, and excluded from the speeds.
+ */
+#include "amrfd_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NG 3 /* ghost width needed by the 5-point MP5 stencil on both biases */
+
+/* ---- variable indexing -------------------------------------------------- */
+enum { W_RHO = 0, W_VX = 1, W_P = 4, W_BX = 5, W_PSI = 8, NW = 9 };
+enum { M_E = 4, M_BX = 5, M_PSI = 8 };
+
+int orc_nvar(const orc_cfg *c) { return c->physics == ORC_EULER ? 2 + c->ndim : 9; }
+
+static int e_index(const orc_cfg *c) { return c->physics == ORC_EULER ? 1 + c->ndim : M_E; }
+static int n_mom(const orc_cfg *c) { return c->physics == ORC_EULER ? c->ndim : 3; }
+
+/* ---- conserved -> primitive (E = p/(gamma-1) + rho v^2/2 + B^2/2) ------- */
+int orc_cons2prim(const orc_cfg *c, const double *u, double *w) {
+  int nm = n_mom(c), ie = e_index(c), k;
+  double rho = u[0], ekin, emag = 0.0, p;
+  w[W_RHO] = rho;
+  for (k = 0; k < 3; k++) w[W_VX + k] = (k < nm) ? u[1 + k] / rho : 0.0;
+  ekin = 0.5 * rho * (w[1] * w[1] + w[2] * w[2] + w[3] * w[3]);
+  if (c->physics == ORC_MHD_GLM) {
+    for (k = 0; k < 3; k++) w[W_BX + k] = u[M_BX + k];
+    w[W_PSI] = u[M_PSI];
+    emag = 0.5 * (w[5] * w[5] + w[6] * w[6] + w[7] * w[7]);
+  } else {
+    for (k = 0; k < 3; k++) w[W_BX + k] = 0.0;
+    w[W_PSI] = 0.0;
+  }
+  p = (c->gamma - 1.0) * (u[ie] - ekin - emag);
+  w[W_P] = p;
+  return (rho > 0.0) && (p > 0.0) && isfinite(rho) && isfinite(p) && isfinite(w[W_PSI]);
+}
+
+/* ---- maximal characteristic speed along d: |v_d| + c_s or |v_d| + c_f --- */
+double orc_char_speed(const orc_cfg *c, const double *w, int d) {
+  double rho = w[W_RHO], p = w[W_P];
+  if (c->physics == ORC_EULER) return fabs(w[W_VX + d]) + sqrt(c->gamma * p / rho);
+  {
+    double bx = w[5], by = w[6], bz = w[7], bd = w[W_BX + d];
+    double a2 = c->gamma * p / rho;                 /* sound speed squared */
+    double b2 = (bx * bx + by * by + bz * bz) / rho; /* Alfven speed squared */
+    double s = a2 + b2;
+    double disc = s * s - 4.0 * a2 * (bd * bd) / rho;
+    double cf;
+    if (disc < 0.0) disc = 0.0; /* (a^2 - b_d^2)^2 >= 0; guards rounding only */
+    cf = sqrt(0.5 * (s + sqrt(disc)));
+    return fabs(w[W_VX + d]) + cf;
+  }
+}
+
+/* ---- physical flux along d ---------------------------------------------- */
+void orc_flux(const orc_cfg *c, const double *u, const double *w, int d, double ch, double *f) {
+  int k;
+  double vd = w[W_VX + d], p = w[W_P];
+  if (c->physics == ORC_EULER) {
+    int nm = c->ndim, ie = 1 + c->ndim;
+    f[0] = u[1 + d];
+    for (k = 0; k < nm; k++) f[1 + k] = vd * u[1 + k] + (k == d ? p : 0.0);
+    f[ie] = vd * (u[ie] + p);
+    return;
+  }
+  {
+    double bx = w[5], by = w[6], bz = w[7], bd = w[W_BX + d], psi = w[W_PSI];
+    double B[3] = {bx, by, bz};
+    double b2 = bx * bx + by * by + bz * bz;
+    double ptot = p + 0.5 * b2;
+    double vb = w[1] * bx + w[2] * by + w[3] * bz;
+    f[0] = u[1 + d];
+    for (k = 0; k < 3; k++) f[1 + k] = vd * u[1 + k] - bd * B[k] + (k == d ? ptot : 0.0);
+    f[M_E] = vd * (u[M_E] + ptot) - bd * vb;
+    for (k = 0; k < 3; k++) f[M_BX + k] = vd * B[k] - bd * w[W_VX + k] + (k == d ? psi : 0.0);
+    f[M_PSI] = ch * ch * bd;
+  }
+}
+
+/* ---- MP5 (Suresh & Huynh 1997) ------------------------------------------ */
+static double sgn(double a) { return (a > 0.0) ? 1.0 : ((a < 0.0) ? -1.0 : 0.0); }
+
+double orc_minmod(double a, double b) {
+  return 0.5 * (sgn(a) + sgn(b)) * fmin(fabs(a), fabs(b));
+}
+
+double orc_minmod4(double w, double x, double y, double z) {
+  double s = 0.125 * (sgn(w) + sgn(x)) * fabs((sgn(w) + sgn(y)) * (sgn(w) + sgn(z)));
+  return s * fmin(fmin(fabs(w), fabs(x)), fmin(fabs(y), fabs(z)));
+}
+
+static double min3(double a, double b, double c) { return fmin(a, fmin(b, c)); }
+static double max3(double a, double b, double c) { return fmax(a, fmax(b, c)); }
+
+/* Left-biased value at the face i+1/2 from (f_{i-2}, f_{i-1}, f_i, f_{i+1}, f_{i+2}).
+   The right-biased value at i+1/2 is orc_mp5(f_{i+3}, f_{i+2}, f_{i+1}, f_i, f_{i-1}). */
+double orc_mp5(double fm2, double fm1, double f0, double fp1, double fp2) {
+  const double alpha = 4.0, eps = 1e-10;
+  double f_or = (2.0 * fm2 - 13.0 * fm1 + 47.0 * f0 + 27.0 * fp1 - 3.0 * fp2) / 60.0;
+  double f_mp = f0 + orc_minmod(fp1 - f0, alpha * (f0 - fm1));
+  double d_m1, d_0, d_p1, dm4_p, dm4_m, f_ul, f_av, f_md, f_lc, f_min, f_max;
+  if ((f_or - f0) * (f_or - f_mp) <= eps) return f_or;
+  d_m1 = fm2 - 2.0 * fm1 + f0; /* curvature at i-1 */
+  d_0 = fm1 - 2.0 * f0 + fp1;  /* curvature at i */
+  d_p1 = f0 - 2.0 * fp1 + fp2; /* curvature at i+1 */
+  dm4_p = orc_minmod4(4.0 * d_0 - d_p1, 4.0 * d_p1 - d_0, d_0, d_p1); /* at i+1/2 */
+  dm4_m = orc_minmod4(4.0 * d_0 - d_m1, 4.0 * d_m1 - d_0, d_0, d_m1); /* at i-1/2 */
+  f_ul = f0 + alpha * (f0 - fm1);
+  f_av = 0.5 * (f0 + fp1);
+  f_md = f_av - 0.5 * dm4_p;
+  f_lc = f0 + 0.5 * (f0 - fm1) + 4.0 / 3.0 * dm4_m;
+  f_min = fmax(min3(f0, fp1, f_md), min3(f0, f_ul, f_lc));
+  f_max = fmin(max3(f0, fp1, f_md), max3(f0, f_ul, f_lc));
+  return f_or + orc_minmod(f_min - f_or, f_max - f_or); /* median(f_or, f_min, f_max) */
+}
+
+/* ---- SSPRK tables (Sec. 2.3) -------------------------------------------- */
+int orc_ssprk_table(int integrator, double a[5][5], double b[5][5]) {
+  memset(a, 0, sizeof(double) * 25);
+  memset(b, 0, sizeof(double) * 25);
+  if (integrator == ORC_SSPRK3) {
+    /* Gottlieb & Shu (1998) third-order TVD RK, Shu-Osher form */
+    a[0][0] = 1.0;                    b[0][0] = 1.0;
+    a[1][0] = 0.75; a[1][1] = 0.25;   b[1][1] = 0.25;
+    a[2][0] = 1.0 / 3.0; a[2][2] = 2.0 / 3.0; b[2][2] = 2.0 / 3.0;
+    return 3;
+  }
+  /* SSPRK(5,4), the table printed in Sec. 2.3, digits as printed */
+  a[0][0] = 1.0;
+  a[1][0] = 0.44437049406734; a[1][1] = 0.55562950593266;
+  a[2][0] = 0.62010185138540; a[2][2] = 0.37989814861460;
+  a[3][0] = 0.17807995410773; a[3][3] = 0.82192004589227;
+  a[4][0] = 0.00683325884039; a[4][2] = 0.51723167208978;
+  a[4][3] = 0.12759831133288; a[4][4] = 0.34833675773694;
+  b[0][0] = 0.39175222700392;
+  b[1][1] = 0.36841059262959;
+  b[2][2] = 0.25189177424738;
+  b[3][3] = 0.54497475021237;
+  b[4][3] = 0.08460416338212; b[4][4] = 0.22600748319395;
+  return 5;
+}
+
+/* ---- geometry helpers --------------------------------------------------- */
+static long ncells(const orc_dom *dm) { return (long)dm->n[0] * dm->n[1] * dm->n[2]; }
+
+/* per-cell active mask from per-block flags (blocks tile the domain) */
+static uint8_t *cell_mask(const orc_dom *dm, const uint8_t *block_active) {
+  long N = ncells(dm), idx = 0;
+  int be[3], x, y, z, d;
+  uint8_t *m = (uint8_t *)malloc((size_t)N);
+  for (d = 0; d < 3; d++) be[d] = dm->n[d] / (dm->nb[d] > 0 ? dm->nb[d] : 1);
+  for (z = 0; z < dm->n[2]; z++)
+    for (y = 0; y < dm->n[1]; y++)
+      for (x = 0; x < dm->n[0]; x++, idx++) {
+        long b = ((long)(z / be[2]) * dm->nb[1] + y / be[1]) * dm->nb[0] + x / be[0];
+        m[idx] = block_active ? (block_active[b] != 0) : 1;
+      }
+  return m;
+}
+
+static void gather(const double *U, long N, int nv, long idx, double *u) {
+  int v;
+  for (v = 0; v < nv; v++) u[v] = U[(long)v * N + idx];
+}
+
+/* ---- per-direction maximal speeds (Sec. 2.2: grid-global c_max) --------- */
+int orc_speeds(const orc_cfg *c, const orc_dom *dm, const double *U, const uint8_t *block_active,
+               double alpha_raw[3], double *rate_max) {
+  long N = ncells(dm), i;
+  int nv = orc_nvar(c), d, flags = 0;
+  double u[NW], w[NW];
+  uint8_t *m = cell_mask(dm, block_active);
+  alpha_raw[0] = alpha_raw[1] = alpha_raw[2] = 0.0;
+  *rate_max = 0.0;
+  for (i = 0; i < N; i++) {
+    double rate = 0.0;
+    if (!m[i]) continue;
+    gather(U, N, nv, i, u);
+    if (!orc_cons2prim(c, u, w)) { flags |= ORC_FLAG_NONPHYSICAL; continue; }
+    for (d = 0; d < c->ndim; d++) {
+      double cd = orc_char_speed(c, w, d);
+      if (cd > alpha_raw[d]) alpha_raw[d] = cd;
+      rate = rate + cd / dm->dx[d];
+    }
+    if (rate > *rate_max) *rate_max = rate;
+  }
+  free(m);
+  return flags;
+}
+
+/* ---- L(U): unsplit sum over directions of the FD flux difference -------- */
+int orc_residual(const orc_cfg *c, const orc_dom *dm, const double *U, const double alpha[3],
+                 double ch, double *L) {
+  const int nv = orc_nvar(c), nd = c->ndim;
+  long N = ncells(dm), NE, i;
+  int ne[3], d, v, flags = 0;
+  double *E;
+  for (d = 0; d < 3; d++) ne[d] = dm->n[d] + (d < nd ? 2 * NG : 0);
+  NE = (long)ne[0] * ne[1] * ne[2];
+  E = (double *)calloc((size_t)NE * nv, sizeof(double));
+  for (i = 0; i < N * nv; i++) L[i] = 0.0;
+
+  /* interior copy */
+  {
+    int x, y, z, o[3];
+    for (d = 0; d < 3; d++) o[d] = d < nd ? NG : 0;
+    for (v = 0; v < nv; v++)
+      for (z = 0; z < dm->n[2]; z++)
+        for (y = 0; y < dm->n[1]; y++)
+          for (x = 0; x < dm->n[0]; x++)
+            E[(long)v * NE + ((long)(z + o[2]) * ne[1] + (y + o[1])) * ne[0] + (x + o[0])] =
+                U[(long)v * N + ((long)z * dm->n[1] + y) * dm->n[0] + x];
+  }
+  /* ghost cells, one direction at a time: periodic wrap or zero-gradient copy */
+  for (d = 0; d < nd; d++) {
+    int x[3], g, n = dm->n[d];
+    for (x[2] = 0; x[2] < ne[2]; x[2]++)
+      for (x[1] = 0; x[1] < ne[1]; x[1]++)
+        for (x[0] = 0; x[0] < ne[0]; x[0]++) {
+          int src[3] = {x[0], x[1], x[2]}, phys;
+          g = x[d] - NG; /* physical index along d */
+          if (g >= 0 && g < n) continue;
+          if (g < 0) phys = dm->bc[d][0] == ORC_BC_PERIODIC ? g + n : 0;
+          else phys = dm->bc[d][1] == ORC_BC_PERIODIC ? g - n : n - 1;
+          src[d] = phys + NG;
+          for (v = 0; v < nv; v++)
+            E[(long)v * NE + ((long)x[2] * ne[1] + x[1]) * ne[0] + x[0]] =
+                E[(long)v * NE + ((long)src[2] * ne[1] + src[1]) * ne[0] + src[0]];
+        }
+  }
+
+  for (d = 0; d < nd; d++) {
+    const int n = dm->n[d], m = n + 2 * NG;
+    long stride[3] = {1, ne[0], (long)ne[0] * ne[1]};
+    int od[2], q = 0, k, j, a1, a2;
+    double *Fp = (double *)malloc(sizeof(double) * nv * m);
+    double *Fm = (double *)malloc(sizeof(double) * nv * m);
+    double *Fh = (double *)malloc(sizeof(double) * nv * (n + 1));
+    for (k = 0; k < 3; k++)
+      if (k != d) od[q++] = k;
+    for (a2 = 0; a2 < dm->n[od[1]]; a2++)
+      for (a1 = 0; a1 < dm->n[od[0]]; a1++) {
+        int pos[3];
+        long base;
+        pos[od[0]] = a1 + (od[0] < nd ? NG : 0);
+        pos[od[1]] = a2 + (od[1] < nd ? NG : 0);
+        pos[d] = 0;
+        base = ((long)pos[2] * ne[1] + pos[1]) * ne[0] + pos[0];
+        /* split fluxes F^{+-} = (F +- alpha_d U)/2 along the whole line */
+        for (j = 0; j < m; j++) {
+          double u[NW], w[NW], f[NW];
+          gather(E, NE, nv, base + j * stride[d], u);
+          if (!orc_cons2prim(c, u, w) && j >= NG && j < NG + n) flags |= ORC_FLAG_NONPHYSICAL;
+          orc_flux(c, u, w, d, ch, f);
+          for (v = 0; v < nv; v++) {
+            Fp[v * m + j] = 0.5 * (f[v] + alpha[d] * u[v]);
+            Fm[v * m + j] = 0.5 * (f[v] - alpha[d] * u[v]);
+          }
+        }
+        /* interface fluxes at faces k = 0..n (face k sits between cells k-1 and k) */
+        for (v = 0; v < nv; v++) {
+          const double *P = Fp + v * m, *M = Fm + v * m;
+          for (k = 0; k <= n; k++) {
+            int ii = k - 1 + NG; /* extended index of the cell left of the face */
+            double left = orc_mp5(P[ii - 2], P[ii - 1], P[ii], P[ii + 1], P[ii + 2]);
+            double right = orc_mp5(M[ii + 3], M[ii + 2], M[ii + 1], M[ii], M[ii - 1]);
+            Fh[v * (n + 1) + k] = left + right;
+          }
+        }
+        /* flux difference into L */
+        for (k = 0; k < n; k++) {
+          int ip[3];
+          long idx;
+          ip[od[0]] = a1;
+          ip[od[1]] = a2;
+          ip[d] = k;
+          idx = ((long)ip[2] * dm->n[1] + ip[1]) * dm->n[0] + ip[0];
+          for (v = 0; v < nv; v++)
+            L[(long)v * N + idx] -= (Fh[v * (n + 1) + k + 1] - Fh[v * (n + 1) + k]) / dm->dx[d];
+        }
+      }
+    free(Fp);
+    free(Fm);
+    free(Fh);
+  }
+  free(E);
+  return flags;
+}
+
+/* ---- one SSPRK step (Sec. 2.3), passive blocks held fixed (App. C) ------- */
+int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
+             double *alpha_stage, double *ch_out) {
+  double a[5][5], b[5][5], araw[3], rate, ch = 0.0, alpha[3];
+  const int nv = orc_nvar(c), s = orc_ssprk_table(c->integrator, a, b);
+  long N = ncells(dm), tot = N * nv, j;
+  int i, k, d, flags = 0;
+  double *Ust[6], *Lst[5];
+  uint8_t *m = cell_mask(dm, block_active);
+  for (i = 0; i <= s; i++) Ust[i] = (double *)malloc(sizeof(double) * tot);
+  for (i = 0; i < s; i++) Lst[i] = (double *)malloc(sizeof(double) * tot);
+  memcpy(Ust[0], U, sizeof(double) * tot);
+
+  flags |= orc_speeds(c, dm, Ust[0], block_active, araw, &rate);
+  if (c->physics == ORC_MHD_GLM)
+    for (d = 0; d < c->ndim; d++) ch = fmax(ch, araw[d]);
+  for (d = 0; d < 3; d++) alpha[d] = fmax(araw[d], ch);
+
+  for (i = 1; i <= s; i++) {
+    if (alpha_stage)
+      for (d = 0; d < 3; d++) alpha_stage[(i - 1) * 3 + d] = alpha[d];
+    flags |= orc_residual(c, dm, Ust[i - 1], alpha, ch, Lst[i - 1]);
+    for (j = 0; j < tot; j++) {
+      long cell = j % N;
+      double acc = 0.0;
+      if (!m[cell]) { Ust[i][j] = U[j]; continue; }
+      for (k = 0; k < i; k++) {
+        if (a[i - 1][k] != 0.0) acc = acc + a[i - 1][k] * Ust[k][j];
+        if (b[i - 1][k] != 0.0) acc = acc + dt * b[i - 1][k] * Lst[k][j];
+      }
+      Ust[i][j] = acc;
+    }
+    if (i < s) {
+      flags |= orc_speeds(c, dm, Ust[i], block_active, araw, &rate);
+      for (d = 0; d < 3; d++) alpha[d] = fmax(araw[d], ch);
+    }
+  }
+  memcpy(U, Ust[s], sizeof(double) * tot);
+  /* GLM source -(c_h^2/c_p^2) psi, integrated exactly and operator-split,
+     with c_p^2/c_h = c_r fixed (Sec. 4.2) */
+  if (c->physics == ORC_MHD_GLM && c->glm_cr > 0.0) {
+    double fac = exp(-dt * ch / c->glm_cr);
+    for (j = 0; j < N; j++)
+      if (m[j]) U[(long)M_PSI * N + j] *= fac;
+  }
+  if (ch_out) *ch_out = ch;
+  for (i = 0; i <= s; i++) free(Ust[i]);
+  for (i = 0; i < s; i++) free(Lst[i]);
+  free(m);
+  return flags;
+}
+
+/* ---- CFL time step (Sec. 4.4: dt < dx / c_w; unsplit multi-D sum) ------- */
+int orc_dt(const orc_cfg *c, const orc_dom *dm, const double *U, const uint8_t *block_active,
+           double cfl, double t, double t_end, double *dt_out) {
+  double araw[3], rate, dt;
+  int d, flags = orc_speeds(c, dm, U, block_active, araw, &rate);
+  if (c->physics == ORC_MHD_GLM) {
+    /* every direction carries the GLM waves at c_h >= c_d, so the cell sum is sum_d c_h/dx_d */
+    double ch = 0.0;
+    for (d = 0; d < c->ndim; d++) ch = fmax(ch, araw[d]);
+    rate = 0.0;
+    for (d = 0; d < c->ndim; d++) rate = rate + ch / dm->dx[d];
+  }
+  dt = rate > 0.0 ? cfl / rate : INFINITY;
+  *dt_out = fmin(dt, t_end - t);
+  return flags;
+}
