@@ -1,0 +1,150 @@
+/*
+ * amrfd.h -- C ABI of the GB300 FP64 conservative finite-difference update of
+ * Porth et al., "MPI-AMRVAC for solar and astrophysics" (ApJS 2014).
+ *
+ * One call advances the conserved state of many domains by one strong-stability-
+ * preserving Runge-Kutta step of the paper's FD scheme:
+ *   conserved -> primitive, maximal characteristic speed per cell, global
+ *   Lax-Friedrichs flux splitting F^{+-} = (F +- c_max U)/2 (Sec. 2.2), MP5
+ *   reconstruction of the split fluxes at faces (Suresh & Huynh 1997, cited in
+ *   Sec. 2.2), the flux difference L(U) = -sum_j dF_j/dx_j (Sec. 2.1), the
+ *   Shu-Osher stage combination of SSPRK3 or SSPRK(5,4) (Sec. 2.3), GLM psi
+ *   damping (Sec. 4.2), and the CFL time step (Sec. 4.4).
+ *
+ * Conventions for every entry point:
+ *  - All state, time-step and gradient arrays are DEVICE pointers owned by the
+ *    caller (e.g. torch tensors). FP64 only.
+ *  - State layout: the caller's buffer holds every domain at its `offset`
+ *    (elements), each domain as U[v][z][y][x], x fastest, interior cells only
+ *    (no ghost cells; halos are synthesised from the boundary kinds).
+ *      Euler   (nv = 2 + ndim): rho, m_1..m_ndim, E
+ *      MHD+GLM (nv = 9):        rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi
+ *    E = p/(gamma-1) + rho v^2/2 + B^2/2 (Sec. 3, Sec. 4.3); units with no
+ *    4 pi or mu_0 (B^2/2 is the magnetic pressure).
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) and does not synchronise, except where stated.
+ *  - Return value: AMRFD_OK or an AMRFD_ERR_* code (see amrfd_strerror).
+ *    Argument errors are detected on the host before anything is launched.
+ *    Conditions found on the device (non-physical states) are latched in the
+ *    handle and read with amrfd_get_error.
+ *  - A handle is not thread-safe; calls on one handle must be serialised.
+ */
+#ifndef AMRFD_H
+#define AMRFD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* physics, integrator, boundary and time-step scope selectors */
+#define AMRFD_EULER 0
+#define AMRFD_MHD_GLM 1
+#define AMRFD_SSPRK3 0
+#define AMRFD_SSPRK54 1
+#define AMRFD_BC_PERIODIC 0
+#define AMRFD_BC_OUTFLOW 1
+#define AMRFD_DT_PER_DOMAIN 0
+#define AMRFD_DT_GLOBAL 1
+
+/* return codes */
+#define AMRFD_OK 0
+#define AMRFD_ERR_INVALID_ARG 1
+#define AMRFD_ERR_CUDA 2
+#define AMRFD_ERR_UNSUPPORTED 3
+#define AMRFD_ERR_NONPHYSICAL 4 /* device found rho <= 0, p <= 0 or a non-finite value */
+
+typedef struct amrfd_config {
+  int physics;    /* AMRFD_EULER | AMRFD_MHD_GLM */
+  int ndim;       /* 1, 2 or 3 */
+  int integrator; /* AMRFD_SSPRK3 (Gottlieb-Shu RK3, Sec. 2.3) | AMRFD_SSPRK54 (printed table, Sec. 2.3) */
+  int dt_scope;   /* AMRFD_DT_PER_DOMAIN | AMRFD_DT_GLOBAL (min over domains) */
+  double gamma;   /* ratio of specific heats, > 1 */
+  double cfl;     /* Courant number used by amrfd_dt */
+  double glm_cr;  /* MHD: psi damping length c_r = c_p^2/c_h (Sec. 4.2); <= 0 disables damping */
+} amrfd_config;
+
+typedef struct amrfd_domain {
+  int n[3];        /* interior cells per dimension; 1 for dimensions >= ndim */
+  int nb[3];       /* blocks per dimension (n[d] % nb[d] == 0); a block is the unit of activity */
+  double dx[3];    /* cell size per dimension (> 0) */
+  int bc[3][2];    /* AMRFD_BC_* of the low and high face of each dimension; periodic must pair */
+  int64_t offset;  /* element offset of U[0][0][0][0] of this domain in the state buffer */
+} amrfd_domain;
+
+typedef struct amrfd_handle amrfd_handle;
+
+/* Create a handle for `ndomain` domains (copied). `active_host` has one flag per
+   block, blocks numbered domain by domain and, inside a domain, x-fastest; NULL
+   means all active (App. C: only active blocks are advanced). Allocates the
+   workspace (stage states, per-direction residuals, speeds, work lists) with
+   cudaMalloc on the current device. Constraints: n[d] >= 3 along periodic
+   dimensions, n[d] >= 1 otherwise; domains must not overlap. Returns
+   AMRFD_ERR_INVALID_ARG on bad arguments, AMRFD_ERR_CUDA on allocation failure. */
+int amrfd_create(amrfd_handle **h, const amrfd_config *cfg, const amrfd_domain *domains, int ndomain,
+                 const uint8_t *active_host, void *stream);
+
+/* Replace the per-block active flags from DEVICE memory (uint8, one per block)
+   and rebuild the device work lists of active blocks. Synchronises `stream`
+   once to keep a host copy for the per-domain path. */
+int amrfd_set_active(amrfd_handle *h, const uint8_t *active_dev, void *stream);
+
+/* CFL time step per domain (Sec. 4.4, unsplit multi-D form):
+   dt = cfl / max over active cells of sum_d c_d/dx_d, where c_d = |v_d| + fast
+   (MHD) or sound (Euler) speed and, with GLM, every c_d is raised to the GLM
+   speed c_h = max_d max_cells c_d; then dt = min(dt, t_end - t). With
+   AMRFD_DT_GLOBAL every entry receives the minimum over domains. Writes
+   dt_dev[ndomain] (device). Domains with no active block get t_end - t. */
+int amrfd_dt(amrfd_handle *h, const double *U, double *dt_dev, double t, double t_end, void *stream);
+
+/* One SSPRK step of every active block, in place, with per-domain time steps
+   dt_dev[ndomain] (device). Plain path: one launch per domain for each pass
+   (flux pass and stage combination of every RK stage). Passive blocks are
+   neither read as interior nor written; active blocks read their passive
+   neighbours' U^n as halo. */
+int amrfd_step(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
+
+/* Same update as amrfd_step, bitwise identical, issued as one persistent launch
+   per pass over a device-side work list of active (block, tile) items sorted
+   largest first; the whole step is replayed from a CUDA graph captured on the
+   first call for a given (U, dt_dev) pair. */
+int amrfd_step_batched(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
+
+/* Discrete adjoint of one amrfd_step with the same U^n and dt: given
+   gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
+   Splitting speeds c_max, c_h and the psi damping factor are held fixed at
+   the values the forward step used; MP5 limiter branches are replayed from
+   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED where not built. */
+int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,
+                  double *gU_n, void *stream);
+
+/* Choose the flux-pass tile (segment length along the sweep, lines per tile,
+   threads per block) by timing the candidates on this handle's work, using U
+   and dt_dev as the sample state (U is restored). Synchronises `stream`. */
+int amrfd_autotune(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
+
+/* Set the flux-pass tile explicitly: seg = max cells per sweep segment
+   (8..64), lines = lines per tile (1..32), threads per block (multiple of 32). */
+int amrfd_set_tile(amrfd_handle *h, int seg, int lines, int threads);
+/* Read back the current tile. */
+int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);
+
+/* Per-stage splitting speeds of the last step, raw (before raising to c_h):
+   out[stage][domain][3], host memory, `nstage` = stages to copy. Synchronises. */
+int amrfd_get_alpha(amrfd_handle *h, double *out, int nstage, void *stream);
+
+/* Synchronise `stream`, return the latched device condition (AMRFD_OK or
+   AMRFD_ERR_NONPHYSICAL) and clear it. */
+int amrfd_get_error(amrfd_handle *h, void *stream);
+
+/* Free the handle and its workspace (synchronises the device first). */
+void amrfd_destroy(amrfd_handle *h);
+
+/* Static description of a return code. */
+const char *amrfd_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,207 @@
+"""Python binding of libamrfd.so (argument marshalling only).
+
+Every step of the update runs in the CUDA kernels behind include/amrfd.h; this
+module converts torch CUDA tensors to device pointers and the current torch
+stream to a cudaStream_t. There is no CPU fallback: if the library is missing
+or no GPU is present, calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamrfd.so")
+
+EULER, MHD_GLM = 0, 1
+SSPRK3, SSPRK54 = 0, 1
+PERIODIC, OUTFLOW = 0, 1
+DT_PER_DOMAIN, DT_GLOBAL = 0, 1
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
+
+EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
+           "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
+           "amrfd_get_error", "amrfd_destroy", "amrfd_strerror")
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("physics", ctypes.c_int), ("ndim", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("dt_scope", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("glm_cr", ctypes.c_double)]
+
+
+class DomainC(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int * 3), ("nb", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
+                ("bc", (ctypes.c_int * 2) * 3), ("offset", ctypes.c_int64)]
+
+
+class AmrfdError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s: %s (code %d)" % (what, _strerror(code), code))
+
+
+_lib = None
+
+
+def load():
+    """Load libamrfd.so (built by paper_1407_2052_gb300.build); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libamrfd.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, dp, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
+    L.amrfd_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), ctypes.POINTER(DomainC), i, vp, vp]
+    L.amrfd_set_active.argtypes = [vp, vp, vp]
+    L.amrfd_dt.argtypes = [vp, vp, vp, dp, dp, vp]
+    L.amrfd_step.argtypes = [vp, vp, vp, vp]
+    L.amrfd_step_batched.argtypes = [vp, vp, vp, vp]
+    L.amrfd_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.amrfd_autotune.argtypes = [vp, vp, vp, vp]
+    L.amrfd_set_tile.argtypes = [vp, i, i, i]
+    L.amrfd_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+    L.amrfd_get_alpha.argtypes = [vp, vp, i, vp]
+    L.amrfd_get_error.argtypes = [vp, vp]
+    L.amrfd_destroy.argtypes = [vp]
+    L.amrfd_destroy.restype = None
+    L.amrfd_strerror.argtypes = [i]
+    L.amrfd_strerror.restype = ctypes.c_char_p
+    for name in EXPORTS:
+        if name not in ("amrfd_destroy", "amrfd_strerror"):
+            getattr(L, name).restype = i
+    _lib = L
+    return L
+
+
+def _strerror(code):
+    try:
+        return load().amrfd_strerror(code).decode()
+    except Exception:  # pragma: no cover - library missing
+        return "error"
+
+
+def _check(rc, what):
+    if rc != OK:
+        raise AmrfdError(rc, what)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def domains_c(domains):
+    arr = (DomainC * len(domains))()
+    for i, d in enumerate(domains):
+        for k in range(3):
+            arr[i].n[k] = int(d.n[k])
+            arr[i].nb[k] = int(d.nb[k])
+            arr[i].dx[k] = float(d.dx[k])
+            arr[i].bc[k][0] = int(d.bc[k][0])
+            arr[i].bc[k][1] = int(d.bc[k][1])
+        arr[i].offset = int(d.offset)
+    return arr
+
+
+class Solver:
+    """One amrfd handle: a set of domains advanced together on the current GPU."""
+
+    def __init__(self, physics, ndim, integrator, gamma, cfl, domains, active=None, glm_cr=0.18,
+                 dt_scope=DT_PER_DOMAIN, stream=None):
+        L = load()
+        self.cfg = Config(physics, ndim, integrator, dt_scope, gamma, cfl, glm_cr)
+        self.domains = list(domains)
+        self.ndom = len(self.domains)
+        self.nv = 2 + ndim if physics == EULER else 9
+        self.nstages = 3 if integrator == SSPRK3 else 5
+        self.nblocks = sum(int(d.nb[0]) * int(d.nb[1]) * int(d.nb[2]) for d in self.domains)
+        self.nelem = max(int(d.offset) + self.nv * int(d.n[0]) * int(d.n[1]) * int(d.n[2]) for d in self.domains)
+        doms = domains_c(self.domains)
+        act = None
+        if active is not None:
+            a = np.ascontiguousarray(active, dtype=np.uint8).ravel()
+            if a.size != self.nblocks:
+                raise ValueError("one active flag per block")
+            self._active_host = a
+            act = a.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        _check(L.amrfd_create(ctypes.byref(h), ctypes.byref(self.cfg), doms, self.ndom, act, _stream(stream)),
+               "amrfd_create")
+        self._h = h
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        return cls(w.physics, w.ndim, w.integrator, w.gamma, w.cfl, w.domains, active=w.active,
+                   glm_cr=w.glm_cr, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().amrfd_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_active(self, active_dev, stream=None):
+        import torch
+        if active_dev.dtype != torch.uint8 or not active_dev.is_cuda or active_dev.numel() != self.nblocks:
+            raise TypeError("expected a CUDA uint8 tensor with one flag per block")
+        _check(load().amrfd_set_active(self._h, ctypes.c_void_p(active_dev.data_ptr()), _stream(stream)),
+               "amrfd_set_active")
+
+    def dt(self, U, t=0.0, t_end=float("inf"), out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self.ndom, dtype=torch.float64, device=U.device)
+        _check(load().amrfd_dt(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)), "amrfd_dt")
+        return out
+
+    def step(self, U, dt, stream=None):
+        _check(load().amrfd_step(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step")
+        return U
+
+    def step_batched(self, U, dt, stream=None):
+        _check(load().amrfd_step_batched(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step_batched")
+        return U
+
+    def adjoint(self, U_n, dt, gU_np1, gU_n, stream=None):
+        _check(load().amrfd_adjoint(self._h, _ptr(U_n), _ptr(dt), _ptr(gU_np1), _ptr(gU_n), _stream(stream)),
+               "amrfd_adjoint")
+        return gU_n
+
+    def autotune(self, U, dt, stream=None):
+        _check(load().amrfd_autotune(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_autotune")
+        return self.get_tile()
+
+    def set_tile(self, seg, lines, threads):
+        _check(load().amrfd_set_tile(self._h, seg, lines, threads), "amrfd_set_tile")
+
+    def get_tile(self):
+        a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().amrfd_get_tile(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "amrfd_get_tile")
+        return a.value, b.value, c.value
+
+    def alpha(self, nstage=None, stream=None):
+        """Raw per-stage splitting speeds of the last step, shape (nstage, ndom, 3)."""
+        nstage = self.nstages if nstage is None else nstage
+        out = np.zeros((nstage, self.ndom, 3))
+        _check(load().amrfd_get_alpha(self._h, out.ctypes.data_as(ctypes.c_void_p), nstage, _stream(stream)),
+               "amrfd_get_alpha")
+        return out
+
+    def error(self, stream=None):
+        return load().amrfd_get_error(self._h, _stream(stream))

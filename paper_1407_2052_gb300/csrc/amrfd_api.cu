@@ -1,0 +1,646 @@
+// amrfd_api.cu -- host runtime behind include/amrfd.h: handle, workspace, work
+// lists, per-domain (plain) and persistent (batched, graph-replayed) steps,
+// time step, tile autotuner, error latch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <utility>
+#include <vector>
+
+#include "../../include/amrfd.h"
+#include "amrfd_internal.h"
+#include "amrfd_kernels.cuh"
+
+using namespace amrfd;
+
+namespace {
+
+struct Graph {
+  cudaGraphExec_t exec = nullptr;
+};
+
+// SSPRK tables of Sec. 2.3 in Shu-Osher form, one StageCoef per stage.
+// SSPRK3 is the third-order TVD Runge-Kutta scheme of Gottlieb & Shu (1998) cited there.
+// SSPRK(5,4) uses the printed coefficients; its last stage references L(U^(3)) only
+// through U^(4) = a40 U^n + a43 U^(3) + dt b43 L(U^(3)), which is substituted so that
+// no residual has to be stored across stages.
+int stage_table(int integrator, StageCoef co[kMaxStages]) {
+  std::memset(co, 0, sizeof(StageCoef) * kMaxStages);
+  auto set = [&](int i, std::initializer_list<std::pair<int, double>> terms, double b) {
+    int t = 0;
+    for (auto& kv : terms) { co[i].k[t] = kv.first; co[i].a[t] = kv.second; t++; }
+    co[i].nterm = t;
+    co[i].b = b;
+  };
+  if (integrator == AMRFD_SSPRK3) {
+    set(0, {{0, 1.0}}, 1.0);
+    set(1, {{0, 0.75}, {1, 0.25}}, 0.25);
+    set(2, {{0, 1.0 / 3.0}, {2, 2.0 / 3.0}}, 2.0 / 3.0);
+    return 3;
+  }
+  const double a10 = 0.44437049406734, a11 = 0.55562950593266;
+  const double a20 = 0.62010185138540, a22 = 0.37989814861460;
+  const double a30 = 0.17807995410773, a33 = 0.82192004589227;
+  const double a40 = 0.00683325884039, a42 = 0.51723167208978, a43 = 0.12759831133288, a44 = 0.34833675773694;
+  const double b00 = 0.39175222700392, b11 = 0.36841059262959, b22 = 0.25189177424738, b33 = 0.54497475021237;
+  const double b43 = 0.08460416338212, b44 = 0.22600748319395;
+  const double r = b43 / b33;  // dt L(U^(3)) = (U^(4) - a30 U^n - a33 U^(3)) / b33
+  set(0, {{0, 1.0}}, b00);
+  set(1, {{0, a10}, {1, a11}}, b11);
+  set(2, {{0, a20}, {2, a22}}, b22);
+  set(3, {{0, a30}, {3, a33}}, b33);
+  set(4, {{0, a40 - r * a30}, {2, a42}, {3, a43 - r * a33}, {4, a44 + r}}, b44);
+  return 5;
+}
+
+}  // namespace
+
+struct amrfd_handle {
+  amrfd_config cfg{};
+  int nv = 0, ns = 0, ndom = 0, nblocks = 0;
+  std::vector<amrfd_domain> doms;
+  std::vector<DomDev> hdom;
+  std::vector<int> dom_block0;
+  std::vector<unsigned char> active_h;
+  StageCoef co[kMaxStages];
+  int dev = 0, nsm = 0;
+  // tile of the flux pass
+  int seg = 32, lines = 32, threads = 0;
+  size_t flux_smem = 0;
+  int flux_grid = 0;
+  // work lists (full, grouped per block in work order) and per-block ranges
+  std::vector<int> order;             // global block id per work position
+  std::vector<int> fbeg, fcnt, cbeg, ccnt;
+  std::vector<int> dom_fbeg, dom_fend, dom_cbeg, dom_cend;  // per domain, in the full lists
+  int nfi = 0, nci = 0;
+  // device
+  DomDev* d_dom = nullptr;
+  unsigned char* d_active = nullptr;
+  FluxItem *d_fall = nullptr, *d_fact = nullptr;
+  CellItem *d_call = nullptr, *d_cact = nullptr;
+  int *d_order = nullptr, *d_fbeg = nullptr, *d_fcnt = nullptr, *d_cbeg = nullptr, *d_ccnt = nullptr;
+  int *d_fdst = nullptr, *d_cdst = nullptr, *d_counts = nullptr;  // counts[0]=flux, [1]=cell
+  int* d_counters = nullptr;        // one per persistent launch
+  double* d_stage[kMaxStages] = {};
+  double* d_L[3] = {};
+  unsigned long long* d_slot = nullptr;  // [kNumSlots][ndom][4]
+  unsigned* d_err = nullptr;
+  size_t nelem = 0;                 // elements of one state-shaped buffer
+  cudaStream_t cap = nullptr;       // private stream for graph capture
+  std::map<std::pair<const void*, const void*>, Graph> graphs;
+};
+
+namespace {
+
+int cuerr(cudaError_t e) {
+  if (e == cudaSuccess) return AMRFD_OK;
+  fprintf(stderr, "amrfd: CUDA error %s\n", cudaGetErrorString(e));
+  return AMRFD_ERR_CUDA;
+}
+#define CK(x) do { int rc_ = cuerr(x); if (rc_) return rc_; } while (0)
+
+void free_graphs(amrfd_handle* h) {
+  for (auto& kv : h->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  h->graphs.clear();
+}
+
+// Build full work lists for the current tile. Blocks are ordered largest first
+// (stable, so a domain's blocks stay contiguous); items are grouped per block.
+int build_items(amrfd_handle* h) {
+  std::vector<FluxItem> fi;
+  std::vector<CellItem> ci;
+  const int nd = h->cfg.ndim;
+  std::vector<int> ord(h->nblocks);
+  std::vector<long long> bsize(h->nblocks);
+  std::vector<int> bdom(h->nblocks), bloc(h->nblocks);
+  for (int d = 0; d < h->ndom; d++) {
+    const DomDev& dm = h->hdom[d];
+    const int nbl = dm.nb[0] * dm.nb[1] * dm.nb[2];
+    for (int b = 0; b < nbl; b++) {
+      const int g = dm.block0 + b;
+      bsize[g] = (long long)dm.be[0] * dm.be[1] * dm.be[2];
+      bdom[g] = d;
+      bloc[g] = b;
+    }
+  }
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
+  h->order = ord;
+  h->fbeg.assign(h->nblocks, 0); h->fcnt.assign(h->nblocks, 0);
+  h->cbeg.assign(h->nblocks, 0); h->ccnt.assign(h->nblocks, 0);
+  h->dom_fbeg.assign(h->ndom, -1); h->dom_fend.assign(h->ndom, -1);
+  h->dom_cbeg.assign(h->ndom, -1); h->dom_cend.assign(h->ndom, -1);
+  const int cell_chunk = 4096;
+  for (int pos = 0; pos < h->nblocks; pos++) {
+    const int g = ord[pos], d = bdom[g], b = bloc[g];
+    const DomDev& dm = h->hdom[d];
+    h->fbeg[pos] = (int)fi.size();
+    for (int dir = 0; dir < nd; dir++) {
+      const int od1 = dir == 0 ? 1 : 0, od2 = dir == 2 ? 1 : 2;
+      const int nlines = dm.be[od1] * dm.be[od2];
+      const int ext = dm.be[dir];
+      const int nseg = (ext + h->seg - 1) / h->seg;
+      const int slen0 = (ext + nseg - 1) / nseg;  // balanced segments
+      for (int sg = 0; sg < nseg; sg++) {
+        const int s0 = sg * slen0;
+        const int sl = std::min(slen0, ext - s0);
+        for (int l0 = 0; l0 < nlines; l0 += h->lines) {
+          FluxItem it{};
+          it.dom = d; it.blk = b; it.l0 = l0;
+          it.s0 = (short)s0; it.slen = (unsigned short)sl;
+          it.d = (unsigned char)dir;
+          it.nl = (unsigned char)std::min(h->lines, nlines - l0);
+          fi.push_back(it);
+        }
+      }
+    }
+    h->fcnt[pos] = (int)fi.size() - h->fbeg[pos];
+    h->cbeg[pos] = (int)ci.size();
+    const int ncb = (int)bsize[g];
+    for (int c0 = 0; c0 < ncb; c0 += cell_chunk) ci.push_back(CellItem{d, b, c0, std::min(cell_chunk, ncb - c0)});
+    h->ccnt[pos] = (int)ci.size() - h->cbeg[pos];
+    if (h->dom_fbeg[d] < 0) { h->dom_fbeg[d] = h->fbeg[pos]; h->dom_cbeg[d] = h->cbeg[pos]; }
+    h->dom_fend[d] = (int)fi.size();
+    h->dom_cend[d] = (int)ci.size();
+  }
+  h->nfi = (int)fi.size();
+  h->nci = (int)ci.size();
+  // (re)allocate and upload
+  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
+  CK(cudaMalloc(&h->d_fall, sizeof(FluxItem) * std::max(1, h->nfi)));
+  CK(cudaMalloc(&h->d_fact, sizeof(FluxItem) * std::max(1, h->nfi)));
+  CK(cudaMalloc(&h->d_call, sizeof(CellItem) * std::max(1, h->nci)));
+  CK(cudaMalloc(&h->d_cact, sizeof(CellItem) * std::max(1, h->nci)));
+  CK(cudaMemcpy(h->d_fall, fi.data(), sizeof(FluxItem) * h->nfi, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_call, ci.data(), sizeof(CellItem) * h->nci, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_order, ord.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_fbeg, h->fbeg.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_fcnt, h->fcnt.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_cbeg, h->cbeg.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->d_ccnt, h->ccnt.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  return AMRFD_OK;
+}
+
+int compact(amrfd_handle* h, cudaStream_t s) {
+  CompactParams p{};
+  p.nsorted = h->nblocks;
+  p.order = h->d_order;
+  p.fbeg = h->d_fbeg; p.fcnt = h->d_fcnt; p.cbeg = h->d_cbeg; p.ccnt = h->d_ccnt;
+  p.active = h->d_active;
+  p.fin = h->d_fall; p.fout = h->d_fact; p.nf = h->d_counts;
+  p.cin = h->d_call; p.cout = h->d_cact; p.nc = h->d_counts + 1;
+  p.fdst = h->d_fdst; p.cdst = h->d_cdst;
+  CK(launch_compact(p, s));
+  return AMRFD_OK;
+}
+
+int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
+  int maxext = 1;
+  for (auto& dm : h->hdom)
+    for (int d = 0; d < h->cfg.ndim; d++) maxext = std::max(maxext, dm.be[d]);
+  const int S = std::min(seg, maxext);
+  int SS = S + 2 * kGhost;
+  if (SS % 2 == 0) SS++;  // odd stride in doubles: conflict-free 64-bit lines
+  size_t smem = sizeof(double) * 2 * h->nv * lines * SS;
+  if (smem > 227 * 1024) return AMRFD_ERR_INVALID_ARG;
+  h->seg = seg;
+  h->lines = lines;
+  h->threads = threads;
+  h->flux_smem = smem;
+  CK(flux_set_smem(h->cfg.physics, h->nv, smem));
+  int per_sm = 0;
+  CK(flux_occupancy(h->cfg.physics, h->nv, threads, smem, &per_sm));
+  if (per_sm < 1) return AMRFD_ERR_INVALID_ARG;
+  h->flux_grid = per_sm * h->nsm;
+  free_graphs(h);
+  int rc = build_items(h);
+  if (rc) return rc;
+  return AMRFD_OK;
+}
+
+int default_threads(int nv, int lines) {
+  int t = ((nv * lines + 31) / 32) * 32;
+  return std::max(64, std::min(t, 384));
+}
+
+unsigned long long* slot(amrfd_handle* h, int k) { return h->d_slot + (size_t)k * h->ndom * 4; }
+
+FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int stage_in) {
+  FluxParams p{};
+  p.doms = h->d_dom;
+  p.active = h->d_active;
+  p.Uk = Uk;
+  p.Un = Un;
+  for (int d = 0; d < 3; d++) p.L[d] = h->d_L[d] ? h->d_L[d] : h->d_L[0];
+  p.araw = slot(h, stage_in);
+  p.araw0 = slot(h, 0);
+  p.gm1 = h->cfg.gamma - 1.0;
+  p.ndim = h->cfg.ndim;
+  p.P = h->lines;
+  int S = 1;
+  for (auto& dm : h->hdom)
+    for (int d = 0; d < h->cfg.ndim; d++) S = std::max(S, std::min(dm.be[d], h->seg));
+  // segments are balanced, never longer than seg
+  int SS = std::min(S, h->seg) + 2 * kGhost;
+  if (SS % 2 == 0) SS++;
+  p.SS = SS;
+  p.glm = h->cfg.physics == AMRFD_MHD_GLM;
+  return p;
+}
+
+CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
+  CombParams p{};
+  p.doms = h->d_dom;
+  p.active = h->d_active;
+  p.buf[0] = U;
+  for (int k = 1; k < kMaxStages; k++) p.buf[k] = h->d_stage[k];
+  p.out = (i == h->ns) ? U : h->d_stage[i];
+  for (int d = 0; d < 3; d++) p.L[d] = h->d_L[d] ? h->d_L[d] : h->d_L[0];
+  p.dt = dt;
+  p.co = h->co[i - 1];
+  p.slot_out = (i < h->ns) ? slot(h, i) : nullptr;
+  p.araw0 = slot(h, 0);
+  p.err = h->d_err;
+  p.gamma = h->cfg.gamma;
+  p.glm_cr = h->cfg.glm_cr;
+  p.ndim = h->cfg.ndim;
+  p.final_stage = (i == h->ns);
+  return p;
+}
+
+SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate) {
+  SpeedParams p{};
+  p.doms = h->d_dom;
+  p.active = h->d_active;
+  p.U = U;
+  p.slot = slot(h, k);
+  p.err = h->d_err;
+  p.gamma = h->cfg.gamma;
+  p.ndim = h->cfg.ndim;
+  p.want_rate = want_rate;
+  return p;
+}
+
+// Enqueue one full step. batched: persistent launches over the compacted lists;
+// else one launch per domain (per pass) over that domain's items.
+int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, bool batched) {
+  const int ph = h->cfg.physics, nv = h->nv;
+  CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
+  if (batched) CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
+  const int cgrid = 8 * h->nsm;
+  // speeds of U^n
+  {
+    SpeedParams p = speed_params(h, U, 0, 0);
+    if (batched) {
+      p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
+      CK(launch_speeds(ph, nv, p, cgrid, 256, s));
+    } else {
+      for (int d = 0; d < h->ndom; d++) {
+        if (h->dom_cbeg[d] < 0) continue;
+        bool any = false;
+        for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++) any |= h->active_h[h->hdom[d].block0 + b] != 0;
+        if (!any) continue;
+        p.items = h->d_call; p.item0 = h->dom_cbeg[d]; p.nitems = h->dom_cend[d] - h->dom_cbeg[d];
+        CK(launch_speeds(ph, nv, p, p.nitems, 256, s));
+      }
+    }
+  }
+  for (int i = 1; i <= h->ns; i++) {
+    const double* Uk = (i == 1) ? U : h->d_stage[i - 1];
+    FluxParams fp = flux_params(h, Uk, U, i - 1);
+    CombParams cp = comb_params(h, U, dt, i);
+    if (batched) {
+      fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
+      CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+      cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
+      CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+    } else {
+      std::vector<int> live;
+      for (int d = 0; d < h->ndom; d++) {
+        bool any = false;
+        for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++) any |= h->active_h[h->hdom[d].block0 + b] != 0;
+        if (any && h->dom_fbeg[d] >= 0) live.push_back(d);
+      }
+      // flux pass: items of passive blocks inside a live domain are skipped by
+      // compacting per domain on the host (same item order as the device list)
+      for (int d : live) {
+        fp.items = h->d_fall; fp.item0 = h->dom_fbeg[d]; fp.nitems = h->dom_fend[d] - h->dom_fbeg[d];
+        fp.counter = nullptr;
+        CK(launch_flux(ph, nv, fp, std::min(fp.nitems, h->flux_grid), h->threads, h->flux_smem, s));
+      }
+      for (int d : live) {
+        cp.items = h->d_call; cp.item0 = h->dom_cbeg[d]; cp.nitems = h->dom_cend[d] - h->dom_cbeg[d];
+        CK(launch_combine(ph, nv, cp, cp.nitems, 256, s));
+      }
+    }
+  }
+  return AMRFD_OK;
+}
+
+int validate(const amrfd_config* c, const amrfd_domain* d, int n) {
+  if (!c || !d || n <= 0) return AMRFD_ERR_INVALID_ARG;
+  if (c->physics != AMRFD_EULER && c->physics != AMRFD_MHD_GLM) return AMRFD_ERR_INVALID_ARG;
+  if (c->ndim < 1 || c->ndim > 3) return AMRFD_ERR_INVALID_ARG;
+  if (c->integrator != AMRFD_SSPRK3 && c->integrator != AMRFD_SSPRK54) return AMRFD_ERR_INVALID_ARG;
+  if (c->dt_scope != AMRFD_DT_PER_DOMAIN && c->dt_scope != AMRFD_DT_GLOBAL) return AMRFD_ERR_INVALID_ARG;
+  if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return AMRFD_ERR_INVALID_ARG;
+  for (int i = 0; i < n; i++) {
+    for (int k = 0; k < 3; k++) {
+      if (d[i].n[k] < 1 || d[i].nb[k] < 1 || d[i].n[k] % d[i].nb[k]) return AMRFD_ERR_INVALID_ARG;
+      if (k >= c->ndim && (d[i].n[k] != 1 || d[i].nb[k] != 1)) return AMRFD_ERR_INVALID_ARG;
+      if (k < c->ndim) {
+        if (!(d[i].dx[k] > 0.0)) return AMRFD_ERR_INVALID_ARG;
+        for (int f = 0; f < 2; f++)
+          if (d[i].bc[k][f] != AMRFD_BC_PERIODIC && d[i].bc[k][f] != AMRFD_BC_OUTFLOW) return AMRFD_ERR_INVALID_ARG;
+        if ((d[i].bc[k][0] == AMRFD_BC_PERIODIC) != (d[i].bc[k][1] == AMRFD_BC_PERIODIC)) return AMRFD_ERR_INVALID_ARG;
+        if (d[i].bc[k][0] == AMRFD_BC_PERIODIC && d[i].n[k] < 3) return AMRFD_ERR_INVALID_ARG;
+        if (d[i].n[k] / d[i].nb[k] > 32767) return AMRFD_ERR_INVALID_ARG;
+      }
+    }
+    if (d[i].offset < 0) return AMRFD_ERR_INVALID_ARG;
+    if ((long long)d[i].n[0] * d[i].n[1] * d[i].n[2] > 0x7fffffffLL) return AMRFD_ERR_INVALID_ARG;
+  }
+  // overlap check: sort by offset
+  const int nv = c->physics == AMRFD_EULER ? 2 + c->ndim : 9;
+  std::vector<std::pair<int64_t, int64_t>> r;
+  for (int i = 0; i < n; i++) r.push_back({d[i].offset, d[i].offset + (int64_t)nv * d[i].n[0] * d[i].n[1] * d[i].n[2]});
+  std::sort(r.begin(), r.end());
+  for (size_t i = 1; i < r.size(); i++)
+    if (r[i].first < r[i - 1].second) return AMRFD_ERR_INVALID_ARG;
+  return AMRFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* amrfd_strerror(int code) {
+  switch (code) {
+    case AMRFD_OK: return "ok";
+    case AMRFD_ERR_INVALID_ARG: return "invalid argument";
+    case AMRFD_ERR_CUDA: return "CUDA runtime error";
+    case AMRFD_ERR_UNSUPPORTED: return "unsupported";
+    case AMRFD_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    default: return "unknown error";
+  }
+}
+
+int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain* domains, int ndomain,
+                 const uint8_t* active_host, void* stream) {
+  if (!out) return AMRFD_ERR_INVALID_ARG;
+  *out = nullptr;
+  int rc = validate(cfg, domains, ndomain);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  amrfd_handle* h = new amrfd_handle();
+  h->cfg = *cfg;
+  h->nv = cfg->physics == AMRFD_EULER ? 2 + cfg->ndim : 9;
+  h->ns = stage_table(cfg->integrator, h->co);
+  h->ndom = ndomain;
+  h->doms.assign(domains, domains + ndomain);
+  CK(cudaGetDevice(&h->dev));
+  CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->dev));
+  int nb = 0;
+  for (int i = 0; i < ndomain; i++) {
+    DomDev dm{};
+    for (int k = 0; k < 3; k++) {
+      dm.n[k] = domains[i].n[k];
+      dm.nb[k] = domains[i].nb[k];
+      dm.be[k] = domains[i].n[k] / domains[i].nb[k];
+      dm.bc[k][0] = domains[i].bc[k][0];
+      dm.bc[k][1] = domains[i].bc[k][1];
+      dm.dx[k] = domains[i].dx[k];
+    }
+    dm.block0 = nb;
+    dm.ncell = dm.n[0] * dm.n[1] * dm.n[2];
+    dm.off = domains[i].offset;
+    h->nelem = std::max(h->nelem, (size_t)(dm.off + (long long)h->nv * dm.ncell));
+    nb += dm.nb[0] * dm.nb[1] * dm.nb[2];
+    h->hdom.push_back(dm);
+  }
+  h->nblocks = nb;
+  h->active_h.assign(nb, 1);
+  if (active_host) std::memcpy(h->active_h.data(), active_host, nb);
+  auto fail = [&](int code) { amrfd_destroy(h); return code; };
+#define CKH(x) do { int rc_ = cuerr(x); if (rc_) return fail(rc_); } while (0)
+  CKH(cudaMalloc(&h->d_dom, sizeof(DomDev) * ndomain));
+  CKH(cudaMemcpy(h->d_dom, h->hdom.data(), sizeof(DomDev) * ndomain, cudaMemcpyHostToDevice));
+  CKH(cudaMalloc(&h->d_active, nb));
+  CKH(cudaMemcpy(h->d_active, h->active_h.data(), nb, cudaMemcpyHostToDevice));
+  CKH(cudaMalloc(&h->d_order, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_fbeg, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_fcnt, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_cbeg, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_ccnt, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_fdst, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_cdst, sizeof(int) * nb));
+  CKH(cudaMalloc(&h->d_counts, sizeof(int) * 2));
+  CKH(cudaMalloc(&h->d_counters, sizeof(int) * 2 * kMaxStages));
+  CKH(cudaMalloc(&h->d_slot, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
+  CKH(cudaMemset(h->d_slot, 0, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
+  CKH(cudaMalloc(&h->d_err, sizeof(unsigned)));
+  CKH(cudaMemset(h->d_err, 0, sizeof(unsigned)));
+  for (int k = 1; k < h->ns; k++) CKH(cudaMalloc(&h->d_stage[k], sizeof(double) * h->nelem));
+  for (int d = 0; d < cfg->ndim; d++) CKH(cudaMalloc(&h->d_L[d], sizeof(double) * h->nelem));
+  CKH(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  const int lines = cfg->ndim == 1 ? 1 : 32;
+  rc = configure_tile(h, 32, lines, default_threads(h->nv, lines));
+  if (rc) return fail(rc);
+  rc = compact(h, s);
+  if (rc) return fail(rc);
+  CKH(cudaStreamSynchronize(s));
+#undef CKH
+  *out = h;
+  return AMRFD_OK;
+}
+
+int amrfd_set_active(amrfd_handle* h, const uint8_t* active_dev, void* stream) {
+  if (!h || !active_dev) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemcpyAsync(h->d_active, active_dev, h->nblocks, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(h->active_h.data(), active_dev, h->nblocks, cudaMemcpyDeviceToHost, s));
+  int rc = compact(h, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return AMRFD_OK;
+}
+
+int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double t_end, void* stream) {
+  if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned long long* sl = slot(h, kSlotDt);
+  CK(cudaMemsetAsync(sl, 0, sizeof(unsigned long long) * h->ndom * 4, s));
+  SpeedParams p = speed_params(h, U, kSlotDt, 1);
+  p.items = h->d_cact;
+  p.nitems_dev = h->d_counts + 1;
+  CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+  DtParams q{};
+  q.doms = h->d_dom;
+  q.slot = sl;
+  q.dt_out = dt_dev;
+  q.ndom = h->ndom;
+  q.cfl = h->cfg.cfl;
+  q.t = t;
+  q.t_end = t_end;
+  q.glm = h->cfg.physics == AMRFD_MHD_GLM;
+  q.ndim = h->cfg.ndim;
+  q.global_min = h->cfg.dt_scope == AMRFD_DT_GLOBAL;
+  CK(launch_dt(q, s));
+  return AMRFD_OK;
+}
+
+int amrfd_step(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
+  if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  return enqueue_step(h, U, dt_dev, (cudaStream_t)stream, false);
+}
+
+int amrfd_step_batched(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
+  if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  auto key = std::make_pair((const void*)U, (const void*)dt_dev);
+  auto itg = h->graphs.find(key);
+  if (itg == h->graphs.end()) {
+    // capture on a private stream, ordered after the caller's work through events
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_step(h, U, dt_dev, h->cap, true);
+    cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (rc) { if (g) cudaGraphDestroy(g); return rc; }
+    CK(e);
+    Graph gr;
+    e = cudaGraphInstantiate(&gr.exec, g, 0);
+    cudaGraphDestroy(g);
+    CK(e);
+    itg = h->graphs.emplace(key, gr).first;
+  }
+  CK(cudaGraphLaunch(itg->second.exec, s));
+  return AMRFD_OK;
+}
+
+int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
+                  void* stream) {
+  (void)h; (void)U_n; (void)dt_dev; (void)gU_np1; (void)gU_n; (void)stream;
+  return AMRFD_ERR_UNSUPPORTED;
+}
+
+int amrfd_set_tile(amrfd_handle* h, int seg, int lines, int threads) {
+  if (!h || seg < 8 || seg > 64 || lines < 1 || lines > 32 || threads < 32 || threads > 384 || threads % 32)
+    return AMRFD_ERR_INVALID_ARG;
+  int rc = configure_tile(h, seg, lines, threads);
+  if (rc) return rc;
+  rc = compact(h, 0);
+  if (rc) return rc;
+  CK(cudaDeviceSynchronize());
+  return AMRFD_OK;
+}
+
+int amrfd_get_tile(const amrfd_handle* h, int* seg, int* lines, int* threads) {
+  if (!h) return AMRFD_ERR_INVALID_ARG;
+  if (seg) *seg = h->seg;
+  if (lines) *lines = h->lines;
+  if (threads) *threads = h->threads;
+  return AMRFD_OK;
+}
+
+int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
+  if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  (void)dt_dev;
+  cudaStream_t s = (cudaStream_t)stream;
+  // sample state speeds (slot 0) so that the flux pass sees realistic c_max
+  CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ndom * 4, s));
+  {
+    SpeedParams p = speed_params(h, U, 0, 0);
+    p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
+    CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+  }
+  const int segs[] = {16, 32, 64};
+  const int lines_c[] = {8, 16, 32};
+  int best_seg = h->seg, best_lines = h->lines, best_thr = h->threads;
+  float best = 1e30f;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int sg : segs) {
+    for (int ln : lines_c) {
+      if (h->cfg.ndim == 1 && ln != 1) continue;
+      for (int mul = 1; mul <= 2; mul++) {
+        const int thr = std::min(384, default_threads(h->nv, ln) * mul);
+        if (mul == 2 && thr == default_threads(h->nv, ln)) continue;
+        if (configure_tile(h, sg, h->cfg.ndim == 1 ? 1 : ln, thr)) continue;
+        if (compact(h, s)) continue;
+        FluxParams fp = flux_params(h, U, U, 0);
+        fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters;
+        float tot = 0.f;
+        bool ok = true;
+        for (int rep = 0; rep < 3 && ok; rep++) {
+          if (cudaMemsetAsync(h->d_counters, 0, sizeof(int), s) != cudaSuccess) ok = false;
+          cudaEventRecord(e0, s);
+          if (launch_flux(h->cfg.physics, h->nv, fp, h->flux_grid, h->threads, h->flux_smem, s) != cudaSuccess) ok = false;
+          cudaEventRecord(e1, s);
+          if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0) tot += ms;
+        }
+        if (ok && tot < best) { best = tot; best_seg = sg; best_lines = h->lines; best_thr = thr; }
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int rc = configure_tile(h, best_seg, best_lines, best_thr);
+  if (rc) return rc;
+  rc = compact(h, s);
+  if (rc) return rc;
+  CK(cudaStreamSynchronize(s));
+  return AMRFD_OK;
+}
+
+int amrfd_get_alpha(amrfd_handle* h, double* out, int nstage, void* stream) {
+  if (!h || !out || nstage < 1 || nstage > kNumSlots) return AMRFD_ERR_INVALID_ARG;
+  std::vector<unsigned long long> tmp((size_t)nstage * h->ndom * 4);
+  CK(cudaMemcpyAsync(tmp.data(), h->d_slot, sizeof(unsigned long long) * tmp.size(), cudaMemcpyDeviceToHost,
+                     (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  for (int k = 0; k < nstage; k++)
+    for (int d = 0; d < h->ndom; d++)
+      for (int q = 0; q < 3; q++) {
+        unsigned long long b = tmp[((size_t)k * h->ndom + d) * 4 + q];
+        double x;
+        std::memcpy(&x, &b, sizeof x);
+        out[((size_t)k * h->ndom + d) * 3 + q] = x;
+      }
+  return AMRFD_OK;
+}
+
+int amrfd_get_error(amrfd_handle* h, void* stream) {
+  if (!h) return AMRFD_ERR_INVALID_ARG;
+  unsigned e = 0;
+  CK(cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+  CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), (cudaStream_t)stream));
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  return (e & kErrNonphysical) ? AMRFD_ERR_NONPHYSICAL : AMRFD_OK;
+}
+
+void amrfd_destroy(amrfd_handle* h) {
+  if (!h) return;
+  cudaDeviceSynchronize();
+  free_graphs(h);
+  cudaFree(h->d_dom); cudaFree(h->d_active);
+  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
+  cudaFree(h->d_order); cudaFree(h->d_fbeg); cudaFree(h->d_fcnt); cudaFree(h->d_cbeg); cudaFree(h->d_ccnt);
+  cudaFree(h->d_fdst); cudaFree(h->d_cdst); cudaFree(h->d_counts); cudaFree(h->d_counters);
+  for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_stage[k]);
+  for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
+  cudaFree(h->d_slot); cudaFree(h->d_err);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  delete h;
+}
+
+}  // extern "C"

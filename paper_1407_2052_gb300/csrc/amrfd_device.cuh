@@ -1,0 +1,189 @@
+// amrfd_device.cuh -- device-side building blocks of the FD-MP5 update.
+//
+// FP64 issue rate on GB300 is 1/64 of FP32, so everything that can be done
+// exactly without the FP64 pipe is: comparisons, min/max, minmod, median and
+// sign logic run on the integer pipe over the IEEE bit patterns (all exact).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "amrfd_internal.h"
+
+namespace amrfd {
+
+enum { PH_EULER = 0, PH_MHD = 1 };
+
+// ---------------------------------------------------------------- exact helpers
+__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
+
+// Monotone signed-integer key of a double (total order; -0 sorts before +0).
+__device__ __forceinline__ long long okey(double x) {
+  long long b = dbits(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double imin(double a, double b) { return okey(a) < okey(b) ? a : b; }
+__device__ __forceinline__ double imax(double a, double b) { return okey(a) < okey(b) ? b : a; }
+
+// minmod(a,b) = (sgn a + sgn b)/2 * min(|a|,|b|): the smaller-magnitude argument
+// when both have the same sign, else zero.
+__device__ __forceinline__ double iminmod(double a, double b) {
+  long long ba = dbits(a), bb = dbits(b);
+  long long ma = ba & 0x7fffffffffffffffLL, mb = bb & 0x7fffffffffffffffLL;
+  long long r = (ma < mb) ? ba : bb;
+  return ((ba ^ bb) < 0) ? 0.0 : bitsd(r);
+}
+
+// minmod of four arguments: signed smallest magnitude if all share a sign, else 0.
+__device__ __forceinline__ double iminmod4(double w, double x, double y, double z) {
+  long long bw = dbits(w), bx = dbits(x), by = dbits(y), bz = dbits(z);
+  const long long M = 0x7fffffffffffffffLL;
+  long long m = bw & M, t;
+  t = bx & M; m = t < m ? t : m;
+  t = by & M; m = t < m ? t : m;
+  t = bz & M; m = t < m ? t : m;
+  bool mixed = ((bw ^ bx) | (bw ^ by) | (bw ^ bz)) < 0;
+  return mixed ? 0.0 : bitsd(m | (bw & ~M));
+}
+
+// median(x, y, z) -- one of its arguments, no rounding
+__device__ __forceinline__ double imedian(double x, double y, double z) {
+  return imax(imin(x, y), imin(imax(x, y), z));
+}
+
+// x <= c for a finite non-negative constant c (NaN compares false)
+__device__ __forceinline__ bool ile_pos(double x, double c) { return okey(x) <= dbits(c); }
+
+// ---------------------------------------------------------- MP5 in difference form
+// Value at the face relative to the centre cell f_i (Suresh & Huynh 1997):
+//   Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1},
+//   Mp, Mm = the minmod4 curvatures at i+1/2 and i-1/2.
+// f_or - f_i = (2 f_{i-2} - 13 f_{i-1} + 47 f_i + 27 f_{i+1} - 3 f_{i+2})/60 - f_i
+//            = (11 D0 - 2 Dm + 24 D1 - 3 Dp)/60.
+// The bounds f_ul, f_md, f_lc, f_min, f_max are shifted by -f_i the same way.
+// eps4 is the MP acceptance threshold in the units of the reconstructed values.
+__device__ __forceinline__ double mp5_rel(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
+                                          double eps4) {
+  const double c11 = 11.0 / 60.0, c2 = 2.0 / 60.0, c24 = 24.0 / 60.0, c3 = 3.0 / 60.0;
+  double X = fma(c24, D1, fma(-c2, Dm, c11 * D0));
+  X = fma(-c3, Dp, X);
+  double ul = 4.0 * D0;                 // f_ul - f_i = alpha (f_i - f_{i-1}), alpha = 4
+  double mp = iminmod(D1, ul);          // f_mp - f_i
+  double chk = X * (X - mp);
+  if (ile_pos(chk, eps4)) return X;
+  double md = 0.5 * (D1 - Mp);          // f_md - f_i = (f_av - f_i) - Mp/2
+  double lc = fma(4.0 / 3.0, Mm, 0.5 * D0);  // f_lc - f_i
+  double fmin = imax(imin(imin(0.0, D1), md), imin(imin(0.0, ul), lc));
+  double fmax = imin(imax(imax(0.0, D1), md), imax(imax(0.0, ul), lc));
+  return imedian(X, fmin, fmax);
+}
+
+// curvature-limited second difference at a face from the curvatures of its two cells
+__device__ __forceinline__ double dm4(double ka, double kb) {
+  return iminmod4(fma(4.0, ka, -kb), fma(4.0, kb, -ka), ka, kb);
+}
+
+// ------------------------------------------------- exact characteristic speeds
+// Same operation order as the CPU definition (no contraction), so that splitting
+// speeds and time steps of a given state agree bit for bit.
+struct Prim {
+  double rho, v[3], p, B[3], psi;
+};
+
+template <int PHYS, int NV>
+__device__ __forceinline__ bool cons2prim_exact(const double* u, double gamma, int ndim, Prim& w) {
+  w.rho = u[0];
+  const int nm = PHYS == PH_EULER ? NV - 2 : 3;
+#pragma unroll
+  for (int k = 0; k < 3; k++) w.v[k] = (k < nm) ? __ddiv_rn(u[1 + k], w.rho) : 0.0;
+  double vv = __dadd_rn(__dadd_rn(__dmul_rn(w.v[0], w.v[0]), __dmul_rn(w.v[1], w.v[1])), __dmul_rn(w.v[2], w.v[2]));
+  double ekin = __dmul_rn(__dmul_rn(0.5, w.rho), vv);
+  double emag = 0.0, E;
+  if (PHYS == PH_MHD) {
+    w.B[0] = u[5]; w.B[1] = u[6]; w.B[2] = u[7]; w.psi = u[8];
+    emag = __dmul_rn(0.5, __dadd_rn(__dadd_rn(__dmul_rn(w.B[0], w.B[0]), __dmul_rn(w.B[1], w.B[1])),
+                                    __dmul_rn(w.B[2], w.B[2])));
+    E = u[4];
+  } else {
+    w.B[0] = w.B[1] = w.B[2] = 0.0; w.psi = 0.0;
+    E = u[NV - 1];
+  }
+  w.p = __dmul_rn(__dsub_rn(gamma, 1.0), __dsub_rn(__dsub_rn(E, ekin), emag));
+  return (w.rho > 0.0) && (w.p > 0.0) && isfinite(w.rho) && isfinite(w.p) && isfinite(w.psi);
+}
+
+template <int PHYS>
+__device__ __forceinline__ double char_speed_exact(const Prim& w, double gamma, int d) {
+  if (PHYS == PH_EULER) return __dadd_rn(fabs(w.v[d]), __dsqrt_rn(__ddiv_rn(__dmul_rn(gamma, w.p), w.rho)));
+  double a2 = __ddiv_rn(__dmul_rn(gamma, w.p), w.rho);
+  double b2 = __ddiv_rn(__dadd_rn(__dadd_rn(__dmul_rn(w.B[0], w.B[0]), __dmul_rn(w.B[1], w.B[1])),
+                                  __dmul_rn(w.B[2], w.B[2])), w.rho);
+  double s = __dadd_rn(a2, b2);
+  double bd = w.B[d];
+  double disc = __dsub_rn(__dmul_rn(s, s), __ddiv_rn(__dmul_rn(__dmul_rn(4.0, a2), __dmul_rn(bd, bd)), w.rho));
+  if (disc < 0.0) disc = 0.0;
+  double cf = __dsqrt_rn(__dmul_rn(0.5, __dadd_rn(s, __dsqrt_rn(disc))));
+  return __dadd_rn(fabs(w.v[d]), cf);
+}
+
+// ------------------------------------------------------ fast flux + LF split
+// G^{+-} = F_d +- alpha_d U = 2 F^{+-}: the factor 1/2 of the splitting is
+// applied once to the final flux difference (MP5 commutes with scaling by 2
+// when its acceptance threshold is scaled by 4).
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void split_flux(const double* u, double gm1, double alpha, double ch2,
+                                           double* gp, double* gm) {
+  double f[NV];
+  const double rho = u[0];
+  const double ir = 1.0 / rho;
+  if (PHYS == PH_EULER) {
+    constexpr int nm = NV - 2;
+    double v[nm];
+    double mv = 0.0;
+#pragma unroll
+    for (int k = 0; k < nm; k++) { v[k] = u[1 + k] * ir; mv = fma(u[1 + k], v[k], mv); }
+    const double E = u[NV - 1];
+    const double p = gm1 * fma(-0.5, mv, E);
+    const double vd = v[D];
+    f[0] = u[1 + D];
+#pragma unroll
+    for (int k = 0; k < nm; k++) f[1 + k] = (k == D) ? fma(vd, u[1 + k], p) : vd * u[1 + k];
+    f[NV - 1] = vd * (E + p);
+  } else {
+    const double E = u[4], psi = u[8];
+    const double B[3] = {u[5], u[6], u[7]};
+    const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+    const double b2 = fma(B[2], B[2], fma(B[1], B[1], B[0] * B[0]));
+    const double mv = fma(u[3], v[2], fma(u[2], v[1], u[1] * v[0]));
+    const double p = gm1 * fma(-0.5, mv + b2, E);
+    const double ptot = fma(0.5, b2, p);
+    const double vb = fma(v[2], B[2], fma(v[1], B[1], v[0] * B[0]));
+    const double vd = v[D], bd = B[D];
+    f[0] = u[1 + D];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      f[1 + k] = fma(vd, u[1 + k], -bd * B[k]);
+      if (k == D) f[1 + k] += ptot;
+      f[5 + k] = (k == D) ? psi : fma(vd, B[k], -bd * v[k]);
+    }
+    f[4] = fma(vd, E + ptot, -bd * vb);
+    f[8] = ch2 * bd;
+  }
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    gp[v] = fma(alpha, u[v], f[v]);
+    gm[v] = fma(-alpha, u[v], f[v]);
+  }
+}
+
+// ------------------------------------------------------------- block reductions
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+    x = y > x ? y : x;
+  }
+  return x;
+}
+
+}  // namespace amrfd

@@ -1,0 +1,480 @@
+// amrfd_kernels.cu -- FP64 kernels of the FD-MP5 update (Porth et al. 2014, Sec. 2).
+//
+//  speeds_kernel   maximal characteristic speed per cell -> per-domain c_max per
+//                  direction (Sec. 2.2, "grid-global c_max") and the CFL rate
+//                  sum_d c_d/dx_d (Sec. 4.4); exact IEEE operations in the order
+//                  of the definition, reduced with integer max on the bit patterns.
+//  flux_kernel     one direction's flux difference for a tile of lines:
+//                  halo synthesis (periodic / zero-gradient), conserved->primitive,
+//                  physical flux, Lax-Friedrichs split G^{+-} = F +- c_max U (Sec. 2.2),
+//                  MP5 at every face (Suresh & Huynh 1997, as cited in Sec. 2.2) on
+//                  both biases, F^ = R_L(F^+) + R_R(F^-), and -dF^/dx (Sec. 2.1).
+//  combine_kernel  Shu-Osher stage U^(i) = sum a U^(k) + dt b L (Sec. 2.3), GLM psi
+//                  damping after the last stage (Sec. 4.2), speeds of U^(i).
+//  dt_kernel       dt = CFL / rate per domain, clamped to t_end - t.
+//  compact kernels device-side work list of the active blocks (App. C).
+#include <cuda_runtime.h>
+
+#include "amrfd_device.cuh"
+#include "amrfd_kernels.cuh"
+
+namespace amrfd {
+
+// ----------------------------------------------------------------- utilities
+__device__ __forceinline__ void block_coords(const DomDev& dm, int blk, int o[3]) {
+  int bx = blk % dm.nb[0];
+  int by = (blk / dm.nb[0]) % dm.nb[1];
+  int bz = blk / (dm.nb[0] * dm.nb[1]);
+  o[0] = bx * dm.be[0];
+  o[1] = by * dm.be[1];
+  o[2] = bz * dm.be[2];
+}
+
+__device__ __forceinline__ DomDev load_dom(const DomDev* p) { return *p; }
+
+// block-wide max of four u64 values; result valid in thread 0
+__device__ __forceinline__ void block_max4(unsigned long long v[4], unsigned long long (*red)[32]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    unsigned long long x = warp_max_u64(v[q]);
+    if (lane == 0) red[q][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      unsigned long long x = lane < nw ? red[q][lane] : 0ull;
+      v[q] = warp_max_u64(x);
+    }
+  }
+  __syncthreads();
+}
+
+// ------------------------------------------------------------------ speeds
+template <int PHYS, int NV>
+__global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
+  __shared__ unsigned long long red[4][32];
+  const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const CellItem ci = p.items[p.item0 + it];
+    const DomDev dm = load_dom(p.doms + ci.dom);
+    if (!p.active[dm.block0 + ci.blk]) continue;
+    int o[3];
+    block_coords(dm, ci.blk, o);
+    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      const double* src = p.U + dm.off + idx;
+      double u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
+      Prim w;
+      if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) {
+        atomicOr(p.err, kErrNonphysical);
+        continue;
+      }
+      double rate = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        if (d < p.ndim) {
+          const double cd = char_speed_exact<PHYS>(w, p.gamma, d);
+          const unsigned long long b = (unsigned long long)dbits(cd);
+          mx[d] = b > mx[d] ? b : mx[d];
+          if (p.want_rate) rate = __dadd_rn(rate, __ddiv_rn(cd, dm.dx[d]));
+        }
+      }
+      const unsigned long long br = (unsigned long long)dbits(rate);
+      mx[3] = br > mx[3] ? br : mx[3];
+    }
+    block_max4(mx, red);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (mx[q]) atomicMax(p.slot + (size_t)ci.dom * 4 + q, mx[q]);
+    }
+  }
+}
+
+// -------------------------------------------------------------------- flux
+__device__ __forceinline__ double glm_speed(const unsigned long long* s0, int ndim) {
+  double ch = 0.0;
+  for (int d = 0; d < ndim; d++) ch = imax(ch, bitsd((long long)s0[d]));
+  return ch;
+}
+
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& dm, const FluxItem& it,
+                                             const int o[3], double alpha, double ch2, double* sm) {
+  constexpr int od1 = D == 0 ? 1 : 0;
+  constexpr int od2 = D == 2 ? 1 : 2;
+  const int W = it.slen + 2 * kGhost;
+  const int nl = it.nl;
+  const int P = p.P, SS = p.SS;
+  const double gm1 = p.gm1;
+  for (int c = threadIdx.x; c < nl * W; c += blockDim.x) {
+    int pl, j;
+    if (D == 0) { pl = c / W; j = c - pl * W; }
+    else { j = c / nl; pl = c - j * nl; }
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    int g = o[D] + it.s0 + j - kGhost;
+    if (g < 0) g = dm.bc[D][0] == 0 ? g + dm.n[D] : 0;
+    else if (g >= dm.n[D]) g = dm.bc[D][1] == 0 ? g - dm.n[D] : dm.n[D] - 1;
+    x[D] = g;
+    const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
+    const double* base = p.active[nbk] ? p.Uk : p.Un;
+    const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
+    const double* src = base + dm.off + idx;
+    double u[NV], gp[NV], gmn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
+    split_flux<PHYS, NV, D>(u, gm1, alpha, ch2, gp, gmn);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      sm[((0 * NV + v) * P + pl) * SS + j] = gp[v];
+      sm[((1 * NV + v) * P + pl) * SS + j] = gmn[v];
+    }
+  }
+}
+
+// Sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of the
+// line's extended index (cell j = k-1 left of face k), then the flux difference of
+// cells j = 3..slen+2 written back over the consumed part of the G^+ line.
+__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double hdx, double eps4) {
+  double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
+  double Pk1 = Pd2 - Pd1, Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
+  double PM2 = dm4(Pk1, Pk2), PM3 = dm4(Pk2, Pk3);
+  double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
+  double Mk2 = Md3 - Md2, Mk3 = Md4 - Md3, Mk4 = Md5 - Md4;
+  double MM3 = dm4(Mk2, Mk3), MM4 = dm4(Mk3, Mk4);
+  double cp = g[2], cm = h[3];
+  double Fprev = 0.0;
+  const int kend = slen + 3;
+  for (int k = 3; k <= kend; ++k) {
+    // left-biased reconstruction of G^+ centred on cell k-1
+    const double Yp = mp5_rel(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps4);
+    // right-biased reconstruction of G^- centred on cell k (mirror image)
+    const double Ym = mp5_rel(-Md5, -Md4, -Md3, -Md2, MM3, MM4, eps4);
+    const double F = (cp + cm) + (Yp + Ym);
+    if (k > 3) g[k - 4] = (Fprev - F) * hdx;
+    Fprev = F;
+    if (k < kend) {
+      const double gn = g[k + 2] - g[k + 1];
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = gn;
+      Pk1 = Pk2; Pk2 = Pk3; Pk3 = Pd4 - Pd3;
+      PM2 = PM3; PM3 = dm4(Pk2, Pk3);
+      cp = g[k];
+      const double hn = h[k + 3] - h[k + 2];
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = hn;
+      Mk2 = Mk3; Mk3 = Mk4; Mk4 = Md5 - Md4;
+      MM3 = MM4; MM4 = dm4(Mk3, Mk4);
+      cm = h[k + 1];
+    }
+  }
+  (void)Pk1;
+  (void)Mk2;
+}
+
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm) {
+  const DomDev dm = load_dom(p.doms + it.dom);
+  int o[3];
+  block_coords(dm, it.blk, o);
+  const unsigned long long* sk = p.araw + (size_t)it.dom * 4;
+  const unsigned long long* s0 = p.araw0 + (size_t)it.dom * 4;
+  const double ch = p.glm ? glm_speed(s0, p.ndim) : 0.0;
+  const double alpha = imax(bitsd((long long)sk[D]), ch);
+  flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch * ch, sm);
+  __syncthreads();
+  const int nl = it.nl, slen = it.slen;
+  const double hdx = 0.5 / dm.dx[D];
+  // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} scales it by 4
+  const double eps4 = 4e-10;
+  for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
+    const int v = t / nl, pl = t - v * nl;
+    double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
+    const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
+    flux_sweep(g, h, slen, hdx, eps4);
+  }
+  __syncthreads();
+  // coalesced write-out of L_D for the segment's interior cells
+  constexpr int od1 = D == 0 ? 1 : 0;
+  constexpr int od2 = D == 2 ? 1 : 2;
+  double* Ld = p.L[D] + dm.off;
+  for (int c = threadIdx.x; c < nl * slen; c += blockDim.x) {
+    int pl, j;
+    if (D == 0) { pl = c / slen; j = c - pl * slen; }
+    else { j = c / nl; pl = c - j * nl; }
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    x[D] = o[D] + it.s0 + j;
+    const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
+#pragma unroll
+    for (int v = 0; v < NV; v++) Ld[(long long)v * dm.ncell + idx] = sm[((0 * NV + v) * p.P + pl) * p.SS + j];
+  }
+  __syncthreads();
+}
+
+template <int PHYS, int NV>
+__global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
+  extern __shared__ double sm[];
+  __shared__ int s_it;
+  const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  int it;
+  if (p.counter) {
+    if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
+    __syncthreads();
+    it = s_it;
+    __syncthreads();
+  } else {
+    it = blockIdx.x;
+  }
+  constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
+  while (it < nitems) {
+    const FluxItem item = p.items[p.item0 + it];
+    const bool live = p.active[p.doms[item.dom].block0 + item.blk] != 0;
+    if (live && item.d == 0) flux_item<PHYS, NV, 0>(p, item, sm);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0)>(p, item, sm); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0)>(p, item, sm); }
+    if (p.counter) {
+      if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
+      __syncthreads();
+      it = s_it;
+      __syncthreads();
+    } else {
+      it += gridDim.x;
+    }
+  }
+}
+
+// ----------------------------------------------------------------- combine
+template <int PHYS, int NV>
+__global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
+  __shared__ unsigned long long red[4][32];
+  __shared__ double s_fac;
+  const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+    const CellItem ci = p.items[p.item0 + it];
+    const DomDev dm = load_dom(p.doms + ci.dom);
+    if (!p.active[dm.block0 + ci.blk]) continue;
+    int o[3];
+    block_coords(dm, ci.blk, o);
+    const double dt = p.dt[ci.dom];
+    const double dtb = dt * p.co.b;
+    const bool damp = PHYS == PH_MHD && p.final_stage && p.glm_cr > 0.0;
+    if (damp) {
+      if (threadIdx.x == 0) {
+        const double ch = glm_speed(p.araw0 + (size_t)ci.dom * 4, p.ndim);
+        s_fac = exp(-dt * ch / p.glm_cr);
+      }
+      __syncthreads();
+    }
+    const double fac = damp ? s_fac : 1.0;
+    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      double u[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        const long long e = idx + (long long)v * dm.ncell;
+        double l_ = p.L[0][e];
+        if (p.ndim > 1) l_ += p.L[1][e];
+        if (p.ndim > 2) l_ += p.L[2][e];
+        double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
+        for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
+        acc = fma(dtb, l_, acc);
+        if (PHYS == PH_MHD && v == 8) acc *= fac;
+        u[v] = acc;
+        p.out[e] = acc;
+      }
+      if (p.slot_out) {
+        Prim w;
+        if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) {
+          atomicOr(p.err, kErrNonphysical);
+          continue;
+        }
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          if (d < p.ndim) {
+            const unsigned long long b = (unsigned long long)dbits(char_speed_exact<PHYS>(w, p.gamma, d));
+            mx[d] = b > mx[d] ? b : mx[d];
+          }
+        }
+      }
+    }
+    if (p.slot_out) {
+      block_max4(mx, red);
+      if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 3; q++)
+          if (mx[q]) atomicMax(p.slot_out + (size_t)ci.dom * 4 + q, mx[q]);
+      }
+    } else if (damp) {
+      __syncthreads();  // s_fac is rewritten by the next item
+    }
+  }
+}
+
+// --------------------------------------------------------------------- dt
+__global__ void __launch_bounds__(1024) dt_kernel(DtParams p) {
+  __shared__ long long red[32];
+  long long best = 0x7fffffffffffffffLL;  // okey of the minimum over this thread's domains
+  for (int dmi = threadIdx.x; dmi < p.ndom; dmi += blockDim.x) {
+    const DomDev& dm = p.doms[dmi];
+    const unsigned long long* s = p.slot + (size_t)dmi * 4;
+    double rate;
+    if (p.glm) {
+      double ch = 0.0;
+      for (int d = 0; d < p.ndim; d++) ch = imax(ch, bitsd((long long)s[d]));
+      rate = 0.0;
+      for (int d = 0; d < p.ndim; d++) rate = __dadd_rn(rate, __ddiv_rn(ch, dm.dx[d]));
+    } else {
+      rate = bitsd((long long)s[3]);
+    }
+    double dt = rate > 0.0 ? __ddiv_rn(p.cfl, rate) : __longlong_as_double(0x7ff0000000000000LL);
+    const double rem = __dsub_rn(p.t_end, p.t);
+    dt = imin(dt, rem);
+    p.dt_out[dmi] = dt;
+    const long long k = okey(dt);
+    best = k < best ? k : best;
+  }
+  if (!p.global_min) return;
+  for (int o = 16; o > 0; o >>= 1) {
+    long long y = __shfl_xor_sync(0xffffffffu, best, o);
+    best = y < best ? y : best;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    long long x = threadIdx.x < (blockDim.x + 31) / 32 ? red[threadIdx.x] : 0x7fffffffffffffffLL;
+    for (int o = 16; o > 0; o >>= 1) {
+      long long y = __shfl_xor_sync(0xffffffffu, x, o);
+      x = y < x ? y : x;
+    }
+    if (threadIdx.x == 0) red[0] = x;
+  }
+  __syncthreads();
+  const long long kb = red[0];
+  const double dmin = bitsd(kb ^ ((kb >> 63) & 0x7fffffffffffffffLL));
+  for (int dmi = threadIdx.x; dmi < p.ndom; dmi += blockDim.x) p.dt_out[dmi] = dmin;
+}
+
+// ------------------------------------------------------------- compaction
+__global__ void __launch_bounds__(1024) compact_scan_kernel(CompactParams p) {
+  __shared__ int wsum[2][32];
+  __shared__ int carry[2];
+  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < p.nsorted; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    int f = 0, c = 0;
+    if (i < p.nsorted && p.active[p.order[i]]) { f = p.fcnt[i]; c = p.ccnt[i]; }
+    // inclusive warp scans
+    int fs = f, cs = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      int a = __shfl_up_sync(0xffffffffu, fs, o), b = __shfl_up_sync(0xffffffffu, cs, o);
+      if (lane >= o) { fs += a; cs += b; }
+    }
+    if (lane == 31) { wsum[0][wid] = fs; wsum[1][wid] = cs; }
+    __syncthreads();
+    if (wid == 0) {
+      const int nw = blockDim.x >> 5;
+      int a = lane < nw ? wsum[0][lane] : 0, b = lane < nw ? wsum[1][lane] : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        int x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, b, o);
+        if (lane >= o) { a += x; b += y; }
+      }
+      if (lane < nw) { wsum[0][lane] = a; wsum[1][lane] = b; }
+    }
+    __syncthreads();
+    const int fo = carry[0] + (wid ? wsum[0][wid - 1] : 0) + fs - f;
+    const int co = carry[1] + (wid ? wsum[1][wid - 1] : 0) + cs - c;
+    if (i < p.nsorted) { p.fdst[i] = fo; p.cdst[i] = co; }
+    __syncthreads();
+    if (threadIdx.x == blockDim.x - 1) { carry[0] = fo + f; carry[1] = co + c; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) { *p.nf = carry[0]; *p.nc = carry[1]; }
+}
+
+__global__ void __launch_bounds__(256) compact_copy_kernel(CompactParams p) {
+  for (int i = blockIdx.x; i < p.nsorted; i += gridDim.x) {
+    if (!p.active[p.order[i]]) continue;
+    const int fb = p.fbeg[i], fc = p.fcnt[i], fd = p.fdst[i];
+    for (int t = threadIdx.x; t < fc; t += blockDim.x) p.fout[fd + t] = p.fin[fb + t];
+    const int cb = p.cbeg[i], cc = p.ccnt[i], cd = p.cdst[i];
+    for (int t = threadIdx.x; t < cc; t += blockDim.x) p.cout[cd + t] = p.cin[cb + t];
+  }
+}
+
+// ------------------------------------------------------------- dispatch
+#define AMRFD_DISPATCH(physics, nv, CALL)                                   \
+  do {                                                                      \
+    if ((physics) == PH_MHD && (nv) == 9) { CALL(PH_MHD, 9); }              \
+    else if ((physics) == PH_EULER && (nv) == 3) { CALL(PH_EULER, 3); }     \
+    else if ((physics) == PH_EULER && (nv) == 4) { CALL(PH_EULER, 4); }     \
+    else if ((physics) == PH_EULER && (nv) == 5) { CALL(PH_EULER, 5); }     \
+    else return cudaErrorInvalidValue;                                      \
+  } while (0)
+
+cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, int block, cudaStream_t s) {
+#define CALL(PH, NVV) speeds_kernel<PH, NVV><<<grid, block, 0, s>>>(p)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s) {
+#define CALL(PH, NVV) flux_kernel<PH, NVV><<<grid, block, smem, s>>>(p)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t flux_set_smem(int physics, int nv, size_t smem) {
+#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaSuccess;
+}
+
+cudaError_t flux_occupancy(int physics, int nv, int block, size_t smem, int* per_sm) {
+#define CALL(PH, NVV) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV>, block, smem)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaSuccess;
+}
+
+cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, int block, cudaStream_t s) {
+#define CALL(PH, NVV) combine_kernel<PH, NVV><<<grid, block, 0, s>>>(p)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dt(const DtParams& p, cudaStream_t s) {
+  dt_kernel<<<1, 1024, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_compact(const CompactParams& p, cudaStream_t s) {
+  compact_scan_kernel<<<1, 1024, 0, s>>>(p);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  compact_copy_kernel<<<p.nsorted < 4096 ? (p.nsorted > 0 ? p.nsorted : 1) : 4096, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace amrfd

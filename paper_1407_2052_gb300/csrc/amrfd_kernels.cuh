@@ -1,0 +1,101 @@
+// amrfd_kernels.cuh -- kernel parameter blocks and host-side launch wrappers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "amrfd_internal.h"
+
+namespace amrfd {
+
+// Per-cell maximal characteristic speeds of a state, reduced per domain into
+// slot[dom][0..2] (raw c_max per direction) and slot[dom][3] (max sum_d c_d/dx_d).
+struct SpeedParams {
+  const DomDev* doms;
+  const unsigned char* active;  // per global block; items of passive blocks are skipped
+  const CellItem* items;
+  int nitems;              // used when nitems_dev == nullptr
+  const int* nitems_dev;   // device count of a compacted list
+  int item0;
+  const double* U;
+  unsigned long long* slot;
+  unsigned* err;
+  double gamma;
+  int ndim;
+  int want_rate;
+};
+
+// One flux pass: L_d(U^(k)) for the items' lines.
+struct FluxParams {
+  const DomDev* doms;
+  const unsigned char* active;  // per global block
+  const FluxItem* items;
+  int nitems;
+  const int* nitems_dev;
+  int item0;
+  int* counter;                 // persistent work counter (nullptr: static grid stride)
+  const double* Uk;             // stage input state
+  const double* Un;             // U^n (halo source inside passive neighbour blocks)
+  double* L[3];
+  const unsigned long long* araw;   // speeds slot of the stage input
+  const unsigned long long* araw0;  // speeds slot of U^n (GLM speed c_h)
+  double gm1;
+  int ndim;
+  int P;                        // lines per tile (smem layout)
+  int SS;                       // smem stride of one line (>= max segment + 6, odd)
+  int glm;
+};
+
+// One stage combination, optionally with the speeds of the new state.
+struct CombParams {
+  const DomDev* doms;
+  const unsigned char* active;
+  const CellItem* items;
+  int nitems;
+  const int* nitems_dev;
+  int item0;
+  const double* buf[5];         // 0: U^n, j: stage j
+  double* out;
+  const double* L[3];
+  const double* dt;
+  StageCoef co;
+  unsigned long long* slot_out; // speeds of the output state (nullptr: none)
+  const unsigned long long* araw0;
+  unsigned* err;
+  double gamma;
+  double glm_cr;
+  int ndim;
+  int final_stage;
+};
+
+struct DtParams {
+  const DomDev* doms;
+  const unsigned long long* slot;
+  double* dt_out;
+  int ndom;
+  double cfl, t, t_end;
+  int glm;
+  int ndim;
+  int global_min;
+};
+
+// compaction of per-block item ranges to the active blocks (order kept)
+struct CompactParams {
+  int nsorted;                 // blocks in work order
+  const int* order;            // global block id per work position
+  const int* fbeg; const int* fcnt;
+  const int* cbeg; const int* ccnt;
+  const unsigned char* active;
+  const FluxItem* fin; FluxItem* fout; int* nf;
+  const CellItem* cin; CellItem* cout; int* nc;
+  int* fdst; int* cdst;        // scratch: destination offsets per work position
+};
+
+// launch wrappers (dispatch on physics / number of variables)
+cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_dt(const DtParams& p, cudaStream_t s);
+cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
+cudaError_t flux_set_smem(int physics, int nv, size_t smem);
+cudaError_t flux_occupancy(int physics, int nv, int block, size_t smem, int* per_sm);
+
+}  // namespace amrfd

@@ -1,0 +1,70 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/amrfd.h declares; argument validation runs on the host."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names += re.findall(r"^\s*(?:int|void|const char\s*\*)\s*(amrfd_\w+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_1407_2052_gb300 import amrfd, build
+    build.build()
+    return amrfd.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared()
+    assert len(declared) >= 10
+    for name in declared:
+        assert hasattr(lib, name), name
+    from paper_1407_2052_gb300 import amrfd
+    assert set(amrfd.EXPORTS) <= set(declared)
+
+
+def test_strerror(lib):
+    assert lib.amrfd_strerror(0) == b"ok"
+    assert b"invalid" in lib.amrfd_strerror(1)
+    assert b"non-physical" in lib.amrfd_strerror(4)
+
+
+@pytest.mark.parametrize("bad", ["physics", "ndim", "gamma", "periodic_small", "overlap", "nb", "unpaired_bc"])
+def test_create_rejects_bad_arguments_on_host(lib, bad):
+    """Validation happens before any CUDA call, so this needs no GPU."""
+    from paper_1407_2052_gb300 import amrfd as A
+    from paper_1407_2052_gb300 import workloads as W
+    cfg = A.Config(A.MHD_GLM, 3, A.SSPRK3, 0, 5 / 3, 0.3, 0.18)
+    doms = [W.Domain((8, 8, 8), (0.1,) * 3), W.Domain((8, 8, 8), (0.1,) * 3, offset=9 * 512)]
+    if bad == "physics":
+        cfg.physics = 7
+    elif bad == "ndim":
+        cfg.ndim = 4
+    elif bad == "gamma":
+        cfg.gamma = 1.0
+    elif bad == "periodic_small":
+        doms[0] = W.Domain((2, 8, 8), (0.1,) * 3)
+    elif bad == "overlap":
+        doms[1] = W.Domain((8, 8, 8), (0.1,) * 3, offset=100)
+    elif bad == "nb":
+        doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, nb=(3, 1, 1))
+    elif bad == "unpaired_bc":
+        doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, bc=((A.PERIODIC, A.OUTFLOW),) * 3)
+    h = ctypes.c_void_p()
+    rc = lib.amrfd_create(ctypes.byref(h), ctypes.byref(cfg), A.domains_c(doms), len(doms), None, None)
+    assert rc == A.ERR_INVALID_ARG
+    assert not h.value

@@ -1,0 +1,334 @@
+"""GPU path (C ABI -> CUDA kernels) against the CPU oracle on the same seeded inputs.
+
+Tolerances (per variable, relative to the oracle's magnitude of that variable):
+  smooth data: relative L-infinity <= 1e-12 after one step, <= 1e-9 after 100 steps;
+  shocked data: relative L1 <= 1e-10;
+  splitting speeds of U^n and the CFL time step: bit-identical.
+Each side computes its own time steps where a run spans several steps.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1407_2052_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def A():
+    from paper_1407_2052_gb300 import amrfd
+    return amrfd
+
+
+def rel_linf(a, b):
+    nv = b.shape[0]
+    out = 0.0
+    for v in range(nv):
+        den = np.abs(b[v]).max()
+        num = np.abs(a[v] - b[v]).max()
+        if den == 0.0:
+            if num != 0.0:
+                return np.inf
+            continue
+        out = max(out, num / den)
+    return out
+
+
+def rel_l1(a, b):
+    out = 0.0
+    for v in range(b.shape[0]):
+        den = np.abs(b[v]).sum()
+        num = np.abs(a[v] - b[v]).sum()
+        if den == 0.0:
+            if num != 0.0:
+                return np.inf
+            continue
+        out = max(out, num / den)
+    return out
+
+
+def ocfg(w):
+    return O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+
+
+def odom(d):
+    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb)
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t, shape):
+    torch.cuda.synchronize()
+    return t.cpu().numpy().reshape(shape)
+
+
+def run_gpu(w, nsteps=1, batched=True, fixed_dt=None, solver=None):
+    s = solver or A().Solver.from_workload(w)
+    U = dev(w.U.copy().ravel())
+    dts = []
+    for _ in range(nsteps):
+        dt = s.dt(U) if fixed_dt is None else torch.full((s.ndom,), fixed_dt, dtype=torch.float64, device="cuda")
+        dts.append(dt.clone())
+        (s.step_batched if batched else s.step)(U, dt)
+    assert s.error() == A().OK
+    return s, U, dts
+
+
+def run_oracle(w, nsteps=1, fixed_dt=None):
+    c, d = ocfg(w), odom(w.domains[0])
+    U = w.U.copy()
+    dts = []
+    for _ in range(nsteps):
+        h = O.dt(c, d, U, w.cfl)[0] if fixed_dt is None else fixed_dt
+        dts.append(h)
+        U, fl, al, ch = O.step(c, d, U, h, active=w.active)
+        assert fl == 0
+    return U, dts
+
+
+# --------------------------------------------------------------- single domains
+def test_sod_first_step_dt_alpha_bitwise():
+    w = W.sod(512)
+    s, U, dts = run_gpu(w, 1)
+    c, d = ocfg(w), odom(w.domains[0])
+    h, _ = O.dt(c, d, w.U, w.cfl)
+    assert float(dts[0][0].item()) == h
+    ref, fl, al, ch = O.step(c, d, w.U, h)
+    assert np.array_equal(s.alpha(1)[0, 0, :1], al[0, :1])
+    assert rel_l1(host(U, ref.shape), ref) <= 1e-10
+
+
+def test_sod_to_final_time_shocked():
+    w = W.sod(512)
+    c, d = ocfg(w), odom(w.domains[0])
+    Uo, t, n, fl = O.evolve(c, d, w.U, w.cfl, w.t_end)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        s.step_batched(U, dt)
+        tg += float(dt[0].item())
+        ng += 1
+    assert s.error() == A().OK
+    assert ng == n
+    assert rel_l1(host(U, Uo.shape), Uo) <= 1e-10
+
+
+@pytest.mark.parametrize("integrator", [O.SSPRK54, O.SSPRK3])
+def test_vortex_smooth_one_step(integrator):
+    w = W.vortex2d(64, integrator=integrator)
+    s, U, dts = run_gpu(w, 1)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref) <= 1e-12
+
+
+def test_vortex_smooth_100_steps():
+    w = W.vortex2d(64)
+    s, U, _ = run_gpu(w, 100)
+    ref, _ = run_oracle(w, 100)
+    assert rel_linf(host(U, ref.shape), ref) <= 1e-9
+
+
+def test_vortex_full_size_one_step():
+    """2D MHD vortex at its full 1024^2 size, SSPRK(5,4): element-wise one-step parity."""
+    w = W.vortex2d(1024)
+    s, U, dts = run_gpu(w, 1)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,block", [(32, 16), (24, 8)])
+def test_blast_shocked(n, block):
+    w = W.blast3d(n, block)
+    s, U, dts = run_gpu(w, 5)
+    ref, odts = run_oracle(w, 5)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_l1(host(U, ref.shape), ref) <= 1e-10
+
+
+def _smooth_domain(physics, ndim, n, bc, seed, nb=(1, 1, 1), integrator=O.SSPRK3):
+    """Smooth seeded state on an arbitrary box (test input)."""
+    rng = np.random.default_rng(seed)
+    g = 1.4 if physics == O.EULER else 5 / 3
+    shp = tuple(n[::-1])  # (nz, ny, nx)
+    dx = [0.7 / n[0], 0.9 / max(n[1], 1), 1.1 / max(n[2], 1)]
+    axes = [np.arange(m) + 0.5 for m in n]
+    Z, Y, X = np.meshgrid(axes[2] * dx[2], axes[1] * dx[1], axes[0] * dx[0], indexing="ij")
+
+    def f(a):
+        k = rng.integers(1, 3, 3)
+        return a * np.sin(2 * np.pi * (k[0] * X / (n[0] * dx[0]) + k[1] * Y / (max(n[1], 1) * dx[1])
+                                        + k[2] * Z / (max(n[2], 1) * dx[2])) + rng.uniform(0, 6.28))
+    rho = 1.0 + f(0.2)
+    p = 1.0 + f(0.2)
+    vel = [f(0.3) for _ in range(3)]
+    if physics == O.EULER:
+        U = W.conserved_euler(rho, vel[:ndim], p, g)
+    else:
+        B = [0.5 + f(0.1), f(0.1), f(0.1)]
+        U = W.conserved_mhd(rho, vel, p, B, g)
+    dom = W.Domain(tuple(n), tuple(dx), bc=bc, nb=nb)
+    return W.Workload("smooth", physics, ndim, integrator, g, 0.4, [dom], U,
+                      active=np.ones(nb[0] * nb[1] * nb[2], np.uint8))
+
+
+RAGGED = [
+    (O.EULER, 1, (37, 1, 1), ((O.OUTFLOW, O.OUTFLOW),) * 3),
+    (O.EULER, 2, (37, 29, 1), ((O.OUTFLOW, O.OUTFLOW), (O.PERIODIC, O.PERIODIC), (0, 0))),
+    (O.EULER, 3, (13, 11, 9), ((O.PERIODIC, O.PERIODIC), (O.OUTFLOW, O.OUTFLOW), (O.PERIODIC, O.PERIODIC))),
+    (O.MHD_GLM, 2, (45, 70, 1), ((O.PERIODIC, O.PERIODIC), (O.OUTFLOW, O.OUTFLOW), (0, 0))),
+    (O.MHD_GLM, 3, (20, 12, 10), ((O.OUTFLOW, O.OUTFLOW), (O.PERIODIC, O.PERIODIC), (O.OUTFLOW, O.OUTFLOW))),
+]
+
+
+@pytest.mark.parametrize("case", range(len(RAGGED)))
+@pytest.mark.parametrize("batched", [True, False])
+def test_ragged_boxes_smooth(case, batched):
+    physics, ndim, n, bc = RAGGED[case]
+    w = _smooth_domain(physics, ndim, n, bc, seed=case)
+    s, U, dts = run_gpu(w, 1, batched=batched)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref) <= 1e-12
+
+
+def test_tiles_do_not_change_results():
+    """Every tile shape gives the same bits (faces are computed identically in any segment)."""
+    w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((O.PERIODIC, O.PERIODIC),) * 3, seed=9)
+    base = None
+    for seg, lines, thr in [(32, 32, 288), (16, 8, 96), (64, 16, 160), (8, 1, 32)]:
+        s = A().Solver.from_workload(w)
+        s.set_tile(seg, lines, thr)
+        _, U, _ = run_gpu(w, 2, solver=s)
+        got = host(U, w.U.shape)
+        if base is None:
+            base = got
+        assert np.array_equal(got, base), (seg, lines, thr)
+
+
+def test_multiblock_passive_blocks():
+    w = W.blast3d(16, 8)
+    w.active = np.array([1, 0, 1, 1, 0, 1, 1, 0], np.uint8)
+    for batched in (True, False):
+        s, U, dts = run_gpu(w, 2, batched=batched)
+        ref, odts = run_oracle(w, 2)
+        got = host(U, ref.shape)
+        assert rel_l1(got, ref) <= 1e-10
+        blk = w.U.reshape(9, 2, 8, 2, 8, 2, 8)
+        gb = got.reshape(9, 2, 8, 2, 8, 2, 8)
+        for b in np.flatnonzero(w.active == 0):
+            bz, by, bx = b // 4, (b // 2) % 2, b % 2
+            assert np.array_equal(gb[:, bz, :, by, :, bx], blk[:, bz, :, by, :, bx])
+
+
+# --------------------------------------------------------------- batched blocks
+def test_batched_uneven_blocks_vs_oracle_and_plain():
+    w = W.batched(nblocks=40)
+    s = A().Solver.from_workload(w)
+    U1 = dev(w.U.copy())
+    U2 = dev(w.U.copy())
+    dt = s.dt(U1)
+    s.step_batched(U1, dt)
+    s.step(U2, dt)
+    assert s.error() == A().OK
+    g1, g2 = U1.cpu().numpy(), U2.cpu().numpy()
+    assert np.array_equal(g1, g2)
+    dth = dt.cpu().numpy()
+    c = ocfg(w)
+    for i, dd in enumerate(w.domains):
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        shape = (9,) + tuple(dd.n[::-1])
+        if not w.active[i]:
+            assert np.array_equal(g1[sl], w.U[sl])
+            continue
+        od = odom(dd)
+        h, _ = O.dt(c, od, w.U[sl].reshape(shape), w.cfl)
+        assert h == dth[i]
+        ref, fl, _, _ = O.step(c, od, w.U[sl].reshape(shape), h)
+        assert rel_linf(g1[sl].reshape(shape), ref) <= 1e-12, i
+
+
+def test_batched_global_dt_scope():
+    w = W.batched(nblocks=12)
+    s = A().Solver.from_workload(w, dt_scope=A().DT_GLOBAL)
+    U = dev(w.U.copy())
+    dt = s.dt(U).cpu().numpy()
+    c = ocfg(w)
+    want = min(O.dt(c, odom(dd), w.U[dd.offset:dd.offset + 9 * dd.ncell].reshape((9,) + tuple(dd.n[::-1])),
+                    w.cfl)[0] for i, dd in enumerate(w.domains) if w.active[i])
+    assert np.all(dt == want)
+
+
+def test_set_active_on_device():
+    w = W.batched(nblocks=20)
+    s = A().Solver.from_workload(w)
+    flip = torch.from_numpy(1 - w.active).cuda()
+    s.set_active(flip)
+    U = dev(w.U.copy())
+    dt = s.dt(U)
+    s.step_batched(U, dt)
+    g = U.cpu().numpy()
+    for i, dd in enumerate(w.domains):
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        assert np.array_equal(g[sl], w.U[sl]) == bool(w.active[i])
+
+
+# --------------------------------------------------------------- failure latch
+def test_nonphysical_state_is_flagged_and_cleared():
+    w = W.blast3d(16, 8)
+    U0 = w.U.copy()
+    U0[4, 3, 5, 7] = -1.0  # negative total energy -> negative pressure
+    s = A().Solver.from_workload(w)
+    U = dev(U0.ravel())
+    dt = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
+    s.step_batched(U, dt)
+    assert s.error() == A().ERR_NONPHYSICAL
+    assert s.error() == A().OK
+    c, d = ocfg(w), odom(w.domains[0])
+    _, fl, _, _ = O.step(c, d, U0, 1e-4)
+    assert fl == O.FLAG_NONPHYSICAL
+
+
+# ------------------------------------------------ full-size properties (3D blast)
+def test_blast_full_size_properties():
+    """256^3 in 16^3 blocks (the bench configuration): dt and c_max of U^n bit-identical to
+    the oracle's; totals of rho, m, E, B conserved to roundoff over one step; a periodic
+    shift of the input shifts the output bit for bit (tile and halo handling at full size)."""
+    w = W.blast3d(256, 16)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel().copy())
+    dt = s.dt(U)
+    c, d = ocfg(w), odom(w.domains[0])
+    h, _ = O.dt(c, d, w.U, w.cfl)
+    assert float(dt[0].item()) == h
+    V = U.view(9, -1)
+    tot0 = V[:8].sum(dim=1)
+    mag = V[:8].abs().sum(dim=1)
+    s.step_batched(U, dt)
+    alpha = s.alpha(1)[0, 0]
+    araw, _, _ = O.speeds(c, d, w.U)
+    assert np.array_equal(alpha, araw)
+    tot1 = V[:8].sum(dim=1)
+    assert torch.all((tot1 - tot0).abs() <= 1e-12 * mag)
+    shift = (3, 7, 5)
+    U2 = dev(np.roll(w.U, shift, axis=(1, 2, 3)).ravel().copy())
+    s.step_batched(U2, dt)
+    a = U.view(9, 256, 256, 256)
+    b = U2.view(9, 256, 256, 256)
+    assert torch.equal(torch.roll(a, shift, dims=(1, 2, 3)), b)
+    assert s.error() == A().OK
