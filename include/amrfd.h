@@ -130,6 +130,17 @@ int amrfd_set_tile(amrfd_handle *h, int seg, int lines, int threads);
 /* Read back the current tile. */
 int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);
 
+/* Kernel timing for measurement. After amrfd_timing_begin(h, capacity), every
+   kernel that amrfd_dt, amrfd_step and amrfd_step_batched launch is bracketed by
+   a pair of CUDA events recorded on the launching stream (amrfd_step_batched
+   then issues its persistent launches directly instead of replaying the graph;
+   the kernels are the same). At most `capacity` launches are recorded.
+   amrfd_timing_end synchronises `stream`, writes per kernel kind
+   (0 speeds, 1 flux pass, 2 stage combination, 3 time step) the summed elapsed
+   milliseconds and the launch counts, and stops timing. */
+int amrfd_timing_begin(amrfd_handle *h, int capacity);
+int amrfd_timing_end(amrfd_handle *h, double ms[4], int counts[4], void *stream);
+
 /* Per-stage splitting speeds of the last step, raw (before raising to c_h):
    out[stage][domain][3], host memory, `nstage` = stages to copy. Synchronises. */
 int amrfd_get_alpha(amrfd_handle *h, double *out, int nstage, void *stream);

@@ -21,7 +21,7 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
 
 EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
-           "amrfd_get_error", "amrfd_destroy", "amrfd_strerror")
+           "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end")
 
 
 class Config(ctypes.Structure):
@@ -64,6 +64,8 @@ def load():
     L.amrfd_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.amrfd_get_alpha.argtypes = [vp, vp, i, vp]
     L.amrfd_get_error.argtypes = [vp, vp]
+    L.amrfd_timing_begin.argtypes = [vp, i]
+    L.amrfd_timing_end.argtypes = [vp, vp, vp, vp]
     L.amrfd_destroy.argtypes = [vp]
     L.amrfd_destroy.restype = None
     L.amrfd_strerror.argtypes = [i]
@@ -202,6 +204,19 @@ class Solver:
         _check(load().amrfd_get_alpha(self._h, out.ctypes.data_as(ctypes.c_void_p), nstage, _stream(stream)),
                "amrfd_get_alpha")
         return out
+
+    KINDS = ("speeds", "flux", "combine", "dt")
+
+    def timing_begin(self, capacity):
+        _check(load().amrfd_timing_begin(self._h, int(capacity)), "amrfd_timing_begin")
+
+    def timing_end(self, stream=None):
+        """{kind: (total_ms, launches)} for the launches since timing_begin."""
+        ms = np.zeros(4)
+        cnt = np.zeros(4, dtype=np.int32)
+        _check(load().amrfd_timing_end(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+                                       cnt.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "amrfd_timing_end")
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
 
     def error(self, stream=None):
         return load().amrfd_get_error(self._h, _stream(stream))

@@ -92,6 +92,11 @@ struct amrfd_handle {
   unsigned* d_err = nullptr;
   size_t nelem = 0;                 // elements of one state-shaped buffer
   cudaStream_t cap = nullptr;       // private stream for graph capture
+  // kernel timing (measurement mode)
+  bool timing = false;
+  std::vector<cudaEvent_t> tev;     // 2 per recorded launch
+  std::vector<int> tkind;
+  int tused = 0;
   std::map<std::pair<const void*, const void*>, Graph> graphs;
 };
 
@@ -231,6 +236,25 @@ int default_threads(int nv, int lines) {
 
 unsigned long long* slot(amrfd_handle* h, int k) { return h->d_slot + (size_t)k * h->ndom * 4; }
 
+enum { K_SPEEDS = 0, K_FLUX = 1, K_COMBINE = 2, K_DT = 3 };
+
+// Bracket one launch with an event pair when timing is on.
+struct Tick {
+  amrfd_handle* h;
+  cudaStream_t s;
+  int slot_ = -1;
+  Tick(amrfd_handle* h_, int kind, cudaStream_t s_) : h(h_), s(s_) {
+    if (h->timing && h->tused < (int)h->tkind.size()) {
+      slot_ = h->tused++;
+      h->tkind[slot_] = kind;
+      cudaEventRecord(h->tev[2 * slot_], s);
+    }
+  }
+  ~Tick() {
+    if (slot_ >= 0) cudaEventRecord(h->tev[2 * slot_ + 1], s);
+  }
+};
+
 FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int stage_in) {
   FluxParams p{};
   p.doms = h->d_dom;
@@ -299,6 +323,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
     SpeedParams p = speed_params(h, U, 0, 0);
     if (batched) {
       p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
+      Tick tk(h, K_SPEEDS, s);
       CK(launch_speeds(ph, nv, p, cgrid, 256, s));
     } else {
       for (int d = 0; d < h->ndom; d++) {
@@ -307,6 +332,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
         for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++) any |= h->active_h[h->hdom[d].block0 + b] != 0;
         if (!any) continue;
         p.items = h->d_call; p.item0 = h->dom_cbeg[d]; p.nitems = h->dom_cend[d] - h->dom_cbeg[d];
+        Tick tk(h, K_SPEEDS, s);
         CK(launch_speeds(ph, nv, p, p.nitems, 256, s));
       }
     }
@@ -317,9 +343,15 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
     CombParams cp = comb_params(h, U, dt, i);
     if (batched) {
       fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
-      CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+      {
+        Tick tk(h, K_FLUX, s);
+        CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+      }
       cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
-      CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+      {
+        Tick tk(h, K_COMBINE, s);
+        CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+      }
     } else {
       std::vector<int> live;
       for (int d = 0; d < h->ndom; d++) {
@@ -332,10 +364,12 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
       for (int d : live) {
         fp.items = h->d_fall; fp.item0 = h->dom_fbeg[d]; fp.nitems = h->dom_fend[d] - h->dom_fbeg[d];
         fp.counter = nullptr;
+        Tick tk(h, K_FLUX, s);
         CK(launch_flux(ph, nv, fp, std::min(fp.nitems, h->flux_grid), h->threads, h->flux_smem, s));
       }
       for (int d : live) {
         cp.items = h->d_call; cp.item0 = h->dom_cbeg[d]; cp.nitems = h->dom_cend[d] - h->dom_cbeg[d];
+        Tick tk(h, K_COMBINE, s);
         CK(launch_combine(ph, nv, cp, cp.nitems, 256, s));
       }
     }
@@ -479,7 +513,10 @@ int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double 
   SpeedParams p = speed_params(h, U, kSlotDt, 1);
   p.items = h->d_cact;
   p.nitems_dev = h->d_counts + 1;
-  CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+  {
+    Tick tk(h, K_SPEEDS, s);
+    CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+  }
   DtParams q{};
   q.doms = h->d_dom;
   q.slot = sl;
@@ -491,6 +528,7 @@ int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double 
   q.glm = h->cfg.physics == AMRFD_MHD_GLM;
   q.ndim = h->cfg.ndim;
   q.global_min = h->cfg.dt_scope == AMRFD_DT_GLOBAL;
+  Tick tk(h, K_DT, s);
   CK(launch_dt(q, s));
   return AMRFD_OK;
 }
@@ -503,6 +541,7 @@ int amrfd_step(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
 int amrfd_step_batched(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  if (h->timing) return enqueue_step(h, U, dt_dev, s, true);
   auto key = std::make_pair((const void*)U, (const void*)dt_dev);
   auto itg = h->graphs.find(key);
   if (itg == h->graphs.end()) {
@@ -602,6 +641,35 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
   return AMRFD_OK;
 }
 
+int amrfd_timing_begin(amrfd_handle* h, int capacity) {
+  if (!h || capacity < 1) return AMRFD_ERR_INVALID_ARG;
+  for (auto e : h->tev) cudaEventDestroy(e);
+  h->tev.assign(2 * (size_t)capacity, nullptr);
+  h->tkind.assign(capacity, 0);
+  for (auto& e : h->tev) CK(cudaEventCreate(&e));
+  h->tused = 0;
+  h->timing = true;
+  return AMRFD_OK;
+}
+
+int amrfd_timing_end(amrfd_handle* h, double ms[4], int counts[4], void* stream) {
+  if (!h || !ms || !counts) return AMRFD_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  for (int k = 0; k < 4; k++) { ms[k] = 0.0; counts[k] = 0; }
+  for (int i = 0; i < h->tused; i++) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, h->tev[2 * i], h->tev[2 * i + 1]));
+    ms[h->tkind[i]] += t;
+    counts[h->tkind[i]]++;
+  }
+  h->timing = false;
+  for (auto e : h->tev) cudaEventDestroy(e);
+  h->tev.clear();
+  h->tkind.clear();
+  h->tused = 0;
+  return AMRFD_OK;
+}
+
 int amrfd_get_alpha(amrfd_handle* h, double* out, int nstage, void* stream) {
   if (!h || !out || nstage < 1 || nstage > kNumSlots) return AMRFD_ERR_INVALID_ARG;
   std::vector<unsigned long long> tmp((size_t)nstage * h->ndom * 4);
@@ -640,6 +708,7 @@ void amrfd_destroy(amrfd_handle* h) {
   for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
   cudaFree(h->d_slot); cudaFree(h->d_err);
   if (h->cap) cudaStreamDestroy(h->cap);
+  for (auto e : h->tev) cudaEventDestroy(e);
   delete h;
 }
 

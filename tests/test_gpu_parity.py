@@ -1,6 +1,10 @@
 """GPU path (C ABI -> CUDA kernels) against the CPU oracle on the same seeded inputs.
 
-Tolerances (per variable, relative to the oracle's magnitude of that variable):
+Errors are per variable, relative to the oracle's magnitude of that variable,
+with the denominator floored at 1e-8 of the largest magnitude in the state, so
+that a field that is zero up to rounding (psi of a divergence-free field, the
+out-of-plane components of planar data) is compared at the state's scale.
+Tolerances:
   smooth data: relative L-infinity <= 1e-12 after one step, <= 1e-9 after 100 steps;
   shocked data: relative L1 <= 1e-10;
   splitting speeds of U^n and the CFL time step: bit-identical.
@@ -30,30 +34,26 @@ def A():
     return amrfd
 
 
+FLOOR = 1e-8
+
+
 def rel_linf(a, b):
     nv = b.shape[0]
+    top = max(np.abs(b[v]).max() for v in range(nv))
     out = 0.0
     for v in range(nv):
-        den = np.abs(b[v]).max()
-        num = np.abs(a[v] - b[v]).max()
-        if den == 0.0:
-            if num != 0.0:
-                return np.inf
-            continue
-        out = max(out, num / den)
+        den = max(np.abs(b[v]).max(), FLOOR * top)
+        out = max(out, np.abs(a[v] - b[v]).max() / den)
     return out
 
 
 def rel_l1(a, b):
+    nv = b.shape[0]
+    top = max(np.abs(b[v]).sum() for v in range(nv))
     out = 0.0
-    for v in range(b.shape[0]):
-        den = np.abs(b[v]).sum()
-        num = np.abs(a[v] - b[v]).sum()
-        if den == 0.0:
-            if num != 0.0:
-                return np.inf
-            continue
-        out = max(out, num / den)
+    for v in range(nv):
+        den = max(np.abs(b[v]).sum(), FLOOR * top)
+        out = max(out, np.abs(a[v] - b[v]).sum() / den)
     return out
 
 
