@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Throughput of the FP64 FD-MP5 update on GB300 (one JSON line on stdout).
+
+Workload (the configuration the metric is quoted on): 3D ideal MHD+GLM blast,
+256^3 cells as 16^3 blocks, gamma 5/3, periodic, SSPRK3, CFL 0.3, seeded
+1e-3 density noise. One step = the CFL time step plus one full SSPRK3 step
+(speeds, 3 x (flux pass + stage combination)); metric = cell-updates/s, one
+cell-update being one full step of one active interior cell.
+
+Arms:
+  default           this library (C ABI -> CUDA kernels), N ranks = N independent
+                    replicas of the workload (weak scaling, no collective).
+  --impl reference  the CPU oracle (oracle/, single-threaded C, -O2), timed on the
+                    host on a bounded sample (a 64^3 blast domain per step).
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_BLAST, BLOCK = 256, 16
+NV = 9
+# Algorithmic HBM bytes per cell-update (SSPRK3, nv = 9): stage reads/writes of
+# U^n, U^(k) and the output, (2 + 3 + 3) * nv * 8 = 64 nv = 576 bytes.
+BYTES_PER_CELL_UPDATE = 64 * NV
+# Minimal HBM bytes of one flux pass per cell: read U^(k) (nv doubles) and write
+# the three per-direction residuals (3 nv doubles).
+FLUX_BYTES_PER_CELL = 4 * NV * 8
+# FP64 operations of one flux pass per cell and direction, counted by ncu
+# (DADD + DMUL + 2 DFMA per executed thread instruction) on this workload; see
+# profiles/flux_kernel_blast3d.md. None until measured.
+FLUX_FLOPS_PER_CELL_DIR = None
+FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (profiling recipe table)
+
+
+def _env_int(k, d):
+    try:
+        return int(os.environ.get(k, d))
+    except ValueError:
+        return d
+
+
+def clocks_sampler(path):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        f = open(path, "w")
+        return subprocess.Popen(cmd, stdout=f, stderr=subprocess.DEVNULL), f
+    except (OSError, FileNotFoundError):
+        return None, None
+
+
+def clocks_summary(path, gpu_index):
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    try:
+        for line in open(path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9 or parts[0] != str(gpu_index):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+    except OSError:
+        pass
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+    sm.sort()
+    return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(cells_side=128, block=16):
+    """The oracle as it stands: one SSPRK3 step of an n^3 blast on one host core."""
+    import oracle as O
+    from paper_1407_2052_gb300 import workloads as W
+    w = W.blast3d(cells_side, block)
+    d0 = w.domains[0]
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    od = O.dom(d0.n, d0.dx, bc=[list(b) for b in d0.bc], nb=d0.nb)
+    h, _ = O.dt(c, od, w.U, w.cfl)
+    t0 = time.perf_counter()
+    h, _ = O.dt(c, od, w.U, w.cfl)
+    O.step(c, od, w.U, h)
+    el = time.perf_counter() - t0
+    return {"value": cells_side ** 3 / el, "unit": "cell-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "one CFL dt + one SSPRK3 step of the %d^3 blast (%d^3 blocks), %.1f s" % (cells_side, block, el)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_1407_2052_gb300 import workloads as W
+    n = 64
+    w = W.blast3d(n, BLOCK)
+    d0 = w.domains[0]
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    od = O.dom(d0.n, d0.dx, bc=[list(b) for b in d0.bc], nb=d0.nb)
+    U = w.U.copy()
+    for _ in range(args.warmup):
+        h, _ = O.dt(c, od, U, w.cfl)
+        U, _, _, _ = O.step(c, od, U, h)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        h, _ = O.dt(c, od, U, w.cfl)
+        U, _, _, _ = O.step(c, od, U, h)
+    el = time.perf_counter() - t0
+    val = n ** 3 * args.steps / el
+    sample = "%d steps of the %d^3 blast (%d^3 blocks) on one host core" % (args.steps, n, BLOCK)
+    out = {"metric": "3D MHD FD-MP5 cell-updates/s (FP64)", "value": val, "unit": "cell-updates/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": "blast3d MHD+GLM SSPRK3 (oracle sample %d^3 of 256^3)" % n, "cells": n ** 3},
+           "cpu_baseline": {"value": val, "unit": "cell-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "e2e": {"value": val, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    import __graft_entry__ as g
+    from paper_1407_2052_gb300 import amrfd as A
+    from paper_1407_2052_gb300 import workloads as W
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    g.build()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    w = W.blast3d(N_BLAST, BLOCK)
+    ncell = N_BLAST ** 3
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel()).cuda()
+    U = U0.clone()
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    del w
+
+    def one_step():
+        s.dt(U, out=dt)
+        s.step_batched(U, dt)
+
+    for _ in range(args.warmup):
+        one_step()
+    barrier()
+
+    # ---- timed region: K steps, CUDA events around every kernel (same stream)
+    gpu_index = local_rank
+    try:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            gpu_index = int(vis.split(",")[local_rank])
+    except ValueError:
+        pass
+    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_bench_rank%d.csv" % rank) if os.path.isdir(
+        os.path.join(ROOT, "gpurun_out")) else "/tmp/amrfd_clocks_rank%d.csv" % rank
+    proc, fh = clocks_sampler(clk_path)
+    s.timing_begin(16 * args.steps + 16)
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    barrier()
+    kt = s.timing_end()
+    ms = e0.elapsed_time(e1)
+    if proc is not None:
+        proc.terminate()
+        proc.wait()
+        fh.close()
+    clocks = clocks_summary(clk_path, gpu_index)
+    assert s.error() == A.OK
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = ncell * args.steps * world / (ms_max * 1e-3)
+    launches = sum(v[1] for v in kt.values())
+
+    # ---- the same K steps replayed from the captured CUDA graph
+    U.copy_(U0)
+    for _ in range(2):
+        one_step()
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    barrier()
+    graph_ms = e0.elapsed_time(e1) / args.steps
+
+    # ---- end to end through the public API with host buffers (pinned)
+    hU = U0.cpu().pin_memory()
+    hout = torch.empty_like(hU).pin_memory()
+    nbytes = hU.numel() * 8
+    for _ in range(2):
+        U.copy_(hU, non_blocking=True)
+        one_step()
+        hout.copy_(U, non_blocking=True)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        U.copy_(hU, non_blocking=True)
+        one_step()
+        hout.copy_(U, non_blocking=True)
+    e1.record(stream)
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = ncell * args.steps * world / (float(t.item()) * 1e-3)
+
+    flux_ms, flux_n = kt["flux"]
+    flux_avg_s = flux_ms / max(flux_n, 1) * 1e-3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    if FLUX_FLOPS_PER_CELL_DIR:
+        achieved = FLUX_FLOPS_PER_CELL_DIR * 3 * ncell / flux_avg_s / 1e12
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None, "kernel": "flux_kernel",
+                "peak_source": "FP64 nominal of the profiling recipe"}
+    else:
+        roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": None, "peak": FP64_PEAK_TFLOPS_NOMINAL,
+                "frac": None, "traffic": None, "kernel": "flux_kernel"}
+    flux_gbs = FLUX_BYTES_PER_CELL * ncell / flux_avg_s / 1e9
+    out = {
+        "metric": "3D MHD FD-MP5 cell-updates/s (FP64)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "blast3d: 3D ideal MHD+GLM blast, 256^3 cells in 16^3 blocks, SSPRK3, CFL 0.3",
+                   "cells": ncell, "integrator": "SSPRK3", "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (1.2 GB state)", "tile": list(s.get_tile())},
+        "gpu_launches": launches,
+        "kernel_ms": {k: {"total": v[0], "launches": v[1]} for k, v in kt.items()},
+        "graph_ms_per_step": graph_ms,
+        "roofline": roof,
+        "roofline_hbm": {"bound": "hbm", "unit": "GB/s",
+                         "achieved_step": value / world * BYTES_PER_CELL_UPDATE / 1e9,
+                         "achieved_flux": flux_gbs, "peak": hbm_peak,
+                         "frac_step": value / world * BYTES_PER_CELL_UPDATE / 1e9 / hbm_peak,
+                         "frac_flux": flux_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+        "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "clocks": clocks,
+    }
+    s.close()
+    del U, U0
+    torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline()
+    if dist is not None:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -120,51 +120,64 @@ def blast3d(n=256, block=16, seed_index=2):
                     active=np.ones(nb ** 3, np.uint8))
 
 
-def _fourier_field(rng, shape_cells, dx, nmodes, amp, kset):
-    """amp * sum_j c_j sin(2 pi k_j . x / L + phi_j) on a periodic box of edge L = n dx."""
-    nz, ny, nx = shape_cells
-    L = np.array([nx, ny, nz]) * dx
-    xs = [(np.arange(m) + 0.5) * dx for m in (nx, ny, nz)]
-    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
-    out = np.zeros(shape_cells)
-    for _ in range(nmodes):
-        k = kset[rng.integers(len(kset))]
-        c = rng.uniform(-1.0, 1.0) / nmodes
-        ph = rng.uniform(0.0, 2 * np.pi)
-        out += c * np.sin(2 * np.pi * (k[0] * X / L[0] + k[1] * Y / L[1] + k[2] * Z / L[2]) + ph)
-    return amp * out
+def _kset3():
+    return np.array([(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1)
+                     if (a, b, c) != (0, 0, 0)])
 
 
-def batched(nblocks=20000, sizes=(8, 12, 16, 24, 32), passive_frac=0.3, seed_index=3, max_cells=None):
+def batched(nblocks=20000, sizes=(8, 12, 16, 24, 32), passive_frac=0.3, seed_index=3):
     """Independent periodic 3D MHD+GLM blocks of uneven sizes, each its own domain.
 
-    Interior edge drawn per block from `sizes`; dx log-uniform in [1e-3, 1e-1];
+    Interior edge m drawn per block from `sizes`; dx log-uniform in [1e-3, 1e-1];
     background rho = 1, p = 1, v = 0, B = (0.5, 0, 0); rho and p get (1 + delta),
-    each velocity component + delta, delta a sum of 8 Fourier modes of amplitude
-    0.05 with k in {-1,0,1}^3 minus 0; B uniform; `passive_frac` flagged passive."""
+    each velocity component + delta, where every delta is a fresh draw of
+        0.05 * sum_{j=1..8} c_j sin(2 pi k_j . x / L + phi_j),
+    k_j uniform in {-1,0,1}^3 minus 0, c_j ~ U[-1,1]/8, phi_j ~ U[0, 2 pi), L = m dx
+    (so the phase only depends on the cell index); B uniform; a seeded Bernoulli
+    draw flags `passive_frac` of the blocks passive. Blocks are stored one after
+    another (domain offsets), each as U[v][z][y][x]."""
     rng = np.random.default_rng(SEED0 + seed_index)
-    kset = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1) if (a, b, c) != (0, 0, 0)]
+    ks = _kset3()
     edges = rng.choice(np.asarray(sizes), size=nblocks)
     dxs = np.exp(rng.uniform(np.log(1e-3), np.log(1e-1), size=nblocks))
     active = (rng.random(nblocks) >= passive_frac).astype(np.uint8)
-    doms, chunks, off = [], [], 0
-    for i in range(nblocks):
-        m = int(edges[i])
-        if max_cells is not None and off // 9 + m ** 3 > max_cells:
-            break
-        shp = (m, m, m)
-        f = lambda: _fourier_field(rng, shp, dxs[i], 8, 0.05, kset)
-        rho = 1.0 * (1.0 + f())
-        p = 1.0 * (1.0 + f())
-        vel = [f(), f(), f()]
-        zero = np.zeros(shp)
-        U = conserved_mhd(rho, vel, p, [zero + 0.5, zero, zero], 5.0 / 3.0)
-        doms.append(Domain((m, m, m), (dxs[i],) * 3, offset=off))
-        chunks.append(U.ravel())
-        off += U.size
-    Uflat = np.concatenate(chunks)
-    return Workload("batched3d", MHD_GLM, 3, SSPRK3, 5.0 / 3.0, 0.4, doms, Uflat,
-                    active=active[:len(doms)].copy())
+    nf, nm = 5, 8  # perturbed fields (rho, p, vx, vy, vz), modes per field
+    kidx = rng.integers(len(ks), size=(nblocks, nf, nm))
+    cj = rng.uniform(-1.0, 1.0, size=(nblocks, nf, nm)) / nm
+    ph = rng.uniform(0.0, 2 * np.pi, size=(nblocks, nf, nm))
+    # sin(theta_k + phi) = sin(theta_k) cos(phi) + cos(theta_k) sin(phi): per block and field the
+    # perturbation is a weighted sum of the 2 x 26 basis fields sin/cos(2 pi k . (i + 1/2) / m)
+    wts = np.zeros((nblocks, nf, 2 * len(ks)))
+    rows = np.arange(nblocks)[:, None, None]
+    fld = np.arange(nf)[None, :, None]
+    np.add.at(wts, (rows, fld, kidx), cj * np.cos(ph))
+    np.add.at(wts, (rows, fld, kidx + len(ks)), cj * np.sin(ph))
+    offs = np.zeros(nblocks, dtype=np.int64)
+    ncell = edges.astype(np.int64) ** 3
+    offs[1:] = np.cumsum(9 * ncell)[:-1]
+    U = np.empty(int(9 * ncell.sum()))
+    for m in sizes:
+        sel = np.flatnonzero(edges == m)
+        if sel.size == 0:
+            continue
+        t = 2 * np.pi * (np.arange(m) + 0.5) / m
+        Z, Y, X = np.meshgrid(t, t, t, indexing="ij")
+        arg = ks[:, 0, None] * X.ravel()[None] + ks[:, 1, None] * Y.ravel()[None] + ks[:, 2, None] * Z.ravel()[None]
+        basis = np.concatenate([np.sin(arg), np.cos(arg)])  # (52, m^3)
+        for c0 in range(0, sel.size, 512):
+            part = sel[c0:c0 + 512]
+            delta = 0.05 * (wts[part].reshape(-1, basis.shape[0]) @ basis).reshape(part.size, nf, m ** 3)
+            rho = 1.0 + delta[:, 0]
+            p = 1.0 + delta[:, 1]
+            vel = [delta[:, 2], delta[:, 3], delta[:, 4]]
+            zero = np.zeros_like(rho)
+            blk = conserved_mhd(rho, vel, p, [zero + 0.5, zero, zero], 5.0 / 3.0)  # (9, nb, m^3)
+            blk = np.ascontiguousarray(blk.transpose(1, 0, 2))
+            for q, b in enumerate(part):
+                U[offs[b]:offs[b] + 9 * m ** 3] = blk[q].ravel()
+    doms = [Domain((int(m), int(m), int(m)), (float(dxs[i]),) * 3, offset=int(offs[i]))
+            for i, m in enumerate(edges)]
+    return Workload("batched3d", MHD_GLM, 3, SSPRK3, 5.0 / 3.0, 0.4, doms, U, active=active)
 
 
 def adjoint2d(n=512, seed_index=4, nmodes=16, amp=0.02):
