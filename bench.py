@@ -150,8 +150,9 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         torch.cuda.synchronize()
 
-    w = W.blast3d(N_BLAST, BLOCK)
-    ncell = N_BLAST ** 3
+    nside = args.n
+    w = W.blast3d(nside, BLOCK)
+    ncell = nside ** 3
     s = A.Solver.from_workload(w)
     U0 = torch.from_numpy(w.U.ravel()).cuda()
     U = U0.clone()
@@ -258,9 +259,9 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "blast3d: 3D ideal MHD+GLM blast, 256^3 cells in 16^3 blocks, SSPRK3, CFL 0.3",
+        "config": {"workload": "blast3d: 3D ideal MHD+GLM blast, %d^3 cells in 16^3 blocks, SSPRK3, CFL 0.3" % nside,
                    "cells": ncell, "integrator": "SSPRK3", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (1.2 GB state)", "tile": list(s.get_tile())},
+                   "l2": "inputs larger than L2 (%.2f GB state)" % (ncell * NV * 8 / 1e9), "tile": list(s.get_tile())},
         "gpu_launches": launches,
         "kernel_ms": {k: {"total": v[0], "launches": v[1]} for k, v in kt.items()},
         "graph_ms_per_step": graph_ms,
@@ -293,6 +294,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n", type=int, default=N_BLAST, help="cells per side of the blast (profiling of small cases)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
