@@ -54,33 +54,89 @@ __device__ __forceinline__ double imedian(double x, double y, double z) {
 // x <= c for a finite non-negative constant c (NaN compares false)
 __device__ __forceinline__ bool ile_pos(double x, double c) { return okey(x) <= dbits(c); }
 
+// x * 2^K exactly. The exponent field is adjusted on the integer pipe when the
+// result stays a normal number (or x is +-0); otherwise one FP64 multiply.
+template <int K>
+__device__ __forceinline__ double dscale(double x) {
+  const long long b = dbits(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  const bool zero = (b & 0x7fffffffffffffffLL) == 0;
+  const bool ok = (e >= 1 + (K < 0 ? -K : 0)) && (e <= 2046 - (K > 0 ? K : 0));
+  if (zero) return x;
+  if (ok) return bitsd(b + ((long long)K << 52));
+  return x * (K >= 0 ? (double)(1LL << (K >= 0 ? K : 0)) : 1.0 / (double)(1LL << (K < 0 ? -K : 0)));
+}
+
+__device__ __forceinline__ double dneg(double x) { return bitsd(dbits(x) ^ (long long)0x8000000000000000ULL); }
+
 // ---------------------------------------------------------- MP5 in difference form
-// Value at the face relative to the centre cell f_i (Suresh & Huynh 1997):
-//   Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1},
-//   Mp, Mm = the minmod4 curvatures at i+1/2 and i-1/2.
-// f_or - f_i = (2 f_{i-2} - 13 f_{i-1} + 47 f_i + 27 f_{i+1} - 3 f_{i+2})/60 - f_i
-//            = (11 D0 - 2 Dm + 24 D1 - 3 Dp)/60.
-// The bounds f_ul, f_md, f_lc, f_min, f_max are shifted by -f_i the same way.
-// eps4 is the MP acceptance threshold in the units of the reconstructed values.
-__device__ __forceinline__ double mp5_rel(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
-                                          double eps4) {
-  const double c11 = 11.0 / 60.0, c2 = 2.0 / 60.0, c24 = 24.0 / 60.0, c3 = 3.0 / 60.0;
-  double X = fma(c24, D1, fma(-c2, Dm, c11 * D0));
-  X = fma(-c3, Dp, X);
-  double ul = 4.0 * D0;                 // f_ul - f_i = alpha (f_i - f_{i-1}), alpha = 4
-  double mp = iminmod(D1, ul);          // f_mp - f_i
-  double chk = X * (X - mp);
-  if (ile_pos(chk, eps4)) return X;
-  double md = 0.5 * (D1 - Mp);          // f_md - f_i = (f_av - f_i) - Mp/2
-  double lc = fma(4.0 / 3.0, Mm, 0.5 * D0);  // f_lc - f_i
-  double fmin = imax(imin(imin(0.0, D1), md), imin(imin(0.0, ul), lc));
-  double fmax = imin(imax(imax(0.0, D1), md), imax(imax(0.0, ul), lc));
+// MP5 (Suresh & Huynh 1997) at face i+1/2 from (f_{i-2}, ..., f_{i+2}), written in
+// differences Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1}
+// and the curvature-limited second differences Mp (at i+1/2) and Mm (at i-1/2):
+//   f_or - f_i = (11 D0 - 2 Dm + 24 D1 - 3 Dp)/60,  f_mp - f_i = minmod(D1, 4 D0),
+//   f_ul - f_i = 4 D0,  f_md - f_i = D1/2 - Mp/2,  f_lc - f_i = D0/2 + 4 Mm/3,
+// with the acceptance test (f_or - f_i)(f_or - f_mp) <= eps and otherwise
+// median(f_or, f_min, f_max). Everything is carried at twice its value, which makes
+// the halvings and the factor 4 exact exponent shifts; the result is
+// 2 (f_face - f_i). NEG evaluates the mirror-image stencil whose differences are
+// the negatives of the ones passed in (the right-biased reconstruction).
+// eps16 = 16 eps: 4 eps for values doubled twice (splitting without the 1/2, and here).
+template <bool NEG>
+__device__ __forceinline__ double mp5_rel2(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
+                                           double eps16) {
+  constexpr double sg = NEG ? -1.0 : 1.0;
+  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
+                   c6 = sg * (6.0 / 60.0);
+  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));  // 2 (f_or - f_i)
+  X = fma(-c6, Dp, X);
+  const double d0 = NEG ? dneg(D0) : D0;
+  const double d1 = NEG ? dneg(D1) : D1;
+  const double ul = dscale<3>(d0);     // 2 (f_ul - f_i)
+  const double d1x2 = dscale<1>(d1);   // 2 (f_{i+1} - f_i)
+  const double mp = iminmod(d1x2, ul);  // 2 (f_mp - f_i)
+  const double chk = X * (X - mp);
+  if (ile_pos(chk, eps16)) return X;
+  const double md = d1 - Mp;                  // 2 (f_md - f_i)
+  const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
+  const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
+  const double fmax = imin(imax(imax(0.0, d1x2), md), imax(imax(0.0, ul), lc));
   return imedian(X, fmin, fmax);
 }
 
-// curvature-limited second difference at a face from the curvatures of its two cells
+// minmod4(4 ka - kb, 4 kb - ka, ka, kb): the curvature-limited second difference at
+// a face from the curvatures of its two cells. Zero unless ka, kb share a sign; then,
+// with s the smaller and l the larger in magnitude, 4 l - s never wins and the
+// result is 4 s - l if it keeps the sign and is smaller than s, else s (one FMA).
 __device__ __forceinline__ double dm4(double ka, double kb) {
-  return iminmod4(fma(4.0, ka, -kb), fma(4.0, kb, -ka), ka, kb);
+  const long long a = dbits(ka), b = dbits(kb);
+  const long long M = 0x7fffffffffffffffLL;
+  const long long ma = a & M, mb = b & M;
+  if (((a ^ b) < 0) | (ma == 0) | (mb == 0)) return 0.0;
+  const bool as = ma < mb;
+  const double sm = as ? ka : kb, lg = as ? kb : ka;
+  const long long ms = as ? ma : mb;
+  const double t = fma(4.0, sm, -lg);
+  const long long bt = dbits(t);
+  if (((bt ^ dbits(sm)) < 0) | ((bt & M) == 0)) return 0.0;
+  return ((bt & M) < ms) ? t : sm;
+}
+
+// Reciprocal of a positive normal double: FP32 seed from the leading bits (integer
+// conversion, MUFU reciprocal) and two Newton steps y <- y + y (1 - x y) in FP64.
+__device__ __forceinline__ double frcp(double x) {
+  const long long b = dbits(x);
+  const int e = (int)((b >> 52) & 0x7ff);
+  if (e < 1023 - 120 || e > 1023 + 120) return 1.0 / x;
+  const unsigned fb = ((unsigned)((unsigned long long)b >> 32) & 0x80000000u) | ((unsigned)(e - 1023 + 127) << 23) |
+                      (unsigned)((b >> 29) & 0x7fffff);
+  const unsigned yb = __float_as_uint(__frcp_rn(__uint_as_float(fb)));
+  const long long db = ((long long)(yb & 0x80000000u) << 32) | ((long long)(((yb >> 23) & 0xff) - 127 + 1023) << 52) |
+                       ((long long)(yb & 0x7fffff) << 29);
+  double y = bitsd(db);
+  double r = fma(-x, y, 1.0);
+  y = fma(y, r, y);
+  r = fma(-x, y, 1.0);
+  return fma(y, r, y);
 }
 
 // ------------------------------------------------- exact characteristic speeds
@@ -135,7 +191,7 @@ __device__ __forceinline__ void split_flux(const double* u, double gm1, double a
                                            double* gp, double* gm) {
   double f[NV];
   const double rho = u[0];
-  const double ir = 1.0 / rho;
+  const double ir = frcp(rho);
   if (PHYS == PH_EULER) {
     constexpr int nm = NV - 2;
     double v[nm];

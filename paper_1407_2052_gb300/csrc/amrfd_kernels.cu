@@ -144,41 +144,42 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 }
 
 // Sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of the
-// line's extended index (cell j = k-1 left of face k), then the flux difference of
-// cells j = 3..slen+2 written back over the consumed part of the G^+ line.
-__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double hdx, double eps4) {
+// line's extended index (cell j = k-1 left of face k), then the flux difference
+// Fsum_{k-1} - Fsum_k of cells j = 3..slen+2 written back over the consumed part of
+// the G^+ line (the factor 1/(2 dx) is applied by the stage combination).
+__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double eps16) {
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
-  double Pk1 = Pd2 - Pd1, Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
-  double PM2 = dm4(Pk1, Pk2), PM3 = dm4(Pk2, Pk3);
+  double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
+  double PM2 = dm4(Pd2 - Pd1, Pk2), PM3 = dm4(Pk2, Pk3);
   double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
-  double Mk2 = Md3 - Md2, Mk3 = Md4 - Md3, Mk4 = Md5 - Md4;
-  double MM3 = dm4(Mk2, Mk3), MM4 = dm4(Mk3, Mk4);
+  double Mk3 = Md4 - Md3, Mk4 = Md5 - Md4;
+  double MM3 = dm4(Md3 - Md2, Mk3), MM4 = dm4(Mk3, Mk4);
   double cp = g[2], cm = h[3];
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     // left-biased reconstruction of G^+ centred on cell k-1
-    const double Yp = mp5_rel(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps4);
+    const double Yp = mp5_rel2<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16);
     // right-biased reconstruction of G^- centred on cell k (mirror image)
-    const double Ym = mp5_rel(-Md5, -Md4, -Md3, -Md2, MM3, MM4, eps4);
-    const double F = (cp + cm) + (Yp + Ym);
-    if (k > 3) g[k - 4] = (Fprev - F) * hdx;
+    const double Ym = mp5_rel2<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16);
+    const double F = fma(0.5, Yp + Ym, cp + cm);
+    if (k > 3) g[k - 4] = Fprev - F;
     Fprev = F;
     if (k < kend) {
-      const double gn = g[k + 2] - g[k + 1];
-      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = gn;
-      Pk1 = Pk2; Pk2 = Pk3; Pk3 = Pd4 - Pd3;
-      PM2 = PM3; PM3 = dm4(Pk2, Pk3);
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
+      const double pk = Pd4 - Pd3;
+      PM2 = PM3; PM3 = dm4(Pk3, pk);
+      Pk3 = pk;
       cp = g[k];
-      const double hn = h[k + 3] - h[k + 2];
-      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = hn;
-      Mk2 = Mk3; Mk3 = Mk4; Mk4 = Md5 - Md4;
-      MM3 = MM4; MM4 = dm4(Mk3, Mk4);
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
+      const double mk = Md5 - Md4;
+      MM3 = MM4; MM4 = dm4(Mk4, mk);
+      Mk4 = mk;
       cm = h[k + 1];
     }
   }
-  (void)Pk1;
-  (void)Mk2;
+  (void)Pk2;
+  (void)Mk3;
 }
 
 template <int PHYS, int NV, int D>
@@ -193,14 +194,14 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch * ch, sm);
   __syncthreads();
   const int nl = it.nl, slen = it.slen;
-  const double hdx = 0.5 / dm.dx[D];
-  // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} scales it by 4
-  const double eps4 = 4e-10;
+  // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
+  // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
+  const double eps16 = 16.0 * 1e-10;
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
     double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
     const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
-    flux_sweep(g, h, slen, hdx, eps4);
+    flux_sweep(g, h, slen, eps16);
   }
   __syncthreads();
   // coalesced write-out of L_D for the segment's interior cells
@@ -270,6 +271,10 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
     block_coords(dm, ci.blk, o);
     const double dt = p.dt[ci.dom];
     const double dtb = dt * p.co.b;
+    // L = sum_d (Fsum_{i-1/2} - Fsum_{i+1/2}) / (2 dx_d), Fsum in units of 2 F^
+    const double w0 = dtb * (0.5 / dm.dx[0]);
+    const double w1 = p.ndim > 1 ? dtb * (0.5 / dm.dx[1]) : 0.0;
+    const double w2 = p.ndim > 2 ? dtb * (0.5 / dm.dx[2]) : 0.0;
     const bool damp = PHYS == PH_MHD && p.final_stage && p.glm_cr > 0.0;
     if (damp) {
       if (threadIdx.x == 0) {
@@ -288,12 +293,11 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
 #pragma unroll
       for (int v = 0; v < NV; v++) {
         const long long e = idx + (long long)v * dm.ncell;
-        double l_ = p.L[0][e];
-        if (p.ndim > 1) l_ += p.L[1][e];
-        if (p.ndim > 2) l_ += p.L[2][e];
         double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
         for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
-        acc = fma(dtb, l_, acc);
+        acc = fma(w0, p.L[0][e], acc);
+        if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
+        if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
         if (PHYS == PH_MHD && v == 8) acc *= fac;
         u[v] = acc;
         p.out[e] = acc;
