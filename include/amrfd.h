@@ -152,6 +152,22 @@ int amrfd_get_error(amrfd_handle *h, void *stream);
 /* Free the handle and its workspace (synchronises the device first). */
 void amrfd_destroy(amrfd_handle *h);
 
+/* CFL time step of amrfd_dt for callers that cannot allocate device memory
+   (no handle, no cudaMalloc, no heap use). The paper has no counterpart: this is
+   a deployment variant of amrfd_dt. Inputs as for amrfd_create plus amrfd_dt:
+   `domains[ndomain]` (host), optional per-block `active_dev` (device, NULL = all
+   active), state `U` and output `dt_dev[ndomain]` (device). Scratch is a fixed
+   ~143 KB __device__ array inside the library, held by every GPU that loads it
+   until the process exits; ndomain is limited to 1024 (AMRFD_ERR_INVALID_ARG,
+   with a message on stderr, beyond). The first call on a device looks up the
+   array's device address and should come before any stream capture. All calls
+   share the one array and each leaves its contents behind: calls whose work
+   overlaps on the GPU (other streams, other host threads) race; serialise them.
+   Non-physical cells are skipped without setting an error latch. */
+int amrfd_dt_noalloc(const amrfd_config *cfg, const amrfd_domain *domains, int ndomain,
+                     const uint8_t *active_dev, const double *U, double *dt_dev, double t, double t_end,
+                     void *stream);
+
 /* Static description of a return code. */
 const char *amrfd_strerror(int code);
 

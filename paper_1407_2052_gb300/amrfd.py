@@ -21,7 +21,8 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
 
 EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
-           "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end")
+           "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
+           "amrfd_dt_noalloc")
 
 
 class Config(ctypes.Structure):
@@ -66,6 +67,7 @@ def load():
     L.amrfd_get_error.argtypes = [vp, vp]
     L.amrfd_timing_begin.argtypes = [vp, i]
     L.amrfd_timing_end.argtypes = [vp, vp, vp, vp]
+    L.amrfd_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(DomainC), i, vp, vp, vp, dp, dp, vp]
     L.amrfd_destroy.argtypes = [vp]
     L.amrfd_destroy.restype = None
     L.amrfd_strerror.argtypes = [i]
@@ -114,6 +116,18 @@ def domains_c(domains):
             arr[i].bc[k][1] = int(d.bc[k][1])
         arr[i].offset = int(d.offset)
     return arr
+
+
+def dt_noalloc(physics, ndim, gamma, cfl, domains, U, out, active=None, t=0.0, t_end=float("inf"),
+               dt_scope=DT_PER_DOMAIN, stream=None):
+    """amrfd_dt_noalloc: the CFL time step without a handle or any device allocation
+    (for callers that cannot allocate; `out` is a caller-owned float64 CUDA tensor)."""
+    cfg = Config(physics, ndim, SSPRK3, dt_scope, gamma, cfl, 0.0)
+    doms = domains_c(domains)
+    act = ctypes.c_void_p(active.data_ptr()) if active is not None else None
+    _check(load().amrfd_dt_noalloc(ctypes.byref(cfg), doms, len(domains), act, _ptr(U), _ptr(out), float(t),
+                                   float(t_end), _stream(stream)), "amrfd_dt_noalloc")
+    return out
 
 
 class Solver:
