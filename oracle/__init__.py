@@ -62,6 +62,7 @@ def lib():
         L.orc_residual.argtypes = [cp, mp, dp, dp, ctypes.c_double, dp]
         L.orc_step.argtypes = [cp, mp, dp, ctypes.c_double, u8p, dp, dp]
         L.orc_dt.argtypes = [cp, mp, dp, u8p, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_step_frozen.argtypes = [cp, mp, dp, ctypes.c_double, u8p, dp, ctypes.c_double]
         _lib = L
     return _lib
 
@@ -181,6 +182,15 @@ def step(c, d, U, dt, active=None):
     ch = np.zeros(1)
     fl = lib().orc_step(ctypes.byref(c), ctypes.byref(d), _dp(U), float(dt), _u8(a), _dp(al), _dp(ch))
     return U, fl, al, float(ch[0])
+
+
+def step_frozen(c, d, U, dt, alpha_stage, ch, active=None):
+    """One SSPRK step with the per-stage splitting speeds and c_h held fixed."""
+    U = _check(c, d, U).copy()
+    a = _active(d, active)
+    al = np.ascontiguousarray(alpha_stage, dtype=np.float64)
+    fl = lib().orc_step_frozen(ctypes.byref(c), ctypes.byref(d), _dp(U), float(dt), _u8(a), _dp(al), float(ch))
+    return U, fl
 
 
 def dt(c, d, U, cfl, t=0.0, t_end=np.inf, active=None):

@@ -320,9 +320,11 @@ int orc_residual(const orc_cfg *c, const orc_dom *dm, const double *U, const dou
   return flags;
 }
 
-/* ---- one SSPRK step (Sec. 2.3), passive blocks held fixed (App. C) ------- */
-int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
-             double *alpha_stage, double *ch_out) {
+/* ---- one SSPRK step (Sec. 2.3), passive blocks held fixed (App. C) -------
+   alpha_in (optional, [s][3]) and ch_in replace the splitting speeds and the GLM
+   speed computed from the stage states ("frozen" speeds, for derivative checks). */
+static int step_impl(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
+                     const double *alpha_in, double ch_in, double *alpha_stage, double *ch_out) {
   double a[5][5], b[5][5], araw[3], rate, ch = 0.0, alpha[3];
   const int nv = orc_nvar(c), s = orc_ssprk_table(c->integrator, a, b);
   long N = ncells(dm), tot = N * nv, j;
@@ -334,9 +336,14 @@ int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const ui
   memcpy(Ust[0], U, sizeof(double) * tot);
 
   flags |= orc_speeds(c, dm, Ust[0], block_active, araw, &rate);
-  if (c->physics == ORC_MHD_GLM)
-    for (d = 0; d < c->ndim; d++) ch = fmax(ch, araw[d]);
-  for (d = 0; d < 3; d++) alpha[d] = fmax(araw[d], ch);
+  if (alpha_in) {
+    ch = ch_in;
+    for (d = 0; d < 3; d++) alpha[d] = alpha_in[d];
+  } else {
+    if (c->physics == ORC_MHD_GLM)
+      for (d = 0; d < c->ndim; d++) ch = fmax(ch, araw[d]);
+    for (d = 0; d < 3; d++) alpha[d] = fmax(araw[d], ch);
+  }
 
   for (i = 1; i <= s; i++) {
     if (alpha_stage)
@@ -354,7 +361,7 @@ int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const ui
     }
     if (i < s) {
       flags |= orc_speeds(c, dm, Ust[i], block_active, araw, &rate);
-      for (d = 0; d < 3; d++) alpha[d] = fmax(araw[d], ch);
+      for (d = 0; d < 3; d++) alpha[d] = alpha_in ? alpha_in[i * 3 + d] : fmax(araw[d], ch);
     }
   }
   memcpy(U, Ust[s], sizeof(double) * tot);
@@ -370,6 +377,16 @@ int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const ui
   for (i = 0; i < s; i++) free(Lst[i]);
   free(m);
   return flags;
+}
+
+int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
+             double *alpha_stage, double *ch_out) {
+  return step_impl(c, dm, U, dt, block_active, NULL, 0.0, alpha_stage, ch_out);
+}
+
+int orc_step_frozen(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
+                    const double *alpha_in, double ch_in) {
+  return step_impl(c, dm, U, dt, block_active, alpha_in, ch_in, NULL, NULL);
 }
 
 /* ---- CFL time step (Sec. 4.4: dt < dx / c_w; unsplit multi-D sum) ------- */

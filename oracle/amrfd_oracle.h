@@ -73,6 +73,12 @@ int orc_residual(const orc_cfg *c, const orc_dom *dm, const double *U, const dou
 int orc_step(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
              double *alpha_stage, double *ch_out);
 
+/* The same step with the splitting speeds of every stage (alpha_in, [s][3], as
+   returned in alpha_stage by orc_step) and the GLM speed ch_in held fixed: the
+   map whose derivative the discrete adjoint transposes. */
+int orc_step_frozen(const orc_cfg *c, const orc_dom *dm, double *U, double dt, const uint8_t *block_active,
+                    const double *alpha_in, double ch_in);
+
 /* CFL time step of one domain; returns flags. */
 int orc_dt(const orc_cfg *c, const orc_dom *dm, const double *U, const uint8_t *block_active,
            double cfl, double t, double t_end, double *dt_out);

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libamrfd.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["amrfd_kernels.cu", "amrfd_api.cu", "amrfd_noalloc.cu"]
+SOURCES = ["amrfd_kernels.cu", "amrfd_adjoint.cu", "amrfd_api.cu", "amrfd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

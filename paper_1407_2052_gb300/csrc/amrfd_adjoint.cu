@@ -1,0 +1,442 @@
+// amrfd_adjoint.cu -- discrete adjoint of one SSPRK step of the FD-MP5 update.
+//
+// With the splitting speeds c_max (per stage), the GLM speed c_h and the psi
+// damping factor held at their forward values, one stage is
+//   U^(i) = sum_t a_t U^(k_t) + sum_d w_d D_d(S),   S = U^(i-1), w_d = dt b / (2 dx_d),
+// where D_d(S)_j = Fsum_j - Fsum_{j+1} and Fsum_k = G+_{k-1} + G-_k + (Y+_k + Y-_k)/2
+// is the interface flux of Sec. 2.2 in units of 2 F^ (G = F +- c_max U). Every MP5
+// value Y is piecewise linear in its stencil once the limiter's choices are fixed;
+// the adjoint recomputes the forward values bit for bit, reads off the chosen
+// pieces and applies their transposes. Gradients are gathered per cell (no atomics):
+// a segment recomputes the faces within reach of its cells (two beyond on the low
+// side, three on the high side) and keeps only contributions to its own cells;
+// with outflow faces the ghost copies of an edge cell fold back into it.
+#include <cuda_runtime.h>
+
+#include "amrfd_device.cuh"
+#include "amrfd_kernels.cuh"
+
+namespace amrfd {
+
+// Transposed flux-split Jacobian: gu = (dG+/dU)^T gp + (dG-/dU)^T gm with
+// G+- = F_D(U) +- alpha U (alpha, c_h fixed).
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void split_flux_adj(const double* u, double gm1, double alpha, double ch2,
+                                               const double* gp, const double* gmn, double* gu) {
+  double y[NV];
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    y[v] = gp[v] + gmn[v];
+    gu[v] = alpha * (gp[v] - gmn[v]);
+  }
+  const double rho = u[0];
+  const double ir = 1.0 / rho;
+  if (PHYS == PH_EULER) {
+    constexpr int nm = NV - 2;
+    double v[nm], gv[nm];
+    double mv = 0.0;
+#pragma unroll
+    for (int k = 0; k < nm; k++) { v[k] = u[1 + k] * ir; mv = fma(u[1 + k], v[k], mv); gv[k] = 0.0; }
+    const double E = u[NV - 1];
+    const double p = gm1 * fma(-0.5, mv, E);
+    const double vd = v[D];
+    double gp_ = 0.0, gE = 0.0;
+    gu[1 + D] += y[0];
+#pragma unroll
+    for (int k = 0; k < nm; k++) {
+      gv[D] += y[1 + k] * u[1 + k];
+      gu[1 + k] += y[1 + k] * vd;
+      if (k == D) gp_ += y[1 + k];
+    }
+    gv[D] += y[NV - 1] * (E + p);
+    gE += y[NV - 1] * vd;
+    gp_ += y[NV - 1] * vd;
+    gE += gm1 * gp_;
+    const double gmv = -0.5 * gm1 * gp_;
+    double gir = 0.0;
+#pragma unroll
+    for (int k = 0; k < nm; k++) {
+      gu[1 + k] += gmv * v[k];
+      gv[k] += gmv * u[1 + k];
+      gu[1 + k] += gv[k] * ir;
+      gir += gv[k] * u[1 + k];
+    }
+    gu[0] -= gir * ir * ir;
+    gu[NV - 1] += gE;
+  } else {
+    const double E = u[4];
+    const double B[3] = {u[5], u[6], u[7]};
+    const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+    const double b2 = fma(B[2], B[2], fma(B[1], B[1], B[0] * B[0]));
+    const double mv = fma(u[3], v[2], fma(u[2], v[1], u[1] * v[0]));
+    const double p = gm1 * fma(-0.5, mv + b2, E);
+    const double ptot = fma(0.5, b2, p);
+    const double vb = fma(v[2], B[2], fma(v[1], B[1], v[0] * B[0]));
+    const double vd = v[D], bd = B[D];
+    double gv[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
+    double gptot = 0.0, gE = 0.0, gvb = 0.0, gpsi = 0.0;
+    gu[1 + D] += y[0];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const double yk = y[1 + k];
+      gv[D] += yk * u[1 + k];
+      gu[1 + k] += yk * vd;
+      gB[D] -= yk * B[k];
+      gB[k] -= yk * bd;
+      if (k == D) gptot += yk;
+    }
+    gv[D] += y[4] * (E + ptot);
+    gE += y[4] * vd;
+    gptot += y[4] * vd;
+    gB[D] -= y[4] * vb;
+    gvb -= y[4] * bd;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      const double yk = y[5 + k];
+      if (k == D) {
+        gpsi += yk;
+      } else {
+        gv[D] += yk * B[k];
+        gB[k] += yk * vd;
+        gB[D] -= yk * v[k];
+        gv[k] -= yk * bd;
+      }
+    }
+    gB[D] += y[8] * ch2;
+#pragma unroll
+    for (int k = 0; k < 3; k++) { gv[k] += gvb * B[k]; gB[k] += gvb * v[k]; }
+    double gb2 = 0.5 * gptot;
+    const double gp_ = gptot;
+    gE += gm1 * gp_;
+    const double gmv = -0.5 * gm1 * gp_;
+    gb2 -= 0.5 * gm1 * gp_;
+    double gir = 0.0;
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      gu[1 + k] += gmv * v[k];
+      gv[k] += gmv * u[1 + k];
+      gB[k] += 2.0 * B[k] * gb2;
+      gu[1 + k] += gv[k] * ir;
+      gir += gv[k] * u[1 + k];
+      gu[5 + k] += gB[k];
+    }
+    gu[0] -= gir * ir * ir;
+    gu[4] += gE;
+    gu[8] += gpsi;
+  }
+}
+
+// Backward of one face k for one variable: gradients of Fsum_k w.r.t. the G+ and
+// G- values of its stencil, times gF, accumulated into gGp / gGm (smem lines
+// indexed by position q; the face's left cell is at q = qk - 1).
+template <bool NEG>
+__device__ __forceinline__ void face_adj(const double* G, double* gG, int q0, double gY, double eps16) {
+  // stencil positions q0 .. q0+4 in the orientation of the + reconstruction:
+  // NEG=false: (a,b,c,d,e) = G[q0..q0+4], centre c;  NEG=true: mirrored, G[q0+4..q0].
+  const double a = G[q0], b = G[q0 + 1], c = G[q0 + 2], d = G[q0 + 3], e = G[q0 + 4];
+  double Dm, D0, D1, Dp, kL, kC, kR;
+  if (!NEG) {
+    Dm = b - a; D0 = c - b; D1 = d - c; Dp = e - d;
+    kL = D0 - Dm; kC = D1 - D0; kR = Dp - D1;   // curvatures at q0+1, q0+2, q0+3
+  } else {
+    // forward differences along the line: h1 = b-a (at q0+1), h2 = c-b, h3 = d-c, h4 = e-d;
+    // the mirrored stencil centred on q0+2 takes (Dm, D0, D1, Dp) = (h4, h3, h2, h1) negated
+    const double h1 = b - a, h2 = c - b, h3 = d - c, h4 = e - d;
+    Dm = h4; D0 = h3; D1 = h2; Dp = h1;
+    kL = h2 - h1; kC = h3 - h2; kR = h4 - h3;   // curvatures at q0+1, q0+2, q0+3 (line order)
+  }
+  int cp, cm, code;
+  double Mp, Mm;
+  if (!NEG) {
+    Mm = dm4_sel(kL, kC, cm);  // at the face left of the centre
+    Mp = dm4_sel(kC, kR, cp);  // at the face right of the centre
+    (void)mp5_rel2_sel<false>(Dm, D0, D1, Dp, Mp, Mm, eps16, code);
+  } else {
+    Mp = dm4_sel(kL, kC, cp);  // mirror: the face on the low side of the centre is its "i+1/2"
+    Mm = dm4_sel(kC, kR, cm);
+    (void)mp5_rel2_sel<true>(Dm, D0, D1, Dp, Mp, Mm, eps16, code);
+  }
+  double gDm, gD0, gD1, gDp, gMp, gMm;
+  if (!NEG) mp5_rel2_grad<false>(code, gY, gDm, gD0, gD1, gDp, gMp, gMm);
+  else mp5_rel2_grad<true>(code, gY, gDm, gD0, gD1, gDp, gMp, gMm);
+  double gkL = 0.0, gkC = 0.0, gkR = 0.0, t1, t2;
+  if (!NEG) {
+    dm4_grad(cm, gMm, t1, t2); gkL += t1; gkC += t2;
+    dm4_grad(cp, gMp, t1, t2); gkC += t1; gkR += t2;
+  } else {
+    dm4_grad(cp, gMp, t1, t2); gkL += t1; gkC += t2;
+    dm4_grad(cm, gMm, t1, t2); gkC += t1; gkR += t2;
+  }
+  // gradients of the line differences h1..h4 (h_j = G[q0+j] - G[q0+j-1])
+  double gh1, gh2, gh3, gh4;
+  if (!NEG) { gh1 = gDm; gh2 = gD0; gh3 = gD1; gh4 = gDp; }
+  else { gh1 = gDp; gh2 = gD1; gh3 = gD0; gh4 = gDm; }
+  // kL = h2 - h1, kC = h3 - h2, kR = h4 - h3
+  gh1 -= gkL; gh2 += gkL - gkC; gh3 += gkC - gkR; gh4 += gkR;
+  gG[q0] -= gh1;
+  gG[q0 + 1] += gh1 - gh2;
+  gG[q0 + 2] += gh2 - gh3;
+  gG[q0 + 3] += gh3 - gh4;
+  gG[q0 + 4] += gh4;
+}
+
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem& it, double* sm) {
+  constexpr int od1 = D == 0 ? 1 : 0;
+  constexpr int od2 = D == 2 ? 1 : 2;
+  const DomDev dm = *(p.doms + it.dom);
+  int o[3];
+  {
+    const int bx = it.blk % dm.nb[0], by = (it.blk / dm.nb[0]) % dm.nb[1], bz = it.blk / (dm.nb[0] * dm.nb[1]);
+    o[0] = bx * dm.be[0]; o[1] = by * dm.be[1]; o[2] = bz * dm.be[2];
+  }
+  const unsigned long long* sk = p.araw + (size_t)it.dom * 4;
+  const unsigned long long* s0p = p.araw0 + (size_t)it.dom * 4;
+  double ch = 0.0;
+  if (p.glm)
+    for (int d = 0; d < p.ndim; d++) ch = imax(ch, bitsd((long long)s0p[d]));
+  const double alpha = imax(bitsd((long long)sk[D]), ch);
+  const double ch2 = ch * ch;
+  const double w = p.dt[it.dom] * p.b * (0.5 / dm.dx[D]);
+  const double pfac = p.psi_fac ? p.psi_fac[it.dom] : 1.0;
+  const int nl = it.nl, slen = it.slen, P = p.P, SA = p.SSa, SG = p.SSg;
+  const int n = dm.n[D];
+  const int s0 = o[D] + it.s0;               // first cell of the segment (domain coordinate)
+  const int WA = slen + 10, WG = slen + 6;
+  double* Gp = sm;                            // [NV][P][SA]
+  double* Gm = Gp + NV * P * SA;
+  double* gGp = Gm + NV * P * SA;
+  double* gGm = gGp + NV * P * SA;
+  double* gh = gGm + NV * P * SA;             // [NV][P][SG] scaled upstream gradient
+  // ---- phase A: forward G+- at positions s0-5 .. s0+slen+4, upstream gradient at s0-3 .. s0+slen+2
+  for (int c = threadIdx.x; c < nl * WA; c += blockDim.x) {
+    int pl, q;
+    if (D == 0) { pl = c / WA; q = c - pl * WA; }
+    else { q = c / nl; pl = c - q * nl; }
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    const int pos = s0 - 5 + q;
+    int g = pos;
+    bool inside = true;
+    if (g < 0) { inside = false; g = dm.bc[D][0] == 0 ? ((g % n) + n) % n : 0; }
+    else if (g >= n) { inside = false; g = dm.bc[D][1] == 0 ? g % n : n - 1; }
+    x[D] = g;
+    const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
+    const double* base = p.active[nbk] ? p.S : p.Un;
+    const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
+    double u[NV], gp[NV], gmn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = base[dm.off + idx + (long long)v * dm.ncell];
+    split_flux<PHYS, NV, D>(u, p.gm1, alpha, ch2, gp, gmn);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      Gp[(v * P + pl) * SA + q] = gp[v];
+      Gm[(v * P + pl) * SA + q] = gmn[v];
+      gGp[(v * P + pl) * SA + q] = 0.0;
+      gGm[(v * P + pl) * SA + q] = 0.0;
+    }
+    const int r = q - 2;  // gradient window starts two positions later
+    if (r >= 0 && r < WG) {
+      const bool periodic_side = pos < 0 ? dm.bc[D][0] == 0 : (pos >= n ? dm.bc[D][1] == 0 : true);
+      const bool live = inside || periodic_side;
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        double gv = 0.0;
+        if (live) {
+          gv = p.G[dm.off + idx + (long long)v * dm.ncell] * w;
+          if (PHYS == PH_MHD && v == 8) gv *= pfac;
+        }
+        gh[(v * P + pl) * SG + r] = gv;
+      }
+    }
+  }
+  __syncthreads();
+  // ---- phase B: one thread per (line, variable) walks the faces within reach
+  int kb = s0 - 2, ke = s0 + slen + 2;
+  if (dm.bc[D][0] == 1 && kb < 0) kb = 0;
+  if (dm.bc[D][1] == 1 && ke > n) ke = n;
+  const double eps16 = 16.0 * 1e-10;
+  for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
+    const int v = t / nl, pl = t - v * nl;
+    const double* gpl = Gp + (v * P + pl) * SA;
+    const double* gml = Gm + (v * P + pl) * SA;
+    double* ggp = gGp + (v * P + pl) * SA;
+    double* ggm = gGm + (v * P + pl) * SA;
+    const double* ghl = gh + (v * P + pl) * SG;
+    for (int k = kb; k <= ke; k++) {
+      const int qk = k - (s0 - 5);        // position of cell k in the G window
+      const int rk = k - (s0 - 3);        // position of cell k in the gradient window
+      const double gF = ghl[rk] - ghl[rk - 1];
+      if (gF == 0.0) continue;
+      ggp[qk - 1] += gF;
+      ggm[qk] += gF;
+      const double gY = 0.5 * gF;
+      face_adj<false>(gpl, ggp, qk - 3, gY, eps16);  // + stencil: cells k-3 .. k+1, centre k-1
+      face_adj<true>(gml, ggm, qk - 2, gY, eps16);   // - stencil: cells k-2 .. k+2, centre k
+    }
+    // outflow: ghost copies of an edge cell fold back into it
+    if (dm.bc[D][0] == 1 && s0 == 0) {
+      const int q0 = 5;  // position of cell 0
+      for (int qq = 2; qq < q0; qq++) { ggp[q0] += ggp[qq]; ggm[q0] += ggm[qq]; }
+    }
+    if (dm.bc[D][1] == 1 && s0 + slen == n) {
+      const int qn = slen + 4;  // position of cell n-1
+      for (int qq = qn + 1; qq <= qn + 3; qq++) { ggp[qn] += ggp[qq]; ggm[qn] += ggm[qq]; }
+    }
+  }
+  __syncthreads();
+  // ---- phase C: transposed flux-split Jacobian per cell of the segment
+  for (int c = threadIdx.x; c < nl * slen; c += blockDim.x) {
+    int pl, j;
+    if (D == 0) { pl = c / slen; j = c - pl * slen; }
+    else { j = c / nl; pl = c - j * nl; }
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    x[D] = s0 + j;
+    const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
+    double u[NV], gpv[NV], gmv[NV], gu[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      u[v] = p.S[dm.off + idx + (long long)v * dm.ncell];
+      gpv[v] = gGp[(v * P + pl) * SA + j + 5];
+      gmv[v] = gGm[(v * P + pl) * SA + j + 5];
+    }
+    split_flux_adj<PHYS, NV, D>(u, p.gm1, alpha, ch2, gpv, gmv, gu);
+#pragma unroll
+    for (int v = 0; v < NV; v++) p.gL[D][dm.off + idx + (long long)v * dm.ncell] = gu[v];
+  }
+  __syncthreads();
+}
+
+template <int PHYS, int NV>
+__global__ void __launch_bounds__(256) adj_flux_kernel(AdjFluxParams p) {
+  extern __shared__ double sm[];
+  constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
+  for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
+    const FluxItem item = p.items[p.item0 + it];
+    if (!p.active[p.doms[item.dom].block0 + item.blk]) continue;
+    if (item.d == 0) adj_item<PHYS, NV, 0>(p, item, sm);
+    if constexpr (maxd > 1) { if (item.d == 1) adj_item<PHYS, NV, 1>(p, item, sm); }
+    if constexpr (maxd > 2) { if (item.d == 2) adj_item<PHYS, NV, 2>(p, item, sm); }
+  }
+}
+
+// Transposed stage combination: g[U^(k_t)] += a_t gOut, g[U^(i-1)] += sum_d gL_d.
+template <int NV>
+__global__ void __launch_bounds__(256) adj_combine_kernel(AdjCombParams p) {
+  for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
+    const CellItem ci = p.items[p.item0 + it];
+    const DomDev dm = p.doms[ci.dom];
+    if (!p.active[dm.block0 + ci.blk]) continue;
+    int o[3];
+    {
+      const int bx = ci.blk % dm.nb[0], by = (ci.blk / dm.nb[0]) % dm.nb[1], bz = ci.blk / (dm.nb[0] * dm.nb[1]);
+      o[0] = bx * dm.be[0]; o[1] = by * dm.be[1]; o[2] = bz * dm.be[2];
+    }
+    const double pfac = p.psi_fac ? p.psi_fac[ci.dom] : 1.0;
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        const long long e = idx + (long long)v * dm.ncell;
+        double g = p.gout[e];
+        if (NV == 9 && v == 8) g *= pfac;
+        for (int t = 0; t < p.co.nterm; t++) p.gbuf[p.co.k[t]][e] = fma(p.co.a[t], g, p.gbuf[p.co.k[t]][e]);
+        double s = p.gL[0][e];
+        if (p.ndim > 1) s += p.gL[1][e];
+        if (p.ndim > 2) s += p.gL[2][e];
+        p.gbuf[p.kin][e] += s;
+      }
+    }
+  }
+}
+
+// Passive blocks are the identity map of U^n: their gradient passes through.
+__global__ void __launch_bounds__(256) adj_passive_kernel(AdjCombParams p) {
+  for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
+    const CellItem ci = p.items[p.item0 + it];
+    const DomDev dm = p.doms[ci.dom];
+    if (p.active[dm.block0 + ci.blk]) continue;
+    int o[3];
+    {
+      const int bx = ci.blk % dm.nb[0], by = (ci.blk / dm.nb[0]) % dm.nb[1], bz = ci.blk / (dm.nb[0] * dm.nb[1]);
+      o[0] = bx * dm.be[0]; o[1] = by * dm.be[1]; o[2] = bz * dm.be[2];
+    }
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      for (int v = 0; v < p.nv; v++) {
+        const long long e = idx + (long long)v * dm.ncell;
+        p.gbuf[0][e] = p.gout[e];
+      }
+    }
+  }
+}
+
+// psi damping factor exp(-dt c_h / c_r) per domain, as applied by the forward step
+__global__ void psi_fac_kernel(const unsigned long long* araw0, const double* dt, double* fac, int ndom, int ndim,
+                               double cr, int glm) {
+  for (int d = blockIdx.x * blockDim.x + threadIdx.x; d < ndom; d += gridDim.x * blockDim.x) {
+    double f = 1.0;
+    if (glm && cr > 0.0) {
+      double ch = 0.0;
+      for (int k = 0; k < ndim; k++) ch = imax(ch, bitsd((long long)araw0[(size_t)d * 4 + k]));
+      f = exp(-dt[d] * ch / cr);
+    }
+    fac[d] = f;
+  }
+}
+
+#define AMRFD_DISPATCH_ADJ(physics, nv, CALL)                               \
+  do {                                                                      \
+    if ((physics) == PH_MHD && (nv) == 9) { CALL(PH_MHD, 9); }              \
+    else if ((physics) == PH_EULER && (nv) == 3) { CALL(PH_EULER, 3); }     \
+    else if ((physics) == PH_EULER && (nv) == 4) { CALL(PH_EULER, 4); }     \
+    else if ((physics) == PH_EULER && (nv) == 5) { CALL(PH_EULER, 5); }     \
+    else return cudaErrorInvalidValue;                                      \
+  } while (0)
+
+cudaError_t launch_adj_flux(int physics, int nv, const AdjFluxParams& p, int grid, int block, size_t smem,
+                            cudaStream_t s) {
+#define CALL(PH, NVV)                                                                                      \
+  {                                                                                                        \
+    cudaError_t e = cudaFuncSetAttribute(adj_flux_kernel<PH, NVV>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                       \
+    if (e != cudaSuccess) return e;                                                                        \
+    adj_flux_kernel<PH, NVV><<<grid, block, smem, s>>>(p);                                                 \
+  }
+  AMRFD_DISPATCH_ADJ(physics, nv, CALL);
+#undef CALL
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_combine(int nv, const AdjCombParams& p, int grid, int block, cudaStream_t s) {
+  if (nv == 9) adj_combine_kernel<9><<<grid, block, 0, s>>>(p);
+  else if (nv == 3) adj_combine_kernel<3><<<grid, block, 0, s>>>(p);
+  else if (nv == 4) adj_combine_kernel<4><<<grid, block, 0, s>>>(p);
+  else if (nv == 5) adj_combine_kernel<5><<<grid, block, 0, s>>>(p);
+  else return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_passive(const AdjCombParams& p, int grid, int block, cudaStream_t s) {
+  adj_passive_kernel<<<grid, block, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_fac(const unsigned long long* araw0, const double* dt, double* fac, int ndom, int ndim,
+                           double cr, int glm, cudaStream_t s) {
+  psi_fac_kernel<<<(ndom + 255) / 256, 256, 0, s>>>(araw0, dt, fac, ndom, ndim, cr, glm);
+  return cudaGetLastError();
+}
+
+}  // namespace amrfd

@@ -92,6 +92,14 @@ struct amrfd_handle {
   unsigned* d_err = nullptr;
   size_t nelem = 0;                 // elements of one state-shaped buffer
   cudaStream_t cap = nullptr;       // private stream for graph capture
+  // adjoint workspace (allocated on the first amrfd_adjoint call)
+  double* d_gstage[kMaxStages] = {};
+  double* d_psifac = nullptr;
+  FluxItem* d_adj_items = nullptr;
+  int adj_nitems = 0;
+  int adj_seg = 16, adj_lines = 8, adj_threads = 128;
+  size_t adj_smem = 0;
+  int adj_P = 8, adj_SSa = 0, adj_SSg = 0;
   // kernel timing (measurement mode)
   bool timing = false;
   std::vector<cudaEvent_t> tev;     // 2 per recorded launch
@@ -562,10 +570,146 @@ int amrfd_step_batched(amrfd_handle* h, double* U, const double* dt_dev, void* s
   return AMRFD_OK;
 }
 
+namespace {
+
+// Work items of the transposed flux pass: all blocks, segments of <= adj_seg cells,
+// adj_lines lines per tile (the kernel skips passive blocks).
+int build_adjoint_items(amrfd_handle* h) {
+  std::vector<FluxItem> fi;
+  int maxseg = 1;
+  for (int d = 0; d < h->ndom; d++) {
+    const DomDev& dm = h->hdom[d];
+    const int nbl = dm.nb[0] * dm.nb[1] * dm.nb[2];
+    for (int b = 0; b < nbl; b++)
+      for (int dir = 0; dir < h->cfg.ndim; dir++) {
+        const int od1 = dir == 0 ? 1 : 0, od2 = dir == 2 ? 1 : 2;
+        const int nlines = dm.be[od1] * dm.be[od2];
+        const int ext = dm.be[dir];
+        const int nseg = (ext + h->adj_seg - 1) / h->adj_seg;
+        const int slen0 = (ext + nseg - 1) / nseg;
+        maxseg = std::max(maxseg, slen0);
+        for (int sg = 0; sg < nseg; sg++) {
+          const int s0 = sg * slen0, sl = std::min(slen0, ext - s0);
+          for (int l0 = 0; l0 < nlines; l0 += h->adj_lines) {
+            FluxItem it{};
+            it.dom = d; it.blk = b; it.l0 = l0;
+            it.s0 = (short)s0; it.slen = (unsigned short)sl;
+            it.d = (unsigned char)dir;
+            it.nl = (unsigned char)std::min(h->adj_lines, nlines - l0);
+            fi.push_back(it);
+          }
+        }
+      }
+  }
+  h->adj_nitems = (int)fi.size();
+  h->adj_P = h->adj_lines;
+  h->adj_SSa = maxseg + 10 + ((maxseg + 10) % 2 == 0 ? 1 : 0);
+  h->adj_SSg = maxseg + 6 + ((maxseg + 6) % 2 == 0 ? 1 : 0);
+  h->adj_smem = sizeof(double) * (size_t)h->nv * h->adj_P * (4 * h->adj_SSa + h->adj_SSg);
+  CK(cudaMalloc(&h->d_adj_items, sizeof(FluxItem) * std::max(1, h->adj_nitems)));
+  CK(cudaMemcpy(h->d_adj_items, fi.data(), sizeof(FluxItem) * h->adj_nitems, cudaMemcpyHostToDevice));
+  return AMRFD_OK;
+}
+
+}  // namespace
+
 int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
                   void* stream) {
-  (void)h; (void)U_n; (void)dt_dev; (void)gU_np1; (void)gU_n; (void)stream;
-  return AMRFD_ERR_UNSUPPORTED;
+  if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  // supported: every domain entirely active or entirely passive; periodic lines >= 6 cells
+  for (int d = 0; d < h->ndom; d++) {
+    const DomDev& dm = h->hdom[d];
+    const int nbl = dm.nb[0] * dm.nb[1] * dm.nb[2];
+    int na = 0;
+    for (int b = 0; b < nbl; b++) na += h->active_h[dm.block0 + b] != 0;
+    if (na != 0 && na != nbl) return AMRFD_ERR_UNSUPPORTED;
+    for (int k = 0; k < h->cfg.ndim; k++)
+      if (dm.bc[k][0] == AMRFD_BC_PERIODIC && dm.n[k] < 6) return AMRFD_ERR_UNSUPPORTED;
+  }
+  if (!h->d_adj_items) {
+    for (int k = 1; k < h->ns; k++) CK(cudaMalloc(&h->d_gstage[k], sizeof(double) * h->nelem));
+    CK(cudaMalloc(&h->d_psifac, sizeof(double) * h->ndom));
+    int rc = build_adjoint_items(h);
+    if (rc) return rc;
+  }
+  const int ph = h->cfg.physics, nv = h->nv;
+  const int cgrid = 8 * h->nsm;
+  double* Un = const_cast<double*>(U_n);
+  // forward recompute of U^(1..s-1) and of the splitting speeds of every stage input
+  CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
+  CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
+  {
+    SpeedParams p = speed_params(h, U_n, 0, 0);
+    p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
+    CK(launch_speeds(ph, nv, p, cgrid, 256, s));
+  }
+  for (int i = 1; i < h->ns; i++) {
+    const double* Uk = (i == 1) ? U_n : h->d_stage[i - 1];
+    FluxParams fp = flux_params(h, Uk, U_n, i - 1);
+    fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
+    CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+    CombParams cp = comb_params(h, Un, dt_dev, i);
+    cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
+    CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+  }
+  CK(launch_psi_fac(slot(h, 0), dt_dev, h->d_psifac, h->ndom, h->cfg.ndim, h->cfg.glm_cr,
+                    h->cfg.physics == AMRFD_MHD_GLM, s));
+  // reverse sweep over the stages
+  CK(cudaMemsetAsync(gU_n, 0, sizeof(double) * h->nelem, s));
+  for (int k = 1; k < h->ns; k++) CK(cudaMemsetAsync(h->d_gstage[k], 0, sizeof(double) * h->nelem, s));
+  for (int i = h->ns; i >= 1; i--) {
+    const double* gout = (i == h->ns) ? gU_np1 : h->d_gstage[i];
+    const double* S = (i == 1) ? U_n : h->d_stage[i - 1];
+    AdjFluxParams ap{};
+    ap.doms = h->d_dom;
+    ap.active = h->d_active;
+    ap.items = h->d_adj_items;
+    ap.nitems = h->adj_nitems;
+    ap.S = S;
+    ap.Un = U_n;
+    ap.G = gout;
+    ap.psi_fac = (i == h->ns) ? h->d_psifac : nullptr;
+    ap.dt = dt_dev;
+    ap.b = h->co[i - 1].b;
+    for (int d = 0; d < 3; d++) ap.gL[d] = h->d_L[d] ? h->d_L[d] : h->d_L[0];
+    ap.araw = slot(h, i - 1);
+    ap.araw0 = slot(h, 0);
+    ap.gm1 = h->cfg.gamma - 1.0;
+    ap.ndim = h->cfg.ndim;
+    ap.P = h->adj_P;
+    ap.SSa = h->adj_SSa;
+    ap.SSg = h->adj_SSg;
+    ap.glm = h->cfg.physics == AMRFD_MHD_GLM;
+    {
+      Tick tk(h, K_FLUX, s);
+      CK(launch_adj_flux(ph, nv, ap, std::min(ap.nitems, 16 * h->nsm), h->adj_threads, h->adj_smem, s));
+    }
+    AdjCombParams cq{};
+    cq.doms = h->d_dom;
+    cq.active = h->d_active;
+    cq.items = h->d_call;
+    cq.nitems = h->nci;
+    cq.gout = gout;
+    cq.psi_fac = ap.psi_fac;
+    cq.gbuf[0] = gU_n;
+    for (int k = 1; k < kMaxStages; k++) cq.gbuf[k] = h->d_gstage[k];
+    for (int d = 0; d < 3; d++) cq.gL[d] = ap.gL[d];
+    cq.co = h->co[i - 1];
+    cq.kin = i - 1;
+    cq.ndim = h->cfg.ndim;
+    cq.nv = nv;
+    {
+      Tick tk(h, K_COMBINE, s);
+      CK(launch_adj_combine(nv, cq, std::min(h->nci, cgrid), 256, s));
+    }
+    if (i == h->ns) {
+      // passive blocks: U^{n+1} = U^n there
+      cq.gout = gU_np1;
+      CK(launch_adj_passive(cq, std::min(h->nci, cgrid), 256, s));
+    }
+  }
+  return AMRFD_OK;
 }
 
 int amrfd_set_tile(amrfd_handle* h, int seg, int lines, int threads) {
@@ -705,6 +849,9 @@ void amrfd_destroy(amrfd_handle* h) {
   cudaFree(h->d_order); cudaFree(h->d_fbeg); cudaFree(h->d_fcnt); cudaFree(h->d_cbeg); cudaFree(h->d_ccnt);
   cudaFree(h->d_fdst); cudaFree(h->d_cdst); cudaFree(h->d_counts); cudaFree(h->d_counters);
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_stage[k]);
+  for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_gstage[k]);
+  cudaFree(h->d_psifac);
+  cudaFree(h->d_adj_items);
   for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
   cudaFree(h->d_slot); cudaFree(h->d_err);
   if (h->cap) cudaStreamDestroy(h->cap);

@@ -17,21 +17,49 @@ enum { PH_EULER = 0, PH_MHD = 1 };
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
+// The helpers below are written in inline PTX so that they stay on the integer
+// pipe: left to itself the compiler turns some of these bit manipulations of
+// doubles back into FP64 compares, negations or multiplies.
+
 // Monotone signed-integer key of a double (total order; -0 sorts before +0).
 __device__ __forceinline__ long long okey(double x) {
   long long b = dbits(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
 }
-__device__ __forceinline__ double imin(double a, double b) { return okey(a) < okey(b) ? a : b; }
-__device__ __forceinline__ double imax(double a, double b) { return okey(a) < okey(b) ? b : a; }
+
+#define AMRFD_OKEY(dst, src) \
+  "shr.s64 " dst ", " src ", 63;\n\t" "and.b64 " dst ", " dst ", 0x7fffffffffffffff;\n\t" \
+  "xor.b64 " dst ", " src ", " dst ";\n\t"
+
+__device__ __forceinline__ double imin(double a, double b) {
+  double r;
+  asm("{\n\t.reg .b64 xa, xb, ka, kb;\n\t.reg .pred p;\n\t"
+      "mov.b64 xa, %1;\n\tmov.b64 xb, %2;\n\t" AMRFD_OKEY("ka", "xa") AMRFD_OKEY("kb", "xb")
+      "setp.lt.s64 p, ka, kb;\n\tselp.b64 xa, xa, xb, p;\n\tmov.b64 %0, xa;\n\t}"
+      : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+__device__ __forceinline__ double imax(double a, double b) {
+  double r;
+  asm("{\n\t.reg .b64 xa, xb, ka, kb;\n\t.reg .pred p;\n\t"
+      "mov.b64 xa, %1;\n\tmov.b64 xb, %2;\n\t" AMRFD_OKEY("ka", "xa") AMRFD_OKEY("kb", "xb")
+      "setp.lt.s64 p, ka, kb;\n\tselp.b64 xa, xb, xa, p;\n\tmov.b64 %0, xa;\n\t}"
+      : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
 
 // minmod(a,b) = (sgn a + sgn b)/2 * min(|a|,|b|): the smaller-magnitude argument
 // when both have the same sign, else zero.
 __device__ __forceinline__ double iminmod(double a, double b) {
-  long long ba = dbits(a), bb = dbits(b);
-  long long ma = ba & 0x7fffffffffffffffLL, mb = bb & 0x7fffffffffffffffLL;
-  long long r = (ma < mb) ? ba : bb;
-  return ((ba ^ bb) < 0) ? 0.0 : bitsd(r);
+  double r;
+  asm("{\n\t.reg .b64 xa, xb, ma, mb, t;\n\t.reg .pred p, q;\n\t"
+      "mov.b64 xa, %1;\n\tmov.b64 xb, %2;\n\t"
+      "and.b64 ma, xa, 0x7fffffffffffffff;\n\tand.b64 mb, xb, 0x7fffffffffffffff;\n\t"
+      "setp.lt.u64 p, ma, mb;\n\tselp.b64 t, xa, xb, p;\n\t"
+      "xor.b64 ma, xa, xb;\n\tsetp.lt.s64 q, ma, 0;\n\tselp.b64 t, 0, t, q;\n\t"
+      "mov.b64 %0, t;\n\t}"
+      : "=d"(r) : "d"(a), "d"(b));
+  return r;
 }
 
 // minmod of four arguments: signed smallest magnitude if all share a sign, else 0.
@@ -52,19 +80,43 @@ __device__ __forceinline__ double imedian(double x, double y, double z) {
 }
 
 // x <= c for a finite non-negative constant c (NaN compares false)
-__device__ __forceinline__ bool ile_pos(double x, double c) { return okey(x) <= dbits(c); }
+__device__ __forceinline__ bool ile_pos(double x, double c) {
+  unsigned r;
+  asm("{\n\t.reg .b64 xa, xc, ka;\n\t.reg .pred p;\n\t"
+      "mov.b64 xa, %1;\n\tmov.b64 xc, %2;\n\t" AMRFD_OKEY("ka", "xa")
+      "setp.le.s64 p, ka, xc;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(r) : "d"(x), "d"(c));
+  return r != 0;
+}
 
 // x * 2^K exactly. The exponent field is adjusted on the integer pipe when the
-// result stays a normal number (or x is +-0); otherwise one FP64 multiply.
+// result stays a normal number (or x is +-0); otherwise (subnormal or near-overflow
+// input, never met in practice) one FP64 multiply in an out-of-line call.
+static __device__ __noinline__ double dscale_slow(double x, double f) { return x * f; }
+
 template <int K>
 __device__ __forceinline__ double dscale(double x) {
-  const long long b = dbits(x);
-  const int e = (int)((b >> 52) & 0x7ff);
-  const bool zero = (b & 0x7fffffffffffffffLL) == 0;
-  const bool ok = (e >= 1 + (K < 0 ? -K : 0)) && (e <= 2046 - (K > 0 ? K : 0));
-  if (zero) return x;
-  if (ok) return bitsd(b + ((long long)K << 52));
-  return x * (K >= 0 ? (double)(1LL << (K >= 0 ? K : 0)) : 1.0 / (double)(1LL << (K < 0 ? -K : 0)));
+  double r;
+  unsigned ok;
+  constexpr long long inc = (long long)K << 52;
+  constexpr long long lo = (long long)(1 + (K < 0 ? -K : 0)) << 52;   // smallest exponent field allowed
+  constexpr long long hi = (long long)(2046 - (K > 0 ? K : 0)) << 52;  // largest exponent field allowed
+  asm("{\n\t.reg .b64 xa, m, e, y;\n\t.reg .pred pz, plo, phi, pok;\n\t"
+      "mov.b64 xa, %2;\n\t"
+      "and.b64 m, xa, 0x7fffffffffffffff;\n\t"
+      "and.b64 e, xa, 0x7ff0000000000000;\n\t"
+      "setp.eq.s64 pz, m, 0;\n\t"
+      "setp.ge.s64 plo, e, %3;\n\t"
+      "setp.le.s64 phi, e, %4;\n\t"
+      "and.pred pok, plo, phi;\n\t"
+      "or.pred pok, pok, pz;\n\t"
+      "add.s64 y, xa, %5;\n\t"
+      "selp.b64 y, xa, y, pz;\n\t"
+      "mov.b64 %0, y;\n\t"
+      "selp.u32 %1, 1, 0, pok;\n\t}"
+      : "=d"(r), "=r"(ok) : "d"(x), "l"(lo), "l"(hi), "l"(inc));
+  if (__builtin_expect(ok == 0, 0)) r = dscale_slow(x, K >= 0 ? (double)(1LL << (K >= 0 ? K : 0)) : 1.0 / (double)(1LL << (K < 0 ? -K : 0)));
+  return r;
 }
 
 __device__ __forceinline__ double dneg(double x) { return bitsd(dbits(x) ^ (long long)0x8000000000000000ULL); }
@@ -107,10 +159,117 @@ __device__ __forceinline__ double mp5_rel2(double Dm, double D0, double D1, doub
 // a face from the curvatures of its two cells. Zero unless ka, kb share a sign; then,
 // with s the smaller and l the larger in magnitude, 4 l - s never wins and the
 // result is 4 s - l if it keeps the sign and is smaller than s, else s (one FMA).
+// Selections and the sign flip of l are integer operations.
 __device__ __forceinline__ double dm4(double ka, double kb) {
+  double sm, nl;
+  unsigned same;
+  asm("{\n\t.reg .b64 a, b, ma, mb, s, l, t;\n\t.reg .pred p, q, z;\n\t"
+      "mov.b64 a, %3;\n\tmov.b64 b, %4;\n\t"
+      "and.b64 ma, a, 0x7fffffffffffffff;\n\tand.b64 mb, b, 0x7fffffffffffffff;\n\t"
+      "setp.lt.u64 p, ma, mb;\n\t"
+      "selp.b64 s, a, b, p;\n\tselp.b64 l, b, a, p;\n\t"
+      "xor.b64 l, l, 0x8000000000000000;\n\t"
+      "xor.b64 t, a, b;\n\tsetp.ge.s64 q, t, 0;\n\t"
+      "setp.ne.s64 z, ma, 0;\n\tand.pred q, q, z;\n\t"
+      "setp.ne.s64 z, mb, 0;\n\tand.pred q, q, z;\n\t"
+      "mov.b64 %0, s;\n\tmov.b64 %1, l;\n\tselp.u32 %2, 1, 0, q;\n\t}"
+      : "=d"(sm), "=d"(nl), "=r"(same) : "d"(ka), "d"(kb));
+  if (!same) return 0.0;
+  const double t = fma(4.0, sm, nl);
+  double r;
+  asm("{\n\t.reg .b64 s, t, ms, mt, x;\n\t.reg .pred p, q;\n\t"
+      "mov.b64 s, %1;\n\tmov.b64 t, %2;\n\t"
+      "and.b64 ms, s, 0x7fffffffffffffff;\n\tand.b64 mt, t, 0x7fffffffffffffff;\n\t"
+      "setp.lt.u64 p, mt, ms;\n\tselp.b64 x, t, s, p;\n\t"
+      "xor.b64 ms, s, t;\n\tsetp.lt.s64 q, ms, 0;\n\t"
+      "setp.eq.s64 p, mt, 0;\n\tor.pred q, q, p;\n\t"
+      "selp.b64 x, 0, x, q;\n\tmov.b64 %0, x;\n\t}"
+      : "=d"(r) : "d"(sm), "d"(t));
+  return r;
+}
+
+// ------------------------------------------------ selection-tracking variants
+// The same operations as mp5_rel2 / dm4 (bit-identical results), also reporting
+// which linear piece produced the value, for the discrete adjoint.
+enum { SEL_X = 0, SEL_ZERO = 1, SEL_D1 = 2, SEL_MD = 3, SEL_UL = 4, SEL_LC = 5 };
+
+__device__ __forceinline__ void imin_sel(double a, int ca, double b, int cb, double& r, int& cr) {
+  const bool t = okey(a) < okey(b);
+  r = t ? a : b;
+  cr = t ? ca : cb;
+}
+__device__ __forceinline__ void imax_sel(double a, int ca, double b, int cb, double& r, int& cr) {
+  const bool t = okey(a) < okey(b);
+  r = t ? b : a;
+  cr = t ? cb : ca;
+}
+
+template <bool NEG>
+__device__ __forceinline__ double mp5_rel2_sel(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
+                                               double eps16, int& code) {
+  constexpr double sg = NEG ? -1.0 : 1.0;
+  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
+                   c6 = sg * (6.0 / 60.0);
+  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));
+  X = fma(-c6, Dp, X);
+  const double d0 = NEG ? dneg(D0) : D0;
+  const double d1 = NEG ? dneg(D1) : D1;
+  const double ul = dscale<3>(d0);
+  const double d1x2 = dscale<1>(d1);
+  const double mp = iminmod(d1x2, ul);
+  const double chk = X * (X - mp);
+  code = SEL_X;
+  if (ile_pos(chk, eps16)) return X;
+  const double md = d1 - Mp;
+  const double lc = fma(8.0 / 3.0, Mm, d0);
+  double a, b, fmin, fmax, t1, t2, t3;
+  int ca, cb, cmin, cmax, c1, c2, c3;
+  imin_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
+  imin_sel(a, ca, md, SEL_MD, a, ca);
+  imin_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
+  imin_sel(b, cb, lc, SEL_LC, b, cb);
+  imax_sel(a, ca, b, cb, fmin, cmin);
+  imax_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
+  imax_sel(a, ca, md, SEL_MD, a, ca);
+  imax_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
+  imax_sel(b, cb, lc, SEL_LC, b, cb);
+  imin_sel(a, ca, b, cb, fmax, cmax);
+  // median(x, y, z) = max(min(x, y), min(max(x, y), z)) with x = X, y = fmin, z = fmax
+  imin_sel(X, SEL_X, fmin, cmin, t1, c1);
+  imax_sel(X, SEL_X, fmin, cmin, t2, c2);
+  imin_sel(t2, c2, fmax, cmax, t3, c3);
+  double r;
+  imax_sel(t1, c1, t3, c3, r, code);
+  return r;
+}
+
+// Gradient of mp5_rel2 w.r.t. (Dm, D0, D1, Dp, Mp, Mm) for the piece `code`, times g.
+template <bool NEG>
+__device__ __forceinline__ void mp5_rel2_grad(int code, double g, double& gDm, double& gD0, double& gD1,
+                                              double& gDp, double& gMp, double& gMm) {
+  constexpr double sg = NEG ? -1.0 : 1.0;
+  gDm = gD0 = gD1 = gDp = gMp = gMm = 0.0;
+  switch (code) {
+    case SEL_X:
+      gDm = (-sg * (4.0 / 60.0)) * g;
+      gD0 = (sg * (22.0 / 60.0)) * g;
+      gD1 = (sg * (48.0 / 60.0)) * g;
+      gDp = (-sg * (6.0 / 60.0)) * g;
+      break;
+    case SEL_D1: gD1 = (2.0 * sg) * g; break;
+    case SEL_MD: gD1 = sg * g; gMp = -g; break;
+    case SEL_UL: gD0 = (8.0 * sg) * g; break;
+    case SEL_LC: gD0 = sg * g; gMm = (8.0 / 3.0) * g; break;
+    default: break;
+  }
+}
+
+// dm4 with the chosen piece: 0 zero, 1 ka, 2 kb, 3 4 ka - kb, 4 4 kb - ka.
+__device__ __forceinline__ double dm4_sel(double ka, double kb, int& code) {
   const long long a = dbits(ka), b = dbits(kb);
   const long long M = 0x7fffffffffffffffLL;
   const long long ma = a & M, mb = b & M;
+  code = 0;
   if (((a ^ b) < 0) | (ma == 0) | (mb == 0)) return 0.0;
   const bool as = ma < mb;
   const double sm = as ? ka : kb, lg = as ? kb : ka;
@@ -118,7 +277,17 @@ __device__ __forceinline__ double dm4(double ka, double kb) {
   const double t = fma(4.0, sm, -lg);
   const long long bt = dbits(t);
   if (((bt ^ dbits(sm)) < 0) | ((bt & M) == 0)) return 0.0;
-  return ((bt & M) < ms) ? t : sm;
+  if ((bt & M) < ms) { code = as ? 3 : 4; return t; }
+  code = as ? 1 : 2;
+  return sm;
+}
+
+__device__ __forceinline__ void dm4_grad(int code, double g, double& gka, double& gkb) {
+  gka = gkb = 0.0;
+  if (code == 1) gka = g;
+  else if (code == 2) gkb = g;
+  else if (code == 3) { gka = 4.0 * g; gkb = -g; }
+  else if (code == 4) { gkb = 4.0 * g; gka = -g; }
 }
 
 // Reciprocal of a positive normal double: FP32 seed from the leading bits (integer

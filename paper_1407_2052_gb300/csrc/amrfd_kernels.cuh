@@ -89,7 +89,52 @@ struct CompactParams {
   int* fdst; int* cdst;        // scratch: destination offsets per work position
 };
 
+// One transposed flux pass (adjoint of one stage's residual).
+struct AdjFluxParams {
+  const DomDev* doms;
+  const unsigned char* active;
+  const FluxItem* items;
+  int nitems;
+  int item0;
+  const double* S;              // stage input state U^(i-1)
+  const double* Un;             // U^n (halo source inside passive neighbour blocks)
+  const double* G;              // gradient w.r.t. the stage output U^(i)
+  const double* psi_fac;        // per-domain psi damping factor (last stage) or nullptr
+  const double* dt;             // per-domain time step
+  double b;                     // stage weight of L(U^(i-1))
+  double* gL[3];                // per-direction gradient w.r.t. S
+  const unsigned long long* araw;
+  const unsigned long long* araw0;
+  double gm1;
+  int ndim;
+  int P, SSa, SSg;
+  int glm;
+};
+
+// Transposed stage combination.
+struct AdjCombParams {
+  const DomDev* doms;
+  const unsigned char* active;
+  const CellItem* items;
+  int nitems;
+  int item0;
+  const double* gout;           // gradient w.r.t. the stage output
+  const double* psi_fac;
+  double* gbuf[5];              // gradients w.r.t. U^n (0) and the stage states
+  const double* gL[3];
+  StageCoef co;
+  int kin;                      // index of the stage input U^(i-1)
+  int ndim;
+  int nv;
+};
+
 // launch wrappers (dispatch on physics / number of variables)
+cudaError_t launch_adj_flux(int physics, int nv, const AdjFluxParams& p, int grid, int block, size_t smem,
+                            cudaStream_t s);
+cudaError_t launch_adj_combine(int nv, const AdjCombParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_adj_passive(const AdjCombParams& p, int grid, int block, cudaStream_t s);
+cudaError_t launch_psi_fac(const unsigned long long* araw0, const double* dt, double* fac, int ndom, int ndim,
+                           double cr, int glm, cudaStream_t s);
 cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, int block, cudaStream_t s);
 cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s);
 cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, int block, cudaStream_t s);

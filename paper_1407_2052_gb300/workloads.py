@@ -182,7 +182,10 @@ def batched(nblocks=20000, sizes=(8, 12, 16, 24, 32), passive_frac=0.3, seed_ind
 
 def adjoint2d(n=512, seed_index=4, nmodes=16, amp=0.02):
     """2D MHD+GLM on periodic [0,2pi]^2, smooth seeded Fourier modes about the
-    batched background; B perturbed through A_z so that it is divergence free."""
+    batched background (rho, p, all three velocity components and B_z perturbed;
+    B_x, B_y perturbed through A_z so that the in-plane field is divergence free).
+    Every component varies, so no flux is identically zero: the update is
+    differentiable at the initial state (MP5 has kinks at exactly uniform data)."""
     rng = np.random.default_rng(SEED0 + seed_index)
     x, dx = centres(n, 0.0, 2 * np.pi)
     X, Y = np.meshgrid(x, x, indexing="xy")
@@ -199,7 +202,7 @@ def adjoint2d(n=512, seed_index=4, nmodes=16, amp=0.02):
 
     rho = 1.0 + modes()
     p = 1.0 + modes()
-    vel = [modes(), modes(), np.zeros_like(X)]
+    vel = [modes(), modes(), modes()]
     # A_z = sum c sin(k.x + phi): B_x = dA/dy, B_y = -dA/dx (analytic)
     bx = np.full_like(X, 0.5)
     by = np.zeros_like(X)
@@ -210,7 +213,8 @@ def adjoint2d(n=512, seed_index=4, nmodes=16, amp=0.02):
         arg = k[0] * X + k[1] * Y + ph
         bx += c * k[1] * np.cos(arg)
         by -= c * k[0] * np.cos(arg)
-    U = conserved_mhd(rho, vel, p, [bx, by, np.zeros_like(X)], 5.0 / 3.0).reshape(9, 1, n, n)
+    bz = modes()
+    U = conserved_mhd(rho, vel, p, [bx, by, bz], 5.0 / 3.0).reshape(9, 1, n, n)
     dom = Domain((n, n, 1), (dx, dx, 1.0))
     return Workload("adjoint2d", MHD_GLM, 2, SSPRK3, 5.0 / 3.0, 0.4, [dom], U, nsteps=200,
                     extra={"dt": 1e-3, "checkpoint_every": 20})

@@ -1,0 +1,211 @@
+"""Discrete adjoint (amrfd_adjoint) against independent derivatives.
+
+The forward map being transposed is one SSPRK step with the splitting speeds of
+every stage, the GLM speed and the psi damping factor held at their forward
+values (and a fixed dt). References:
+  * autograd of tests/torchref.py (plain FP64 PyTorch ops, CPU) with the speeds
+    the oracle's step used, relative max error <= 1e-10;
+  * central finite differences of the oracle's frozen-speed step along random
+    directions (h = 1e-6), relative error <= 1e-6;
+  * the checkpointed multi-step rollout equals the chain of single-step adjoints.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1407_2052_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+
+
+def _A():
+    from paper_1407_2052_gb300 import amrfd
+    return amrfd
+
+
+def _torchref():
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    import torchref
+    return torchref
+
+
+def _odom(d):
+    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb)
+
+
+def _gpu_adjoint(w, dt, g):
+    A = _A()
+    s = A.Solver.from_workload(w)
+    U = torch.from_numpy(np.ascontiguousarray(w.U.ravel())).cuda()
+    dtt = torch.full((s.ndom,), dt, dtype=torch.float64, device="cuda")
+    gg = torch.from_numpy(np.ascontiguousarray(g.ravel())).cuda()
+    out = torch.empty_like(U)
+    s.adjoint(U, dtt, gg, out)
+    assert s.error() == A.OK
+    return out.cpu().numpy().reshape(w.U.shape), s
+
+
+def _ref_grad(w, dt, g):
+    T = _torchref()
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    _, fl, al, ch = O.step(c, _odom(w.domains[0]), w.U, dt)
+    U = torch.from_numpy(w.U.copy()).requires_grad_(True)
+    out = T.step(U, dt, w.domains[0].dx, w.domains[0].bc, w.physics, w.ndim, w.gamma, w.integrator, al, ch,
+                 w.glm_cr)
+    (out * torch.from_numpy(g)).sum().backward()
+    return U.grad.numpy(), al, ch
+
+
+def _smooth(physics, ndim, n, bc, seed, integrator):
+    rng = np.random.default_rng(seed)
+    g = 1.4 if physics == O.EULER else 5 / 3
+    dx = [1.0 / n[0], 1.0 / max(n[1], 1), 1.0 / max(n[2], 1)]
+    axes = [(np.arange(m) + 0.5) / m for m in n]
+    Z, Y, X = np.meshgrid(axes[2], axes[1], axes[0], indexing="ij")
+
+    def f(a):
+        k = rng.integers(1, 3, 3) * np.array([1, ndim > 1, ndim > 2])
+        return a * np.sin(2 * np.pi * (k[0] * X + k[1] * Y + k[2] * Z) + rng.uniform(0, 6.28))
+    rho, p = 1.0 + f(0.2), 1.0 + f(0.2)
+    vel = [f(0.3) + 0.1 for _ in range(3)]
+    if physics == O.EULER:
+        U = W.conserved_euler(rho, vel[:ndim], p, g)
+    else:
+        U = W.conserved_mhd(rho, vel, p, [0.5 + f(0.1), 0.2 + f(0.1), 0.1 + f(0.1)], g, psi=f(0.01))
+    dom = W.Domain(tuple(n), tuple(dx), bc=bc)
+    return W.Workload("smooth", physics, ndim, integrator, g, 0.4, [dom], U, active=np.ones(1, np.uint8))
+
+
+CASES = [
+    ("mhd2d_ssprk3", lambda: W.adjoint2d(32), 1e-3),
+    ("mhd2d_ssprk54", lambda: W.Workload(**{**W.adjoint2d(32).__dict__, "integrator": O.SSPRK54}), 1e-3),
+    ("euler1d_outflow", lambda: _smooth(O.EULER, 1, (40, 1, 1), ((1, 1), (0, 0), (0, 0)), 1, O.SSPRK3), 2e-3),
+    ("euler2d_mixed", lambda: _smooth(O.EULER, 2, (24, 20, 1), ((1, 1), (0, 0), (0, 0)), 2, O.SSPRK54), 2e-3),
+    ("mhd3d_mixed", lambda: _smooth(O.MHD_GLM, 3, (12, 10, 8), ((0, 0), (1, 1), (0, 0)), 3, O.SSPRK3), 1e-3),
+]
+
+
+@pytest.mark.parametrize("name,make,dt", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_matches_autograd_of_torch_reference(name, make, dt):
+    w = make()
+    g = np.random.default_rng(7).standard_normal(w.U.shape)
+    got, _ = _gpu_adjoint(w, dt, g)
+    want, _, _ = _ref_grad(w, dt, g)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err <= 1e-10, err
+
+
+@pytest.mark.parametrize("name,make,dt", CASES[:1] + CASES[4:], ids=[CASES[0][0], CASES[4][0]])
+def test_adjoint_against_oracle_central_differences(name, make, dt):
+    w = make()
+    rng = np.random.default_rng(11)
+    g = rng.standard_normal(w.U.shape)
+    got, _ = _gpu_adjoint(w, dt, g)
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    d = _odom(w.domains[0])
+    _, _, al, ch = O.step(c, d, w.U, dt)
+    h = 1e-6
+    for _ in range(5):
+        v = rng.standard_normal(w.U.shape)
+        v /= np.linalg.norm(v)
+        up, _ = O.step_frozen(c, d, w.U + h * v, dt, al, ch)
+        um, _ = O.step_frozen(c, d, w.U - h * v, dt, al, ch)
+        fd = float(np.sum(g * (up - um)) / (2 * h))
+        ad = float(np.sum(got * v))
+        assert abs(fd - ad) <= 1e-6 * max(abs(fd), 1e-12), (fd, ad)
+
+
+def test_checkpointed_rollout_equals_chained_adjoints():
+    from paper_1407_2052_gb300 import autodiff
+    A = _A()
+    w = W.adjoint2d(48)
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel().copy()).cuda()
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    nsteps, every = 12, 5
+    U0r = U0.clone().requires_grad_(True)
+    Uf = autodiff.rollout(s, U0r, dt, nsteps, every)
+    B = Uf.view(9, -1)[5:8]
+    J = 0.5 * (B * B).sum() * w.domains[0].dx[0] * w.domains[0].dx[1]
+    J.backward()
+    grad = U0r.grad.clone()
+    # chain of single-step adjoints over stored states
+    states = [U0.clone()]
+    for _ in range(nsteps):
+        nxt = states[-1].clone()
+        s.step_batched(nxt, dt)
+        states.append(nxt)
+    assert torch.equal(states[-1], Uf.detach())
+    gB = torch.zeros_like(U0).view(9, -1)
+    gB[5:8] = states[-1].view(9, -1)[5:8] * (w.domains[0].dx[0] * w.domains[0].dx[1])
+    g = gB.view(-1).clone()
+    out = torch.empty_like(g)
+    for j in reversed(range(nsteps)):
+        s.adjoint(states[j], dt, g, out)
+        g, out = out, g
+    assert torch.equal(g, grad)
+
+
+def test_rollout_matches_torch_reference_over_steps():
+    """Three steps at 24^2: GPU rollout gradient vs autograd through three torchref steps,
+    each with the speeds of the oracle's trajectory."""
+    from paper_1407_2052_gb300 import autodiff
+    A = _A()
+    T = _torchref()
+    w = W.adjoint2d(24)
+    dtv, nsteps = 1e-3, 3
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel().copy()).cuda().requires_grad_(True)
+    dt = torch.full((1,), dtv, dtype=torch.float64, device="cuda")
+    Uf = autodiff.rollout(s, U0, dt, nsteps, 2)
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(w.U.size)).cuda()
+    (Uf * g).sum().backward()
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    d = _odom(w.domains[0])
+    Ut = torch.from_numpy(w.U.copy()).requires_grad_(True)
+    Uc, Un = Ut, w.U.copy()
+    for _ in range(nsteps):
+        Un, _, al, ch = O.step(c, d, Un, dtv)
+        Uc = T.step(Uc, dtv, w.domains[0].dx, w.domains[0].bc, w.physics, w.ndim, w.gamma, w.integrator, al, ch,
+                    w.glm_cr)
+    (Uc * g.cpu().view(w.U.shape)).sum().backward()
+    want = Ut.grad.numpy().ravel()
+    got = U0.grad.cpu().numpy()
+    assert np.abs(got - want).max() / np.abs(want).max() <= 1e-10
+
+
+def test_adjoint_passive_blocks_pass_through():
+    A = _A()
+    w = W.batched(nblocks=12, sizes=(8, 12))
+    s = A.Solver.from_workload(w)
+    U = torch.from_numpy(w.U.copy()).cuda()
+    dt = torch.full((s.ndom,), 1e-4, dtype=torch.float64, device="cuda")
+    g = torch.from_numpy(np.random.default_rng(5).standard_normal(w.U.size)).cuda()
+    out = torch.empty_like(U)
+    s.adjoint(U, dt, g, out)
+    got, gg = out.cpu().numpy(), g.cpu().numpy()
+    T = _torchref()
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    for i, dd in enumerate(w.domains):
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        if not w.active[i]:
+            assert np.array_equal(got[sl], gg[sl])
+            continue
+        shape = (9,) + tuple(dd.n[::-1])
+        _, _, al, ch = O.step(c, _odom(dd), w.U[sl].reshape(shape), 1e-4)
+        Ut = torch.from_numpy(w.U[sl].reshape(shape).copy()).requires_grad_(True)
+        o = T.step(Ut, 1e-4, dd.dx, dd.bc, w.physics, w.ndim, w.gamma, w.integrator, al, ch, w.glm_cr)
+        (o * torch.from_numpy(gg[sl].reshape(shape))).sum().backward()
+        want = Ut.grad.numpy().ravel()
+        assert np.abs(got[sl] - want).max() / np.abs(want).max() <= 1e-10, i
