@@ -99,6 +99,72 @@ def cpu_baseline(cells_side=128, block=16):
             "sample": "one CFL dt + one SSPRK3 step of the %d^3 blast (%d^3 blocks), %.1f s" % (cells_side, block, el)}
 
 
+def batched_extra(torch, A, W, steps=2):
+    """20000 uneven independent blocks, 30% passive: persistent work-list launches
+    (graph) vs one launch per domain (block) per pass; active cell-updates/s."""
+    w = W.batched(20000)
+    s = A.Solver.from_workload(w)
+    ncell_active = sum(d.ncell for d, a in zip(w.domains, w.active) if a)
+    U0 = torch.from_numpy(w.U).cuda()
+    del w
+    U = U0.clone()
+    dt = torch.empty(s.ndom, dtype=torch.float64, device="cuda")
+    out = {"workload": "20000 blocks, edges {8,12,16,24,32}^3, 30% passive, MHD+GLM SSPRK3",
+           "active_cells": ncell_active}
+    for name, fn in (("persistent", s.step_batched), ("per_block", s.step)):
+        U.copy_(U0)
+        s.dt(U, out=dt)
+        fn(U, dt)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            s.dt(U, out=dt)
+            fn(U, dt)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "cell_updates_per_s": ncell_active / (ms * 1e-3)}
+    assert s.error() == A.OK
+    out["speedup"] = out["per_block"]["ms_per_step"] / out["persistent"]["ms_per_step"]
+    s.close()
+    del U, U0
+    torch.cuda.empty_cache()
+    return out
+
+
+def adjoint_extra(torch, A, W, reps=3):
+    """2D MHD+GLM 512^2, fixed dt 1e-3, SSPRK3: one adjoint step vs one forward step."""
+    w = W.adjoint2d(512)
+    s = A.Solver.from_workload(w)
+    U = torch.from_numpy(w.U.ravel().copy()).cuda()
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    g = torch.randn(U.numel(), dtype=torch.float64, device="cuda")
+    gout = torch.empty_like(U)
+    V = U.clone()
+    s.step_batched(V, dt)
+    s.adjoint(U, dt, g, gout)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        V.copy_(U)
+        s.step_batched(V, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd = e0.elapsed_time(e1) / reps
+    e0.record()
+    for _ in range(reps):
+        s.adjoint(U, dt, g, gout)
+    e1.record()
+    torch.cuda.synchronize()
+    adj = e0.elapsed_time(e1) / reps
+    assert s.error() == A.OK
+    s.close()
+    return {"workload": "adjoint2d: 2D MHD+GLM 512^2, SSPRK3, dt 1e-3", "forward_ms": fwd, "adjoint_ms": adj,
+            "ratio": adj / fwd}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -278,6 +344,9 @@ def run_ours(args, rank, world, local_rank):
     s.close()
     del U, U0
     torch.cuda.empty_cache()
+    if rank == 0 and world == 1 and not args.no_extras:
+        out["batched"] = batched_extra(torch, A, W)
+        out["adjoint"] = adjoint_extra(torch, A, W)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if dist is not None:
@@ -294,6 +363,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched-block and adjoint comparisons")
     ap.add_argument("--n", type=int, default=N_BLAST, help="cells per side of the blast (profiling of small cases)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -106,7 +106,15 @@ def test_adjoint_matches_autograd_of_torch_reference(name, make, dt):
     assert err <= 1e-10, err
 
 
-@pytest.mark.parametrize("name,make,dt", CASES[:1] + CASES[4:], ids=[CASES[0][0], CASES[4][0]])
+FD_CASES = [
+    # well resolved (>= 32 cells per wavelength): the limiter stays on one linear piece
+    # under the perturbation; at 32^2 the same data sits on MP5 kinks near extrema
+    ("mhd2d_128", lambda: W.adjoint2d(128), 1e-3),
+    CASES[4],
+]
+
+
+@pytest.mark.parametrize("name,make,dt", FD_CASES, ids=[c[0] for c in FD_CASES])
 def test_adjoint_against_oracle_central_differences(name, make, dt):
     w = make()
     rng = np.random.default_rng(11)
