@@ -32,11 +32,17 @@ BYTES_PER_CELL_UPDATE = 64 * NV
 # Minimal HBM bytes of one flux pass per cell: read U^(k) (nv doubles) and write
 # the three per-direction residuals (3 nv doubles).
 FLUX_BYTES_PER_CELL = 4 * NV * 8
-# FP64 operations of one flux pass per cell and direction, counted by ncu
-# (DADD + DMUL + 2 DFMA per executed thread instruction) on this workload; see
-# profiles/flux_kernel_blast3d.md. None until measured.
-FLUX_FLOPS_PER_CELL_DIR = None
+# FP64 work of one flux pass per cell and direction, counted by ncu on the blast
+# (profiles/flux_kernel_blast3d.md): DADD + DMUL + 2 DFMA thread instructions = flop,
+# and DADD + DMUL + DFMA = FP64 pipe instructions.
+FLUX_FLOPS_PER_CELL_DIR = 412.2
+FLUX_FP64_INST_PER_CELL_DIR = 293.1
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (profiling recipe table)
+# FP64 pipe: 2 thread instructions / clock / SM (ncu peak_sustained) x 152 SMs x 2.07 GHz
+FP64_PEAK_GINST = 2 * 152 * 2.07
+# DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write, 128^3 capture,
+# scaled by cells): traffic grows with the cells processed
+FLUX_TRAFFIC_BYTES_PER_CELL = (190.86336 + 398.993664) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):
@@ -313,9 +319,13 @@ def run_ours(args, rank, world, local_rank):
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     if FLUX_FLOPS_PER_CELL_DIR:
         achieved = FLUX_FLOPS_PER_CELL_DIR * 3 * ncell / flux_avg_s / 1e12
+        ginst = FLUX_FP64_INST_PER_CELL_DIR * 3 * ncell / flux_avg_s / 1e9
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_TFLOPS_NOMINAL,
-                "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": None, "kernel": "flux_kernel",
-                "peak_source": "FP64 nominal of the profiling recipe"}
+                "frac": achieved / FP64_PEAK_TFLOPS_NOMINAL, "traffic": FLUX_TRAFFIC_BYTES_PER_CELL * ncell,
+                "kernel": "flux_kernel", "flop_per_cell_dir": FLUX_FLOPS_PER_CELL_DIR,
+                "launch_ms": flux_avg_s * 1e3,
+                "fp64_pipe_frac": ginst / FP64_PEAK_GINST,
+                "peak_source": "FP64 nominal of the profiling recipe (1.25 TFLOP/s; ncu peak 2 DFMA/clk/SM)"}
     else:
         roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": None, "peak": FP64_PEAK_TFLOPS_NOMINAL,
                 "frac": None, "traffic": None, "kernel": "flux_kernel"}
