@@ -121,6 +121,47 @@ __device__ __forceinline__ double dscale(double x) {
 
 __device__ __forceinline__ double dneg(double x) { return bitsd(dbits(x) ^ (long long)0x8000000000000000ULL); }
 
+// |x| rounded toward zero to FP32, from the bits of |x| whose exponent lies in
+// [2^-60, 2^61) (caller checks): the mantissa's top 23 bits and a rebiased exponent.
+__device__ __forceinline__ float f32_trunc_abs(long long ax) {
+  float r;
+  asm("{\n\t.reg .b64 t;\n\t.reg .b32 u;\n\t"
+      "shr.u64 t, %1, 29;\n\tsub.u64 t, t, 7516192768;\n\tcvt.u32.u64 u, t;\n\tmov.b32 %0, u;\n\t}"
+      : "=f"(r) : "l"(ax));
+  return r;
+}
+
+// The MP acceptance test fl(X * fl(X - mp)) <= eps, decided exactly as the FP64
+// expression decides it. Signs are read from the bit patterns; a product of
+// like-signed factors is estimated in FP32 with a rigorous error bound (inputs
+// truncated to 23 bits, three FP32 roundings, the two FP64 roundings), and only
+// an estimate within the bound of eps falls back to the FP64 evaluation.
+__device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
+  const long long bx = dbits(X), bm = dbits(mp);
+  const long long M = 0x7fffffffffffffffLL;
+  const long long ax = bx & M, am = bm & M;
+  if (ax == 0) return true;                       // X = +-0: product +-0
+  const long long kx = okey(X), km = okey(mp);
+  if (kx == km) return true;                      // X == mp: zero difference
+  if ((kx > km) != (bx >= 0)) return true;        // X and X - mp of opposite sign: product <= 0
+  const int ex = (int)(ax >> 52), em = (int)(am >> 52);
+  const bool in_range = ex >= 963 && ex <= 1083 && (am == 0 || (em >= 963 && em <= 1083));
+  if (in_range) {
+    const float fx = f32_trunc_abs(ax);
+    const float fm0 = am == 0 ? 0.0f : f32_trunc_abs(am);
+    // |X - mp| = |X| - s mp with s = sign(X): the subtrahend keeps its magnitude, its
+    // sign is flipped when mp and X have opposite signs
+    const float fm = ((bx ^ bm) < 0) ? -fm0 : fm0;
+    const float df = fx - fm;
+    const float pe = fx * df;
+    const float bound = 9.5367431640625e-07f * fmaf(fx, fx + fabsf(fm), fabsf(pe));  // 2^-20 (...)
+    const float ef = (float)eps;
+    if (pe + bound < ef * 0.99999809f) return true;   // ef (1 - 2^-19)
+    if (pe - bound > ef * 1.00000191f) return false;  // ef (1 + 2^-19)
+  }
+  return ile_pos(X * (X - mp), eps);
+}
+
 // ---------------------------------------------------------- MP5 in difference form
 // MP5 (Suresh & Huynh 1997) at face i+1/2 from (f_{i-2}, ..., f_{i+2}), written in
 // differences Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1}
@@ -146,8 +187,7 @@ __device__ __forceinline__ double mp5_rel2(double Dm, double D0, double D1, doub
   const double ul = dscale<3>(d0);     // 2 (f_ul - f_i)
   const double d1x2 = dscale<1>(d1);   // 2 (f_{i+1} - f_i)
   const double mp = iminmod(d1x2, ul);  // 2 (f_mp - f_i)
-  const double chk = X * (X - mp);
-  if (ile_pos(chk, eps16)) return X;
+  if (mp_accept(X, mp, eps16)) return X;
   const double md = d1 - Mp;                  // 2 (f_md - f_i)
   const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
   const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
@@ -217,9 +257,8 @@ __device__ __forceinline__ double mp5_rel2_sel(double Dm, double D0, double D1, 
   const double ul = dscale<3>(d0);
   const double d1x2 = dscale<1>(d1);
   const double mp = iminmod(d1x2, ul);
-  const double chk = X * (X - mp);
   code = SEL_X;
-  if (ile_pos(chk, eps16)) return X;
+  if (mp_accept(X, mp, eps16)) return X;
   const double md = d1 - Mp;
   const double lc = fma(8.0 / 3.0, Mm, d0);
   double a, b, fmin, fmax, t1, t2, t3;
