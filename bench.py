@@ -236,6 +236,10 @@ def run_ours(args, rank, world, local_rank):
         s.dt(U, out=dt)
         s.step_batched(U, dt)
 
+    tile_default = list(s.get_tile())
+    if not args.no_autotune:
+        s.dt(U, out=dt)
+        s.autotune(U, dt)
     for _ in range(args.warmup):
         one_step()
     barrier()
@@ -337,7 +341,8 @@ def run_ours(args, rank, world, local_rank):
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": "blast3d: 3D ideal MHD+GLM blast, %d^3 cells in 16^3 blocks, SSPRK3, CFL 0.3" % nside,
                    "cells": ncell, "integrator": "SSPRK3", "parallelism": "replicas" if world > 1 else "single",
-                   "l2": "inputs larger than L2 (%.2f GB state)" % (ncell * NV * 8 / 1e9), "tile": list(s.get_tile())},
+                   "l2": "inputs larger than L2 (%.2f GB state)" % (ncell * NV * 8 / 1e9), "tile": list(s.get_tile()),
+                   "tile_default": tile_default, "autotuned": not args.no_autotune},
         "gpu_launches": launches,
         "kernel_ms": {k: {"total": v[0], "launches": v[1]} for k, v in kt.items()},
         "graph_ms_per_step": graph_ms,
@@ -374,6 +379,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-block and adjoint comparisons")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default flux-pass tile")
     ap.add_argument("--n", type=int, default=N_BLAST, help="cells per side of the blast (profiling of small cases)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -6,8 +6,9 @@
 // where D_d(S)_j = Fsum_j - Fsum_{j+1} and Fsum_k = G+_{k-1} + G-_k + (Y+_k + Y-_k)/2
 // is the interface flux of Sec. 2.2 in units of 2 F^ (G = F +- c_max U). Every MP5
 // value Y is piecewise linear in its stencil once the limiter's choices are fixed;
-// the adjoint recomputes the forward values bit for bit, reads off the chosen
-// pieces and applies their transposes. Gradients are gathered per cell (no atomics):
+// the forward recomputation records, per face, variable and bias, which pieces the
+// limiter took (a 9-bit tape), and the adjoint applies their transposes without
+// re-evaluating the limiter. Gradients are gathered per cell (no atomics):
 // a segment recomputes the faces within reach of its cells (two beyond on the low
 // side, three on the high side) and keeps only contributions to its own cells;
 // with outflow faces the ghost copies of an edge cell fold back into it.
@@ -126,48 +127,25 @@ __device__ __forceinline__ void split_flux_adj(const double* u, double gm1, doub
   }
 }
 
-// Backward of one face k for one variable: gradients of Fsum_k w.r.t. the G+ and
-// G- values of its stencil, times gF, accumulated into gGp / gGm (smem lines
-// indexed by position q; the face's left cell is at q = qk - 1).
+// Backward of one reconstruction at face k for one variable, from the recorded
+// pieces: rec = (piece of the MP5 value) | (piece of Mp) << 3 | (piece of Mm) << 6.
+// The stencil occupies positions q0..q0+4 of the line window; NEG is the mirrored
+// (right-biased) reconstruction. Accumulates d(value)/dG * gY into gG.
 template <bool NEG>
-__device__ __forceinline__ void face_adj(const double* G, double* gG, int q0, double gY, double eps16) {
-  // stencil positions q0 .. q0+4 in the orientation of the + reconstruction:
-  // NEG=false: (a,b,c,d,e) = G[q0..q0+4], centre c;  NEG=true: mirrored, G[q0+4..q0].
-  const double a = G[q0], b = G[q0 + 1], c = G[q0 + 2], d = G[q0 + 3], e = G[q0 + 4];
-  double Dm, D0, D1, Dp, kL, kC, kR;
-  if (!NEG) {
-    Dm = b - a; D0 = c - b; D1 = d - c; Dp = e - d;
-    kL = D0 - Dm; kC = D1 - D0; kR = Dp - D1;   // curvatures at q0+1, q0+2, q0+3
-  } else {
-    // forward differences along the line: h1 = b-a (at q0+1), h2 = c-b, h3 = d-c, h4 = e-d;
-    // the mirrored stencil centred on q0+2 takes (Dm, D0, D1, Dp) = (h4, h3, h2, h1) negated
-    const double h1 = b - a, h2 = c - b, h3 = d - c, h4 = e - d;
-    Dm = h4; D0 = h3; D1 = h2; Dp = h1;
-    kL = h2 - h1; kC = h3 - h2; kR = h4 - h3;   // curvatures at q0+1, q0+2, q0+3 (line order)
-  }
-  int cp, cm, code;
-  double Mp, Mm;
-  if (!NEG) {
-    Mm = dm4_sel(kL, kC, cm);  // at the face left of the centre
-    Mp = dm4_sel(kC, kR, cp);  // at the face right of the centre
-    (void)mp5_rel2_sel<false>(Dm, D0, D1, Dp, Mp, Mm, eps16, code);
-  } else {
-    Mp = dm4_sel(kL, kC, cp);  // mirror: the face on the low side of the centre is its "i+1/2"
-    Mm = dm4_sel(kC, kR, cm);
-    (void)mp5_rel2_sel<true>(Dm, D0, D1, Dp, Mp, Mm, eps16, code);
-  }
+__device__ __forceinline__ void face_adj(double* gG, int q0, double gY, unsigned rec) {
   double gDm, gD0, gD1, gDp, gMp, gMm;
-  if (!NEG) mp5_rel2_grad<false>(code, gY, gDm, gD0, gD1, gDp, gMp, gMm);
-  else mp5_rel2_grad<true>(code, gY, gDm, gD0, gD1, gDp, gMp, gMm);
+  if (!NEG) mp5_rel2_grad<false>(rec & 7, gY, gDm, gD0, gD1, gDp, gMp, gMm);
+  else mp5_rel2_grad<true>(rec & 7, gY, gDm, gD0, gD1, gDp, gMp, gMm);
+  // curvatures kL, kC, kR at q0+1, q0+2, q0+3 (line order)
   double gkL = 0.0, gkC = 0.0, gkR = 0.0, t1, t2;
   if (!NEG) {
-    dm4_grad(cm, gMm, t1, t2); gkL += t1; gkC += t2;
-    dm4_grad(cp, gMp, t1, t2); gkC += t1; gkR += t2;
+    dm4_grad((rec >> 6) & 7, gMm, t1, t2); gkL += t1; gkC += t2;  // Mm from (kL, kC)
+    dm4_grad((rec >> 3) & 7, gMp, t1, t2); gkC += t1; gkR += t2;  // Mp from (kC, kR)
   } else {
-    dm4_grad(cp, gMp, t1, t2); gkL += t1; gkC += t2;
-    dm4_grad(cm, gMm, t1, t2); gkC += t1; gkR += t2;
+    dm4_grad((rec >> 3) & 7, gMp, t1, t2); gkL += t1; gkC += t2;  // mirrored: Mp from (kL, kC)
+    dm4_grad((rec >> 6) & 7, gMm, t1, t2); gkC += t1; gkR += t2;  // Mm from (kC, kR)
   }
-  // gradients of the line differences h1..h4 (h_j = G[q0+j] - G[q0+j-1])
+  // gradients of the line differences h_j = G[q0+j] - G[q0+j-1], j = 1..4
   double gh1, gh2, gh3, gh4;
   if (!NEG) { gh1 = gDm; gh2 = gD0; gh3 = gD1; gh4 = gDp; }
   else { gh1 = gDp; gh2 = gD1; gh3 = gD0; gh4 = gDm; }
@@ -203,54 +181,40 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
   const int n = dm.n[D];
   const int s0 = o[D] + it.s0;               // first cell of the segment (domain coordinate)
   const int WA = slen + 10, WG = slen + 6;
-  double* Gp = sm;                            // [NV][P][SA]
-  double* Gm = Gp + NV * P * SA;
-  double* gGp = Gm + NV * P * SA;
+  double* gGp = sm;                           // [NV][P][SA] gradient w.r.t. G+ at positions s0-5 ..
   double* gGm = gGp + NV * P * SA;
-  double* gh = gGm + NV * P * SA;             // [NV][P][SG] scaled upstream gradient
-  // ---- phase A: forward G+- at positions s0-5 .. s0+slen+4, upstream gradient at s0-3 .. s0+slen+2
+  double* gh = gGm + NV * P * SA;             // [NV][P][SG] scaled upstream gradient at s0-3 ..
+  // ---- phase A: upstream gradient at s0-3 .. s0+slen+2 (zero beyond an outflow face)
   for (int c = threadIdx.x; c < nl * WA; c += blockDim.x) {
     int pl, q;
     if (D == 0) { pl = c / WA; q = c - pl * WA; }
     else { q = c / nl; pl = c - q * nl; }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      gGp[(v * P + pl) * SA + q] = 0.0;
+      gGm[(v * P + pl) * SA + q] = 0.0;
+    }
+    const int r = q - 2;
+    if (r < 0 || r >= WG) continue;
     const int line = it.l0 + pl;
     const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
     int x[3];
     x[od1] = o[od1] + a1;
     x[od2] = o[od2] + a2;
-    const int pos = s0 - 5 + q;
-    int g = pos;
-    bool inside = true;
-    if (g < 0) { inside = false; g = dm.bc[D][0] == 0 ? ((g % n) + n) % n : 0; }
-    else if (g >= n) { inside = false; g = dm.bc[D][1] == 0 ? g % n : n - 1; }
+    int g = s0 - 3 + r;
+    bool live = true;
+    if (g < 0) { live = dm.bc[D][0] == 0; g = ((g % n) + n) % n; }
+    else if (g >= n) { live = dm.bc[D][1] == 0; g = g % n; }
     x[D] = g;
-    const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
-    const double* base = p.active[nbk] ? p.S : p.Un;
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
-    double u[NV], gp[NV], gmn[NV];
-#pragma unroll
-    for (int v = 0; v < NV; v++) u[v] = base[dm.off + idx + (long long)v * dm.ncell];
-    split_flux<PHYS, NV, D>(u, p.gm1, alpha, ch2, gp, gmn);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-      Gp[(v * P + pl) * SA + q] = gp[v];
-      Gm[(v * P + pl) * SA + q] = gmn[v];
-      gGp[(v * P + pl) * SA + q] = 0.0;
-      gGm[(v * P + pl) * SA + q] = 0.0;
-    }
-    const int r = q - 2;  // gradient window starts two positions later
-    if (r >= 0 && r < WG) {
-      const bool periodic_side = pos < 0 ? dm.bc[D][0] == 0 : (pos >= n ? dm.bc[D][1] == 0 : true);
-      const bool live = inside || periodic_side;
-#pragma unroll
-      for (int v = 0; v < NV; v++) {
-        double gv = 0.0;
-        if (live) {
-          gv = p.G[dm.off + idx + (long long)v * dm.ncell] * w;
-          if (PHYS == PH_MHD && v == 8) gv *= pfac;
-        }
-        gh[(v * P + pl) * SG + r] = gv;
+      double gv = 0.0;
+      if (live) {
+        gv = p.G[dm.off + idx + (long long)v * dm.ncell] * w;
+        if (PHYS == PH_MHD && v == 8) gv *= pfac;
       }
+      gh[(v * P + pl) * SG + r] = gv;
     }
   }
   __syncthreads();
@@ -258,24 +222,28 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
   int kb = s0 - 2, ke = s0 + slen + 2;
   if (dm.bc[D][0] == 1 && kb < 0) kb = 0;
   if (dm.bc[D][1] == 1 && ke > n) ke = n;
-  const double eps16 = 16.0 * 1e-10;
+  const long long nlines = (long long)dm.n[od1] * dm.n[od2];
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
-    const double* gpl = Gp + (v * P + pl) * SA;
-    const double* gml = Gm + (v * P + pl) * SA;
     double* ggp = gGp + (v * P + pl) * SA;
     double* ggm = gGm + (v * P + pl) * SA;
     const double* ghl = gh + (v * P + pl) * SG;
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
+    const unsigned short* tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (n + 1);
+    const unsigned short* tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (n + 1);
     for (int k = kb; k <= ke; k++) {
       const int qk = k - (s0 - 5);        // position of cell k in the G window
       const int rk = k - (s0 - 3);        // position of cell k in the gradient window
       const double gF = ghl[rk] - ghl[rk - 1];
       if (gF == 0.0) continue;
+      const int f = (k < 0) ? k + n : (k >= n && dm.bc[D][1] == 0 ? k - n : k);  // periodic faces wrap
       ggp[qk - 1] += gF;
       ggm[qk] += gF;
       const double gY = 0.5 * gF;
-      face_adj<false>(gpl, ggp, qk - 3, gY, eps16);  // + stencil: cells k-3 .. k+1, centre k-1
-      face_adj<true>(gml, ggm, qk - 2, gY, eps16);   // - stencil: cells k-2 .. k+2, centre k
+      face_adj<false>(ggp, qk - 3, gY, tp[f]);  // + stencil: cells k-3 .. k+1, centre k-1
+      face_adj<true>(ggm, qk - 2, gY, tm[f]);   // - stencil: cells k-2 .. k+2, centre k
     }
     // outflow: ghost copies of an edge cell fold back into it
     if (dm.bc[D][0] == 1 && s0 == 0) {

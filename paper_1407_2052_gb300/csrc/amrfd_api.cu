@@ -95,6 +95,8 @@ struct amrfd_handle {
   // adjoint workspace (allocated on the first amrfd_adjoint call)
   double* d_gstage[kMaxStages] = {};
   double* d_psifac = nullptr;
+  unsigned short* d_tape = nullptr;   // limiter pieces of every face, per stage
+  long long tape_len = 0;             // records per stage
   FluxItem* d_adj_items = nullptr;
   int adj_nitems = 0;
   int adj_seg = 16, adj_lines = 8, adj_threads = 128;
@@ -464,6 +466,13 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
     dm.off = domains[i].offset;
     h->nelem = std::max(h->nelem, (size_t)(dm.off + (long long)h->nv * dm.ncell));
     nb += dm.nb[0] * dm.nb[1] * dm.nb[2];
+    for (int k = 0; k < 3; k++) {
+      dm.tape_off[k] = h->tape_len;
+      if (k < cfg->ndim) {
+        const int od1 = k == 0 ? 1 : 0, od2 = k == 2 ? 1 : 2;
+        h->tape_len += (long long)h->nv * 2 * dm.n[od1] * dm.n[od2] * (dm.n[k] + 1);
+      }
+    }
     h->hdom.push_back(dm);
   }
   h->nblocks = nb;
@@ -605,7 +614,7 @@ int build_adjoint_items(amrfd_handle* h) {
   h->adj_P = h->adj_lines;
   h->adj_SSa = maxseg + 10 + ((maxseg + 10) % 2 == 0 ? 1 : 0);
   h->adj_SSg = maxseg + 6 + ((maxseg + 6) % 2 == 0 ? 1 : 0);
-  h->adj_smem = sizeof(double) * (size_t)h->nv * h->adj_P * (4 * h->adj_SSa + h->adj_SSg);
+  h->adj_smem = sizeof(double) * (size_t)h->nv * h->adj_P * (2 * h->adj_SSa + h->adj_SSg);
   CK(cudaMalloc(&h->d_adj_items, sizeof(FluxItem) * std::max(1, h->adj_nitems)));
   CK(cudaMemcpy(h->d_adj_items, fi.data(), sizeof(FluxItem) * h->adj_nitems, cudaMemcpyHostToDevice));
   return AMRFD_OK;
@@ -630,6 +639,8 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
   if (!h->d_adj_items) {
     for (int k = 1; k < h->ns; k++) CK(cudaMalloc(&h->d_gstage[k], sizeof(double) * h->nelem));
     CK(cudaMalloc(&h->d_psifac, sizeof(double) * h->ndom));
+    CK(cudaMalloc(&h->d_tape, sizeof(unsigned short) * std::max<long long>(1, h->tape_len) * h->ns));
+    CK(flux_rec_set_smem(h->cfg.physics, h->nv, h->flux_smem));
     int rc = build_adjoint_items(h);
     if (rc) return rc;
   }
@@ -644,11 +655,17 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
     CK(launch_speeds(ph, nv, p, cgrid, 256, s));
   }
-  for (int i = 1; i < h->ns; i++) {
+  for (int i = 1; i <= h->ns; i++) {
+    // every stage's flux pass records the limiter's pieces; states up to U^(s-1)
     const double* Uk = (i == 1) ? U_n : h->d_stage[i - 1];
     FluxParams fp = flux_params(h, Uk, U_n, i - 1);
     fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
-    CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+    fp.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
+    {
+      Tick tk(h, K_FLUX, s);
+      CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+    }
+    if (i == h->ns) break;
     CombParams cp = comb_params(h, Un, dt_dev, i);
     cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
     CK(launch_combine(ph, nv, cp, cgrid, 256, s));
@@ -681,6 +698,7 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     ap.SSa = h->adj_SSa;
     ap.SSg = h->adj_SSg;
     ap.glm = h->cfg.physics == AMRFD_MHD_GLM;
+    ap.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
     {
       Tick tk(h, K_FLUX, s);
       CK(launch_adj_flux(ph, nv, ap, std::min(ap.nitems, 16 * h->nsm), h->adj_threads, h->adj_smem, s));
@@ -851,6 +869,7 @@ void amrfd_destroy(amrfd_handle* h) {
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_stage[k]);
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_gstage[k]);
   cudaFree(h->d_psifac);
+  cudaFree(h->d_tape);
   cudaFree(h->d_adj_items);
   for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
   cudaFree(h->d_slot); cudaFree(h->d_err);

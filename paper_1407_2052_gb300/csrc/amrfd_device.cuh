@@ -131,6 +131,12 @@ __device__ __forceinline__ float f32_trunc_abs(long long ax) {
   return r;
 }
 
+// FP64 evaluation of the acceptance test, out of line so that it costs nothing
+// unless taken.
+static __device__ __noinline__ bool mp_accept_slow(double X, double mp, double eps) {
+  return ile_pos(X * (X - mp), eps);
+}
+
 // The MP acceptance test fl(X * fl(X - mp)) <= eps, decided exactly as the FP64
 // expression decides it. Signs are read from the bit patterns; a product of
 // like-signed factors is estimated in FP32 with a rigorous error bound (inputs
@@ -159,7 +165,7 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
     if (pe + bound < ef * 0.99999809f) return true;   // ef (1 - 2^-19)
     if (pe - bound > ef * 1.00000191f) return false;  // ef (1 + 2^-19)
   }
-  return ile_pos(X * (X - mp), eps);
+  return mp_accept_slow(X, mp, eps);
 }
 
 // ---------------------------------------------------------- MP5 in difference form

@@ -20,6 +20,7 @@ struct DomDev {
   int ncell;         // n0*n1*n2
   long long off;     // element offset in every state-shaped buffer
   double dx[3];
+  long long tape_off[3];  // offset (records) of this domain's limiter tape, per direction
 };
 
 // One flux-pass work item: `nl` lines along direction `d` inside block `blk`

@@ -147,33 +147,60 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 // line's extended index (cell j = k-1 left of face k), then the flux difference
 // Fsum_{k-1} - Fsum_k of cells j = 3..slen+2 written back over the consumed part of
 // the G^+ line (the factor 1/(2 dx) is applied by the stage combination).
-__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double eps16) {
+// REC additionally records, per face and bias, which linear piece the limiter took
+// (3 bits) and the pieces of the two curvature limiters it read (3 bits each):
+// tp/tm point at the line's records, face k goes to index f0 + k - 3 if below fend.
+template <bool REC>
+__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double eps16, unsigned short* tp,
+                                           unsigned short* tm, int f0, int fend) {
+  int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
   double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
-  double PM2 = dm4(Pd2 - Pd1, Pk2), PM3 = dm4(Pk2, Pk3);
+  double PM2, PM3, MM3, MM4;
+  if (REC) { PM2 = dm4_sel(Pd2 - Pd1, Pk2, c1); PM3 = dm4_sel(Pk2, Pk3, c2); }
+  else { PM2 = dm4(Pd2 - Pd1, Pk2); PM3 = dm4(Pk2, Pk3); }
   double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
   double Mk3 = Md4 - Md3, Mk4 = Md5 - Md4;
-  double MM3 = dm4(Md3 - Md2, Mk3), MM4 = dm4(Mk3, Mk4);
+  if (REC) { MM3 = dm4_sel(Md3 - Md2, Mk3, c3); MM4 = dm4_sel(Mk3, Mk4, c4); }
+  else { MM3 = dm4(Md3 - Md2, Mk3); MM4 = dm4(Mk3, Mk4); }
   double cp = g[2], cm = h[3];
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
-    // left-biased reconstruction of G^+ centred on cell k-1
-    const double Yp = mp5_rel2<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16);
-    // right-biased reconstruction of G^- centred on cell k (mirror image)
-    const double Ym = mp5_rel2<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16);
+    double Yp, Ym;
+    if (REC) {
+      int yp, ym;
+      // left-biased reconstruction of G^+ centred on cell k-1
+      Yp = mp5_rel2_sel<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16, yp);
+      // right-biased reconstruction of G^- centred on cell k (mirror image)
+      Ym = mp5_rel2_sel<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, ym);
+      const int f = f0 + k - 3;
+      if (f < fend) {
+        tp[f] = (unsigned short)(yp | (c2 << 3) | (c1 << 6));
+        tm[f] = (unsigned short)(ym | (c3 << 3) | (c4 << 6));
+      }
+    } else {
+      Yp = mp5_rel2<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16);
+      Ym = mp5_rel2<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16);
+    }
     const double F = fma(0.5, Yp + Ym, cp + cm);
     if (k > 3) g[k - 4] = Fprev - F;
     Fprev = F;
     if (k < kend) {
       Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
       const double pk = Pd4 - Pd3;
-      PM2 = PM3; PM3 = dm4(Pk3, pk);
+      PM2 = PM3;
+      c1 = c2;
+      if (REC) PM3 = dm4_sel(Pk3, pk, c2);
+      else PM3 = dm4(Pk3, pk);
       Pk3 = pk;
       cp = g[k];
       Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
       const double mk = Md5 - Md4;
-      MM3 = MM4; MM4 = dm4(Mk4, mk);
+      MM3 = MM4;
+      c3 = c4;
+      if (REC) MM4 = dm4_sel(Mk4, mk, c4);
+      else MM4 = dm4(Mk4, mk);
       Mk4 = mk;
       cm = h[k + 1];
     }
@@ -182,7 +209,7 @@ __device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen,
   (void)Mk3;
 }
 
-template <int PHYS, int NV, int D>
+template <int PHYS, int NV, int D, bool REC>
 __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm) {
   const DomDev dm = load_dom(p.doms + it.dom);
   int o[3];
@@ -197,16 +224,27 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
   // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
   const double eps16 = 16.0 * 1e-10;
+  constexpr int od1 = D == 0 ? 1 : 0;
+  constexpr int od2 = D == 2 ? 1 : 2;
+  const int f0 = o[D] + it.s0;
+  const int fend = f0 + slen + ((dm.bc[D][1] == 1 && f0 + slen == dm.n[D]) ? 1 : 0);
+  const long long nlines = (long long)dm.n[od1] * dm.n[od2];
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
     double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
     const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
-    flux_sweep(g, h, slen, eps16);
+    unsigned short *tp = nullptr, *tm = nullptr;
+    if (REC) {
+      const int line = it.l0 + pl;
+      const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+      const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
+      tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
+      tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
+    }
+    flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend);
   }
   __syncthreads();
   // coalesced write-out of L_D for the segment's interior cells
-  constexpr int od1 = D == 0 ? 1 : 0;
-  constexpr int od2 = D == 2 ? 1 : 2;
   double* Ld = p.L[D] + dm.off;
   for (int c = threadIdx.x; c < nl * slen; c += blockDim.x) {
     int pl, j;
@@ -225,7 +263,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   __syncthreads();
 }
 
-template <int PHYS, int NV>
+template <int PHYS, int NV, bool REC>
 __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
   __shared__ int s_it;
@@ -243,9 +281,9 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
   while (it < nitems) {
     const FluxItem item = p.items[p.item0 + it];
     const bool live = p.active[p.doms[item.dom].block0 + item.blk] != 0;
-    if (live && item.d == 0) flux_item<PHYS, NV, 0>(p, item, sm);
-    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0)>(p, item, sm); }
-    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0)>(p, item, sm); }
+    if (live && item.d == 0) flux_item<PHYS, NV, 0, REC>(p, item, sm);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), REC>(p, item, sm); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), REC>(p, item, sm); }
     if (p.counter) {
       if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
       __syncthreads();
@@ -441,21 +479,30 @@ cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, i
 }
 
 cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-#define CALL(PH, NVV) flux_kernel<PH, NVV><<<grid, block, smem, s>>>(p)
+#define CALL(PH, NVV)                                                   \
+  if (p.tape) flux_kernel<PH, NVV, true><<<grid, block, smem, s>>>(p); \
+  else flux_kernel<PH, NVV, false><<<grid, block, smem, s>>>(p)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaGetLastError();
 }
 
 cudaError_t flux_set_smem(int physics, int nv, size_t smem) {
-#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+  AMRFD_DISPATCH(physics, nv, CALL);
+#undef CALL
+  return cudaSuccess;
+}
+
+cudaError_t flux_rec_set_smem(int physics, int nv, size_t smem) {
+#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;
 }
 
 cudaError_t flux_occupancy(int physics, int nv, int block, size_t smem, int* per_sm) {
-#define CALL(PH, NVV) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV>, block, smem)
+#define CALL(PH, NVV) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV, false>, block, smem)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;

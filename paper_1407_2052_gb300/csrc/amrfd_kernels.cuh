@@ -42,6 +42,7 @@ struct FluxParams {
   int P;                        // lines per tile (smem layout)
   int SS;                       // smem stride of one line (>= max segment + 6, odd)
   int glm;
+  unsigned short* tape;         // limiter pieces of every face (recording pass) or nullptr
 };
 
 // One stage combination, optionally with the speeds of the new state.
@@ -109,6 +110,7 @@ struct AdjFluxParams {
   int ndim;
   int P, SSa, SSg;
   int glm;
+  const unsigned short* tape;   // limiter pieces recorded by the forward pass of this stage
 };
 
 // Transposed stage combination.
@@ -137,6 +139,7 @@ cudaError_t launch_psi_fac(const unsigned long long* araw0, const double* dt, do
                            double cr, int glm, cudaStream_t s);
 cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, int block, cudaStream_t s);
 cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s);
+cudaError_t flux_rec_set_smem(int physics, int nv, size_t smem);
 cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, int block, cudaStream_t s);
 cudaError_t launch_dt(const DtParams& p, cudaStream_t s);
 cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
