@@ -74,17 +74,16 @@ struct amrfd_handle {
   size_t flux_smem = 0;
   int flux_grid = 0;
   // work lists (full, grouped per block in work order) and per-block ranges
-  std::vector<int> order;             // global block id per work position
-  std::vector<int> fbeg, fcnt, cbeg, ccnt;
   std::vector<int> dom_fbeg, dom_fend, dom_cbeg, dom_cend;  // per domain, in the full lists
+  int nfgroups = 0;
+  int* d_grp[12] = {};                // group tables: flux (owner, stride, span, beg, cnt, dst), cell (same)
   int nfi = 0, nci = 0;
   // device
   DomDev* d_dom = nullptr;
   unsigned char* d_active = nullptr;
   FluxItem *d_fall = nullptr, *d_fact = nullptr;
   CellItem *d_call = nullptr, *d_cact = nullptr;
-  int *d_order = nullptr, *d_fbeg = nullptr, *d_fcnt = nullptr, *d_cbeg = nullptr, *d_ccnt = nullptr;
-  int *d_fdst = nullptr, *d_cdst = nullptr, *d_counts = nullptr;  // counts[0]=flux, [1]=cell
+  int* d_counts = nullptr;          // counts[0] = flux items, [1] = cell items
   int* d_counters = nullptr;        // one per persistent launch
   double* d_stage[kMaxStages] = {};
   double* d_L[3] = {};
@@ -126,7 +125,11 @@ void free_graphs(amrfd_handle* h) {
 }
 
 // Build full work lists for the current tile. Blocks are ordered largest first
-// (stable, so a domain's blocks stay contiguous); items are grouped per block.
+// (stable, so a domain's blocks stay contiguous). Flux items come in groups, one per
+// (run owner block, direction): when a block edge is shorter than the segment
+// length, runs of consecutive blocks along the direction share long segments (less
+// halo recomputation); a group is live when any block of its run is active. Cell
+// items come in groups of one block.
 int build_items(amrfd_handle* h) {
   std::vector<FluxItem> fi;
   std::vector<CellItem> ci;
@@ -146,22 +149,29 @@ int build_items(amrfd_handle* h) {
   }
   std::iota(ord.begin(), ord.end(), 0);
   std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return bsize[a] > bsize[b]; });
-  h->order = ord;
-  h->fbeg.assign(h->nblocks, 0); h->fcnt.assign(h->nblocks, 0);
-  h->cbeg.assign(h->nblocks, 0); h->ccnt.assign(h->nblocks, 0);
+  std::vector<int> g_owner, g_stride, g_span, g_beg, g_cnt;
+  std::vector<int> c_owner, c_one, c_beg, c_cnt;
   h->dom_fbeg.assign(h->ndom, -1); h->dom_fend.assign(h->ndom, -1);
   h->dom_cbeg.assign(h->ndom, -1); h->dom_cend.assign(h->ndom, -1);
   const int cell_chunk = 4096;
   for (int pos = 0; pos < h->nblocks; pos++) {
     const int g = ord[pos], d = bdom[g], b = bloc[g];
     const DomDev& dm = h->hdom[d];
-    h->fbeg[pos] = (int)fi.size();
+    const int bidx[3] = {b % dm.nb[0], (b / dm.nb[0]) % dm.nb[1], b / (dm.nb[0] * dm.nb[1])};
+    if (h->dom_fbeg[d] < 0) { h->dom_fbeg[d] = (int)fi.size(); h->dom_cbeg[d] = (int)ci.size(); }
     for (int dir = 0; dir < nd; dir++) {
+      const int run = std::max(1, h->seg / dm.be[dir]);
+      if (bidx[dir] % run) continue;  // not the first block of its run
+      const int span = std::min(run, dm.nb[dir] - bidx[dir]);
       const int od1 = dir == 0 ? 1 : 0, od2 = dir == 2 ? 1 : 2;
       const int nlines = dm.be[od1] * dm.be[od2];
-      const int ext = dm.be[dir];
+      const int ext = span * dm.be[dir];
       const int nseg = (ext + h->seg - 1) / h->seg;
       const int slen0 = (ext + nseg - 1) / nseg;  // balanced segments
+      g_owner.push_back(g);
+      g_stride.push_back(dir == 0 ? 1 : (dir == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]));
+      g_span.push_back(span);
+      g_beg.push_back((int)fi.size());
       for (int sg = 0; sg < nseg; sg++) {
         const int s0 = sg * slen0;
         const int sl = std::min(slen0, ext - s0);
@@ -174,51 +184,67 @@ int build_items(amrfd_handle* h) {
           fi.push_back(it);
         }
       }
+      g_cnt.push_back((int)fi.size() - g_beg.back());
     }
-    h->fcnt[pos] = (int)fi.size() - h->fbeg[pos];
-    h->cbeg[pos] = (int)ci.size();
+    c_owner.push_back(g);
+    c_one.push_back(1);
+    c_beg.push_back((int)ci.size());
     const int ncb = (int)bsize[g];
     for (int c0 = 0; c0 < ncb; c0 += cell_chunk) ci.push_back(CellItem{d, b, c0, std::min(cell_chunk, ncb - c0)});
-    h->ccnt[pos] = (int)ci.size() - h->cbeg[pos];
-    if (h->dom_fbeg[d] < 0) { h->dom_fbeg[d] = h->fbeg[pos]; h->dom_cbeg[d] = h->cbeg[pos]; }
+    c_cnt.push_back((int)ci.size() - c_beg.back());
     h->dom_fend[d] = (int)fi.size();
     h->dom_cend[d] = (int)ci.size();
   }
   h->nfi = (int)fi.size();
   h->nci = (int)ci.size();
+  h->nfgroups = (int)g_owner.size();
   // (re)allocate and upload
   cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
+  for (int k = 0; k < 12; k++) cudaFree(h->d_grp[k]);
   CK(cudaMalloc(&h->d_fall, sizeof(FluxItem) * std::max(1, h->nfi)));
   CK(cudaMalloc(&h->d_fact, sizeof(FluxItem) * std::max(1, h->nfi)));
   CK(cudaMalloc(&h->d_call, sizeof(CellItem) * std::max(1, h->nci)));
   CK(cudaMalloc(&h->d_cact, sizeof(CellItem) * std::max(1, h->nci)));
   CK(cudaMemcpy(h->d_fall, fi.data(), sizeof(FluxItem) * h->nfi, cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->d_call, ci.data(), sizeof(CellItem) * h->nci, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->d_order, ord.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->d_fbeg, h->fbeg.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->d_fcnt, h->fcnt.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->d_cbeg, h->cbeg.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->d_ccnt, h->ccnt.data(), sizeof(int) * h->nblocks, cudaMemcpyHostToDevice));
+  const std::vector<int>* src[12] = {&g_owner, &g_stride, &g_span, &g_beg, &g_cnt, &g_cnt,
+                                     &c_owner, &c_one, &c_one, &c_beg, &c_cnt, &c_cnt};
+  for (int k = 0; k < 12; k++) {
+    const size_t n = std::max<size_t>(1, src[k]->size());
+    CK(cudaMalloc(&h->d_grp[k], sizeof(int) * n));
+    CK(cudaMemcpy(h->d_grp[k], src[k]->data(), sizeof(int) * src[k]->size(), cudaMemcpyHostToDevice));
+  }
   return AMRFD_OK;
 }
 
+// Device-side work lists of the live groups (flux items) and active blocks (cell items).
 int compact(amrfd_handle* h, cudaStream_t s) {
   CompactParams p{};
-  p.nsorted = h->nblocks;
-  p.order = h->d_order;
-  p.fbeg = h->d_fbeg; p.fcnt = h->d_fcnt; p.cbeg = h->d_cbeg; p.ccnt = h->d_ccnt;
   p.active = h->d_active;
-  p.fin = h->d_fall; p.fout = h->d_fact; p.nf = h->d_counts;
-  p.cin = h->d_call; p.cout = h->d_cact; p.nc = h->d_counts + 1;
-  p.fdst = h->d_fdst; p.cdst = h->d_cdst;
+  CompactList& f = p.list;
+  f.ngroups = h->nfgroups;
+  f.owner = h->d_grp[0]; f.stride = h->d_grp[1]; f.span = h->d_grp[2]; f.beg = h->d_grp[3]; f.cnt = h->d_grp[4];
+  f.dst = h->d_grp[5];
+  f.count = h->d_counts;
+  f.item_bytes = sizeof(FluxItem);
+  f.in = h->d_fall; f.out = h->d_fact;
+  CK(launch_compact(p, s));
+  CompactList& c = p.list;
+  c.ngroups = h->nblocks;
+  c.owner = h->d_grp[6]; c.stride = h->d_grp[7]; c.span = h->d_grp[8]; c.beg = h->d_grp[9]; c.cnt = h->d_grp[10];
+  c.dst = h->d_grp[11];
+  c.count = h->d_counts + 1;
+  c.item_bytes = sizeof(CellItem);
+  c.in = h->d_call; c.out = h->d_cact;
   CK(launch_compact(p, s));
   return AMRFD_OK;
 }
 
 int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
+  // segments run through blocks, never beyond the domain nor longer than seg
   int maxext = 1;
   for (auto& dm : h->hdom)
-    for (int d = 0; d < h->cfg.ndim; d++) maxext = std::max(maxext, dm.be[d]);
+    for (int d = 0; d < h->cfg.ndim; d++) maxext = std::max(maxext, dm.n[d]);
   const int S = std::min(seg, maxext);
   int SS = S + 2 * kGhost;
   if (SS % 2 == 0) SS++;  // odd stride in doubles: conflict-free 64-bit lines
@@ -279,7 +305,7 @@ FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int 
   p.P = h->lines;
   int S = 1;
   for (auto& dm : h->hdom)
-    for (int d = 0; d < h->cfg.ndim; d++) S = std::max(S, std::min(dm.be[d], h->seg));
+    for (int d = 0; d < h->cfg.ndim; d++) S = std::max(S, std::min(dm.n[d], h->seg));
   // segments are balanced, never longer than seg
   int SS = std::min(S, h->seg) + 2 * kGhost;
   if (SS % 2 == 0) SS++;
@@ -484,13 +510,6 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
   CKH(cudaMemcpy(h->d_dom, h->hdom.data(), sizeof(DomDev) * ndomain, cudaMemcpyHostToDevice));
   CKH(cudaMalloc(&h->d_active, nb));
   CKH(cudaMemcpy(h->d_active, h->active_h.data(), nb, cudaMemcpyHostToDevice));
-  CKH(cudaMalloc(&h->d_order, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_fbeg, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_fcnt, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_cbeg, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_ccnt, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_fdst, sizeof(int) * nb));
-  CKH(cudaMalloc(&h->d_cdst, sizeof(int) * nb));
   CKH(cudaMalloc(&h->d_counts, sizeof(int) * 2));
   CKH(cudaMalloc(&h->d_counters, sizeof(int) * 2 * kMaxStages));
   CKH(cudaMalloc(&h->d_slot, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
@@ -864,8 +883,8 @@ void amrfd_destroy(amrfd_handle* h) {
   free_graphs(h);
   cudaFree(h->d_dom); cudaFree(h->d_active);
   cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
-  cudaFree(h->d_order); cudaFree(h->d_fbeg); cudaFree(h->d_fcnt); cudaFree(h->d_cbeg); cudaFree(h->d_ccnt);
-  cudaFree(h->d_fdst); cudaFree(h->d_cdst); cudaFree(h->d_counts); cudaFree(h->d_counters);
+  for (int k = 0; k < 12; k++) cudaFree(h->d_grp[k]);
+  cudaFree(h->d_counts); cudaFree(h->d_counters);
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_stage[k]);
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_gstage[k]);
   cudaFree(h->d_psifac);

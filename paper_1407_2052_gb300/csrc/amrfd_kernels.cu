@@ -256,6 +256,8 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
     x[od1] = o[od1] + a1;
     x[od2] = o[od2] + a2;
     x[D] = o[D] + it.s0 + j;
+    const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
+    if (!p.active[nbk]) continue;  // a segment through several blocks may cross a passive one
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
 #pragma unroll
     for (int v = 0; v < NV; v++) Ld[(long long)v * dm.ncell + idx] = sm[((0 * NV + v) * p.P + pl) * p.SS + j];
@@ -280,7 +282,19 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
   while (it < nitems) {
     const FluxItem item = p.items[p.item0 + it];
-    const bool live = p.active[p.doms[item.dom].block0 + item.blk] != 0;
+    bool live;
+    {
+      // the item's segment may run through several blocks along its direction
+      const DomDev& dm = p.doms[item.dom];
+      const int d = item.d;
+      const int bidx[3] = {item.blk % dm.nb[0], (item.blk / dm.nb[0]) % dm.nb[1], item.blk / (dm.nb[0] * dm.nb[1])};
+      const int stride = d == 0 ? 1 : (d == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+      const int c0 = bidx[d] * dm.be[d] + item.s0;
+      const int b0 = c0 / dm.be[d], b1 = (c0 + item.slen - 1) / dm.be[d];
+      const int g0 = dm.block0 + item.blk + (b0 - bidx[d]) * stride;
+      live = false;
+      for (int b = b0; b <= b1; b++) live |= p.active[g0 + (b - b0) * stride] != 0;
+    }
     if (live && item.d == 0) flux_item<PHYS, NV, 0, REC>(p, item, sm);
     if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), REC>(p, item, sm); }
     if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), REC>(p, item, sm); }
@@ -413,51 +427,57 @@ __global__ void __launch_bounds__(1024) dt_kernel(DtParams p) {
 }
 
 // ------------------------------------------------------------- compaction
+__device__ __forceinline__ bool group_live(const CompactParams& p, int i) {
+  const int o = p.list.owner[i], st = p.list.stride[i], sp = p.list.span[i];
+  bool live = false;
+  for (int m = 0; m < sp; m++) live |= p.active[o + m * st] != 0;
+  return live;
+}
+
 __global__ void __launch_bounds__(1024) compact_scan_kernel(CompactParams p) {
-  __shared__ int wsum[2][32];
-  __shared__ int carry[2];
-  if (threadIdx.x == 0) { carry[0] = 0; carry[1] = 0; }
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < p.nsorted; base += blockDim.x) {
+  for (int base = 0; base < p.list.ngroups; base += blockDim.x) {
     const int i = base + threadIdx.x;
-    int f = 0, c = 0;
-    if (i < p.nsorted && p.active[p.order[i]]) { f = p.fcnt[i]; c = p.ccnt[i]; }
-    // inclusive warp scans
-    int fs = f, cs = c;
+    const int f = (i < p.list.ngroups && group_live(p, i)) ? p.list.cnt[i] : 0;
+    int fs = f;
     for (int o = 1; o < 32; o <<= 1) {
-      int a = __shfl_up_sync(0xffffffffu, fs, o), b = __shfl_up_sync(0xffffffffu, cs, o);
-      if (lane >= o) { fs += a; cs += b; }
+      const int a = __shfl_up_sync(0xffffffffu, fs, o);
+      if (lane >= o) fs += a;
     }
-    if (lane == 31) { wsum[0][wid] = fs; wsum[1][wid] = cs; }
+    if (lane == 31) wsum[wid] = fs;
     __syncthreads();
     if (wid == 0) {
       const int nw = blockDim.x >> 5;
-      int a = lane < nw ? wsum[0][lane] : 0, b = lane < nw ? wsum[1][lane] : 0;
+      int a = lane < nw ? wsum[lane] : 0;
       for (int o = 1; o < 32; o <<= 1) {
-        int x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, b, o);
-        if (lane >= o) { a += x; b += y; }
+        const int x = __shfl_up_sync(0xffffffffu, a, o);
+        if (lane >= o) a += x;
       }
-      if (lane < nw) { wsum[0][lane] = a; wsum[1][lane] = b; }
+      if (lane < nw) wsum[lane] = a;
     }
     __syncthreads();
-    const int fo = carry[0] + (wid ? wsum[0][wid - 1] : 0) + fs - f;
-    const int co = carry[1] + (wid ? wsum[1][wid - 1] : 0) + cs - c;
-    if (i < p.nsorted) { p.fdst[i] = fo; p.cdst[i] = co; }
+    const int fo = carry + (wid ? wsum[wid - 1] : 0) + fs - f;
+    if (i < p.list.ngroups) p.list.dst[i] = f ? fo : -1;
     __syncthreads();
-    if (threadIdx.x == blockDim.x - 1) { carry[0] = fo + f; carry[1] = co + c; }
+    if (threadIdx.x == blockDim.x - 1) carry = fo + f;
     __syncthreads();
   }
-  if (threadIdx.x == 0) { *p.nf = carry[0]; *p.nc = carry[1]; }
+  if (threadIdx.x == 0) *p.list.count = carry;
 }
 
 __global__ void __launch_bounds__(256) compact_copy_kernel(CompactParams p) {
-  for (int i = blockIdx.x; i < p.nsorted; i += gridDim.x) {
-    if (!p.active[p.order[i]]) continue;
-    const int fb = p.fbeg[i], fc = p.fcnt[i], fd = p.fdst[i];
-    for (int t = threadIdx.x; t < fc; t += blockDim.x) p.fout[fd + t] = p.fin[fb + t];
-    const int cb = p.cbeg[i], cc = p.ccnt[i], cd = p.cdst[i];
-    for (int t = threadIdx.x; t < cc; t += blockDim.x) p.cout[cd + t] = p.cin[cb + t];
+  const int w = p.list.item_bytes / 4;
+  const unsigned* in = (const unsigned*)p.list.in;
+  unsigned* out = (unsigned*)p.list.out;
+  for (int i = blockIdx.x; i < p.list.ngroups; i += gridDim.x) {
+    const int d = p.list.dst[i];
+    if (d < 0) continue;
+    const int b = p.list.beg[i], c = p.list.cnt[i];
+    for (int t = threadIdx.x; t < c * w; t += blockDim.x) out[(size_t)d * w + t] = in[(size_t)b * w + t];
   }
 }
 
@@ -524,7 +544,8 @@ cudaError_t launch_compact(const CompactParams& p, cudaStream_t s) {
   compact_scan_kernel<<<1, 1024, 0, s>>>(p);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  compact_copy_kernel<<<p.nsorted < 4096 ? (p.nsorted > 0 ? p.nsorted : 1) : 4096, 256, 0, s>>>(p);
+  const int n = p.list.ngroups;
+  compact_copy_kernel<<<n < 4096 ? (n > 0 ? n : 1) : 4096, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -78,16 +78,21 @@ struct DtParams {
   int global_min;
 };
 
-// compaction of per-block item ranges to the active blocks (order kept)
+// Compaction of item groups to the active ones, order kept. A group is live when
+// any of the `span` blocks owner, owner+stride, ... is active; its items occupy
+// [beg, beg+cnt) of the full list.
+struct CompactList {
+  int ngroups;
+  const int* owner; const int* stride; const int* span;
+  const int* beg; const int* cnt;
+  int* dst;                    // scratch: destination offset per group
+  int* count;                  // device: number of items kept
+  int item_bytes;
+  const void* in; void* out;
+};
 struct CompactParams {
-  int nsorted;                 // blocks in work order
-  const int* order;            // global block id per work position
-  const int* fbeg; const int* fcnt;
-  const int* cbeg; const int* ccnt;
   const unsigned char* active;
-  const FluxItem* fin; FluxItem* fout; int* nf;
-  const CellItem* cin; CellItem* cout; int* nc;
-  int* fdst; int* cdst;        // scratch: destination offsets per work position
+  CompactList list;
 };
 
 // One transposed flux pass (adjoint of one stage's residual).

@@ -219,9 +219,16 @@ def test_ragged_boxes_smooth(case, batched):
     assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
 
 
-def test_tiles_do_not_change_results():
-    """Every tile shape gives the same bits (faces are computed identically in any segment)."""
-    w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((O.PERIODIC, O.PERIODIC),) * 3, seed=9)
+@pytest.mark.parametrize("multiblock", [False, True])
+def test_tiles_do_not_change_results(multiblock):
+    """Every tile shape gives the same bits (faces are computed identically in any segment,
+    including segments that run through several blocks)."""
+    if multiblock:
+        w = W.blast3d(32, 8)
+        w.active = np.ones(64, np.uint8)
+        w.active[[3, 17, 42]] = 0
+    else:
+        w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((O.PERIODIC, O.PERIODIC),) * 3, seed=9)
     base = None
     for seg, lines, thr in [(32, 32, 288), (16, 8, 96), (64, 16, 160), (8, 1, 32)]:
         s = A().Solver.from_workload(w)
