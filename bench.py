@@ -237,7 +237,9 @@ def run_ours(args, rank, world, local_rank):
         s.step_batched(U, dt)
 
     tile_default = list(s.get_tile())
-    if not args.no_autotune:
+    if args.tile:
+        s.set_tile(*[int(x) for x in args.tile.split(",")])
+    elif not args.no_autotune:
         s.dt(U, out=dt)
         s.autotune(U, dt)
     for _ in range(args.warmup):
@@ -342,7 +344,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": "blast3d: 3D ideal MHD+GLM blast, %d^3 cells in 16^3 blocks, SSPRK3, CFL 0.3" % nside,
                    "cells": ncell, "integrator": "SSPRK3", "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (%.2f GB state)" % (ncell * NV * 8 / 1e9), "tile": list(s.get_tile()),
-                   "tile_default": tile_default, "autotuned": not args.no_autotune},
+                   "tile_default": tile_default, "autotuned": not (args.no_autotune or args.tile)},
         "gpu_launches": launches,
         "kernel_ms": {k: {"total": v[0], "launches": v[1]} for k, v in kt.items()},
         "graph_ms_per_step": graph_ms,
@@ -380,6 +382,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched-block and adjoint comparisons")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default flux-pass tile")
+    ap.add_argument("--tile", default="", help="seg,lines,threads of the flux pass (skips autotuning)")
     ap.add_argument("--n", type=int, default=N_BLAST, help="cells per side of the blast (profiling of small cases)")
     args = ap.parse_args()
     if args.warmup < 3:

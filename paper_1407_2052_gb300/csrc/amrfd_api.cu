@@ -796,9 +796,9 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
         if (compact(h, s)) continue;
         FluxParams fp = flux_params(h, U, U, 0);
         fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters;
-        float tot = 0.f;
+        float tot = 1e30f;
         bool ok = true;
-        for (int rep = 0; rep < 3 && ok; rep++) {
+        for (int rep = 0; rep < 5 && ok; rep++) {
           if (cudaMemsetAsync(h->d_counters, 0, sizeof(int), s) != cudaSuccess) ok = false;
           cudaEventRecord(e0, s);
           if (launch_flux(h->cfg.physics, h->nv, fp, h->flux_grid, h->threads, h->flux_smem, s) != cudaSuccess) ok = false;
@@ -806,7 +806,7 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
           if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
           float ms = 0.f;
           cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0) tot += ms;
+          if (rep > 0) tot = std::min(tot, ms);  // best of four after one warm-up launch
         }
         if (ok && tot < best) { best = tot; best_seg = sg; best_lines = h->lines; best_thr = thr; }
       }

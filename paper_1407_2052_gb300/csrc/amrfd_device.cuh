@@ -396,6 +396,82 @@ __device__ __forceinline__ double char_speed_exact(const Prim& w, double gamma, 
   return __dadd_rn(fabs(w.v[d]), cf);
 }
 
+// --------------------------------------- bounded FP32 estimate of the speeds
+// FP32 conversion of x (truncation, relative error < 2^-23) when |x| lies in
+// [2^-100, 2^100] or x is zero; ok = false otherwise.
+__device__ __forceinline__ float f32_of(double x, bool& ok) {
+  const long long b = dbits(x);
+  const long long ax = b & 0x7fffffffffffffffLL;
+  if (ax == 0) return 0.0f;
+  const int e = (int)(ax >> 52);
+  if (e < 923 || e > 1123) { ok = false; return 0.0f; }
+  const float f = f32_trunc_abs(ax);
+  return b < 0 ? -f : f;
+}
+
+// Bounds lo <= c_d <= up of the exact characteristic speeds of a cell (d < ndim), and
+// of its CFL rate sum_d c_d/dx_d (index 3), from an FP32 evaluation. The relative
+// error of every FP32 quantity is bounded by the input truncation (2^-23 each), the
+// FP32 roundings (2^-24 each) and the cancellation in p = (gamma-1)(E - rho v^2/2 -
+// B^2/2), which scales them by T/S with T = E + rho v^2/2 + B^2/2, S = p/(gamma-1);
+// the discriminant of the fast speed is formed as (a^2 - b_d^2)^2 + b_t^2 (b_t^2 +
+// 2 (a^2 + b_d^2)) (b_t the transverse Alfven speed), a sum of non-negative terms,
+// so the square roots do not amplify it. The bound used, 2^-17 (T/S + 1), holds with
+// a margin of four. force = true when no bound is claimed (non-physical or out of
+// FP32 range): the caller then evaluates the cell exactly.
+template <int PHYS, int NV>
+__device__ __forceinline__ void speed_bounds(const double* u, float gam, int ndim, const float* rdx, bool want_rate,
+                                             float up[4], float lo[4], bool& force) {
+  bool ok = true;
+  const float rho = f32_of(u[0], ok);
+  constexpr int nm = PHYS == PH_EULER ? NV - 2 : 3;
+  float m[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < nm; k++) m[k] = f32_of(u[1 + k], ok);
+  const float E = f32_of(u[PHYS == PH_EULER ? NV - 1 : 4], ok);
+  if (PHYS == PH_MHD) {
+#pragma unroll
+    for (int k = 0; k < 3; k++) B[k] = f32_of(u[5 + k], ok);
+  }
+  if (PHYS == PH_MHD && ((dbits(u[8]) >> 52) & 0x7ff) == 0x7ff) ok = false;  // psi not finite
+  force = !ok || !(rho > 0.0f) || !(E > 0.0f);
+  if (force) return;
+  const float ir = __frcp_rn(rho);
+  const float v[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+  const float ke2 = fmaf(m[2], v[2], fmaf(m[1], v[1], m[0] * v[0]));
+  const float sq[3] = {B[0] * B[0], B[1] * B[1], B[2] * B[2]};
+  const float b2 = sq[0] + sq[1] + sq[2];
+  const float half = 0.5f * (ke2 + b2);
+  const float T = E + half, S = E - half;
+  if (!(S > 1.9073486e-6f * T)) { force = true; return; }  // S <= 2^-19 T: too uncertain
+  const float rel = 7.6293945e-6f * fmaf(T, __frcp_rn(S), 1.0f);  // 2^-17 (T/S + 1)
+  const float a2 = gam * (gam - 1.0f) * S * ir;                   // gamma p / rho
+  float rate_up = 0.0f, rate_lo = 0.0f;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (d >= ndim) { up[d] = 0.0f; lo[d] = 0.0f; continue; }
+    float cf;
+    if (PHYS == PH_EULER) {
+      cf = sqrtf(a2);
+    } else {
+      const float bd2 = sq[d] * ir;
+      const float bt2 = (sq[(d + 1) % 3] + sq[(d + 2) % 3]) * ir;
+      const float x = a2 - bd2;
+      const float disc = fmaf(x, x, bt2 * (bt2 + 2.0f * (a2 + bd2)));
+      cf = sqrtf(0.5f * (a2 + bd2 + bt2 + sqrtf(disc)));
+    }
+    const float c = fabsf(v[d]) + cf;
+    up[d] = c * (1.0f + rel);
+    lo[d] = c * (1.0f - rel);
+    if (want_rate) {
+      rate_up = fmaf(up[d], rdx[d], rate_up);
+      rate_lo = fmaf(lo[d], rdx[d], rate_lo);
+    }
+  }
+  up[3] = rate_up * 1.0000153f;  // (1 + 2^-16): rounding of the rate sums and 1/dx
+  lo[3] = rate_lo * 0.9999847f;
+}
+
 // ------------------------------------------------------ fast flux + LF split
 // G^{+-} = F_d +- alpha_d U = 2 F^{+-}: the factor 1/2 of the splitting is
 // applied once to the final flux difference (MP5 commutes with scaling by 2

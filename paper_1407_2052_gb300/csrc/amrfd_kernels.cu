@@ -51,43 +51,112 @@ __device__ __forceinline__ void block_max4(unsigned long long v[4], unsigned lon
   __syncthreads();
 }
 
+// block-wide max of four non-negative floats, broadcast to every thread
+__device__ __forceinline__ void block_max4f_bcast(float v[4], float (*redf)[32], float* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int q = 0; q < 4; q++) {
+    float x = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    if (lane == 0) redf[q][wid] = x;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      float x = lane < nw ? redf[q][lane] : 0.0f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+      if (lane == 0) out[q] = x;
+    }
+  }
+  __syncthreads();
+}
+
+// Exact speeds of one cell folded into the running maxima (IEEE operations in the
+// order of the definition); returns false for a non-physical state.
+template <int PHYS, int NV>
+__device__ __forceinline__ bool exact_speeds(const double* u, double gamma, int ndim, const double* dx, bool want_rate,
+                                             unsigned long long mx[4]) {
+  Prim w;
+  if (!cons2prim_exact<PHYS, NV>(u, gamma, ndim, w)) return false;
+  double rate = 0.0;
+#pragma unroll
+  for (int d = 0; d < 3; d++) {
+    if (d < ndim) {
+      const double cd = char_speed_exact<PHYS>(w, gamma, d);
+      const unsigned long long b = (unsigned long long)dbits(cd);
+      mx[d] = b > mx[d] ? b : mx[d];
+      if (want_rate) rate = __dadd_rn(rate, __ddiv_rn(cd, dx[d]));
+    }
+  }
+  const unsigned long long br = (unsigned long long)dbits(rate);
+  mx[3] = br > mx[3] ? br : mx[3];
+  return true;
+}
+
 // ------------------------------------------------------------------ speeds
+// Two passes per chunk of K cells per thread: FP32 bounds of every cell's speeds,
+// the chunk's largest lower bound T, then the exact IEEE speeds only of the cells
+// whose upper bound reaches T (or that carry no bound). The chunk maximum, hence
+// every per-domain maximum, is the exact one: a cell left out lies below T, and
+// the cell holding the largest lower bound is at least T.
+constexpr int kSpeedK = 4;
+
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
   __shared__ unsigned long long red[4][32];
+  __shared__ float redf[4][32];
+  __shared__ float thr[4];
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  const float gam = (float)p.gamma;
+  const bool want_rate = p.want_rate != 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
     const DomDev dm = load_dom(p.doms + ci.dom);
     if (!p.active[dm.block0 + ci.blk]) continue;
     int o[3];
     block_coords(dm, ci.blk, o);
+    const float rdx[3] = {(float)(1.0 / dm.dx[0]), (float)(1.0 / dm.dx[1]), (float)(1.0 / dm.dx[2])};
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
-      const int l = ci.c0 + c;
-      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
-      const long long idx = ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-      const double* src = p.U + dm.off + idx;
-      double u[NV];
+    for (int base = 0; base < ci.cnt; base += kSpeedK * blockDim.x) {
+      float up[kSpeedK][4];
+      bool force[kSpeedK];
+      long long idxs[kSpeedK];
+      float lom[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
-      Prim w;
-      if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) {
-        atomicOr(p.err, kErrNonphysical);
-        continue;
-      }
-      double rate = 0.0;
+      for (int k = 0; k < kSpeedK; k++) {
+        const int c = base + k * blockDim.x + threadIdx.x;
+        idxs[k] = -1;
+        force[k] = false;
+        if (c >= ci.cnt) continue;
+        const int l = ci.c0 + c;
+        const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+        idxs[k] = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+        double u[NV];
 #pragma unroll
-      for (int d = 0; d < 3; d++) {
-        if (d < p.ndim) {
-          const double cd = char_speed_exact<PHYS>(w, p.gamma, d);
-          const unsigned long long b = (unsigned long long)dbits(cd);
-          mx[d] = b > mx[d] ? b : mx[d];
-          if (p.want_rate) rate = __dadd_rn(rate, __ddiv_rn(cd, dm.dx[d]));
-        }
+        for (int v = 0; v < NV; v++) u[v] = p.U[idxs[k] + (long long)v * dm.ncell];
+        float lo[4];
+        speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, want_rate, up[k], lo, force[k]);
+        if (!force[k])
+#pragma unroll
+          for (int q = 0; q < 4; q++) lom[q] = fmaxf(lom[q], lo[q]);
       }
-      const unsigned long long br = (unsigned long long)dbits(rate);
-      mx[3] = br > mx[3] ? br : mx[3];
+      block_max4f_bcast(lom, redf, thr);
+#pragma unroll
+      for (int k = 0; k < kSpeedK; k++) {
+        if (idxs[k] < 0) continue;
+        bool cand = force[k];
+#pragma unroll
+        for (int q = 0; q < 4; q++) cand |= (q < 3 || want_rate) && up[k][q] >= thr[q];
+        if (!cand) continue;
+        double u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = p.U[idxs[k] + (long long)v * dm.ncell];
+        if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, want_rate, mx)) atomicOr(p.err, kErrNonphysical);
+      }
+      __syncthreads();  // thr is rewritten by the next chunk
     }
     block_max4(mx, red);
     if (threadIdx.x == 0) {
@@ -313,8 +382,11 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
   __shared__ unsigned long long red[4][32];
+  __shared__ float redf[4][32];
+  __shared__ float thr[4];
   __shared__ double s_fac;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  const float gam = (float)p.gamma;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
     const DomDev dm = load_dom(p.doms + ci.dom);
@@ -336,38 +408,59 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
       __syncthreads();
     }
     const double fac = damp ? s_fac : 1.0;
+    const float rdx[3] = {0.f, 0.f, 0.f};
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
-      const int l = ci.c0 + c;
-      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
-      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-      double u[NV];
+    for (int base = 0; base < ci.cnt; base += kSpeedK * blockDim.x) {
+      float up[kSpeedK][4];
+      bool force[kSpeedK];
+      long long idxs[kSpeedK];
+      float lom[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int v = 0; v < NV; v++) {
-        const long long e = idx + (long long)v * dm.ncell;
-        double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
-        for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
-        acc = fma(w0, p.L[0][e], acc);
-        if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
-        if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
-        if (PHYS == PH_MHD && v == 8) acc *= fac;
-        u[v] = acc;
-        p.out[e] = acc;
-      }
-      if (p.slot_out) {
-        Prim w;
-        if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) {
-          atomicOr(p.err, kErrNonphysical);
-          continue;
-        }
+      for (int k = 0; k < kSpeedK; k++) {
+        const int c = base + k * blockDim.x + threadIdx.x;
+        idxs[k] = -1;
+        force[k] = false;
+        if (c >= ci.cnt) continue;
+        const int l = ci.c0 + c;
+        const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+        const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+        idxs[k] = idx;
+        double u[NV];
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          if (d < p.ndim) {
-            const unsigned long long b = (unsigned long long)dbits(char_speed_exact<PHYS>(w, p.gamma, d));
-            mx[d] = b > mx[d] ? b : mx[d];
-          }
+        for (int v = 0; v < NV; v++) {
+          const long long e = idx + (long long)v * dm.ncell;
+          double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
+          for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
+          acc = fma(w0, p.L[0][e], acc);
+          if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
+          if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
+          if (PHYS == PH_MHD && v == 8) acc *= fac;
+          u[v] = acc;
+          p.out[e] = acc;
+        }
+        if (p.slot_out) {
+          float lo[4];
+          speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up[k], lo, force[k]);
+          if (!force[k])
+#pragma unroll
+            for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
         }
       }
+      if (!p.slot_out) continue;
+      block_max4f_bcast(lom, redf, thr);
+#pragma unroll
+      for (int k = 0; k < kSpeedK; k++) {
+        if (idxs[k] < 0) continue;
+        bool cand = force[k];
+#pragma unroll
+        for (int q = 0; q < 3; q++) cand |= up[k][q] >= thr[q];
+        if (!cand) continue;
+        double u[NV];
+#pragma unroll
+        for (int v = 0; v < NV; v++) u[v] = p.out[idxs[k] + (long long)v * dm.ncell];
+        if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, false, mx)) atomicOr(p.err, kErrNonphysical);
+      }
+      __syncthreads();
     }
     if (p.slot_out) {
       block_max4(mx, red);
