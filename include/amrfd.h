@@ -43,6 +43,7 @@ extern "C" {
 #define AMRFD_MHD_GLM 1
 #define AMRFD_SSPRK3 0
 #define AMRFD_SSPRK54 1
+#define AMRFD_SSPRK43 2
 #define AMRFD_BC_PERIODIC 0
 #define AMRFD_BC_OUTFLOW 1
 #define AMRFD_DT_PER_DOMAIN 0
@@ -58,7 +59,7 @@ extern "C" {
 typedef struct amrfd_config {
   int physics;    /* AMRFD_EULER | AMRFD_MHD_GLM */
   int ndim;       /* 1, 2 or 3 */
-  int integrator; /* AMRFD_SSPRK3 (Gottlieb-Shu RK3, Sec. 2.3) | AMRFD_SSPRK54 (printed table, Sec. 2.3) */
+  int integrator; /* AMRFD_SSPRK3 (Gottlieb-Shu RK3, Sec. 2.3) | AMRFD_SSPRK54 | AMRFD_SSPRK43 (printed tables, Sec. 2.3) */
   int dt_scope;   /* AMRFD_DT_PER_DOMAIN | AMRFD_DT_GLOBAL (min over domains) */
   double gamma;   /* ratio of specific heats, > 1 */
   double cfl;     /* Courant number used by amrfd_dt */

@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 EULER, MHD_GLM = 0, 1
-SSPRK3, SSPRK54 = 0, 1
+SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW = 0, 1
 FLAG_NONPHYSICAL = 1
 
@@ -177,7 +177,7 @@ def step(c, d, U, dt, active=None):
     """One SSPRK step; returns (U_new, flags, alpha_per_stage[s,3], c_h)."""
     U = _check(c, d, U).copy()
     a = _active(d, active)
-    s = 3 if c.integrator == SSPRK3 else 5
+    s = {SSPRK3: 3, SSPRK54: 5, SSPRK43: 4}[c.integrator]
     al = np.zeros((s, 3))
     ch = np.zeros(1)
     fl = lib().orc_step(ctypes.byref(c), ctypes.byref(d), _dp(U), float(dt), _u8(a), _dp(al), _dp(ch))

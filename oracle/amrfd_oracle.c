@@ -15,7 +15,7 @@
  *   interface flux = R_L(F^+) + R_R(F^-) ......................... Sec. 2.2
  *   MP5 reconstruction R ...... Suresh & Huynh (1997), cited in Sec. 2.2
  *   s-stage SSPRK in Shu-Osher form .............................. Sec. 2.3
- *   SSPRK(5,4) coefficient table (printed, used verbatim) ........ Sec. 2.3
+ *   SSPRK(5,4), SSPRK(4,3) coefficient tables (printed, verbatim) . Sec. 2.3
  *   RK3 of Gottlieb & Shu (1998), cited in Sec. 2.3 (Shu-Osher SSPRK3)
  *   ideal-gas total energy E = p/(gamma-1) + rho v^2/2 + B^2/2 ... Sec. 3, 4.3
  *   ideal MHD fluxes (B_0 = 0, eta = eta_h = 0) .................. Sec. 4.1, 4.3
@@ -157,6 +157,14 @@ int orc_ssprk_table(int integrator, double a[5][5], double b[5][5]) {
     a[1][0] = 0.75; a[1][1] = 0.25;   b[1][1] = 0.25;
     a[2][0] = 1.0 / 3.0; a[2][2] = 2.0 / 3.0; b[2][2] = 2.0 / 3.0;
     return 3;
+  }
+  if (integrator == ORC_SSPRK43) {
+    /* SSPRK(4,3), the table printed in Sec. 2.3 */
+    a[0][0] = 1.0;                    b[0][0] = 0.5;
+    a[1][1] = 1.0;                    b[1][1] = 0.5;
+    a[2][0] = 2.0 / 3.0; a[2][2] = 1.0 / 3.0; b[2][2] = 1.0 / 6.0;
+    a[3][3] = 1.0;                    b[3][3] = 0.5;
+    return 4;
   }
   /* SSPRK(5,4), the table printed in Sec. 2.3, digits as printed */
   a[0][0] = 1.0;

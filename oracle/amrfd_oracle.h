@@ -22,6 +22,7 @@
 #define ORC_MHD_GLM 1
 #define ORC_SSPRK3 0
 #define ORC_SSPRK54 1
+#define ORC_SSPRK43 2
 #define ORC_BC_PERIODIC 0
 #define ORC_BC_OUTFLOW 1
 
@@ -31,7 +32,7 @@
 typedef struct orc_cfg {
   int physics;    /* ORC_EULER | ORC_MHD_GLM */
   int ndim;       /* 1..3 */
-  int integrator; /* ORC_SSPRK3 | ORC_SSPRK54 */
+  int integrator; /* ORC_SSPRK3 | ORC_SSPRK54 | ORC_SSPRK43 */
   int pad_;
   double gamma;
   double glm_cr;  /* psi damping length c_r = c_p^2/c_h; <= 0 disables damping */

@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libamrfd.so")
 
 EULER, MHD_GLM = 0, 1
-SSPRK3, SSPRK54 = 0, 1
+SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW = 0, 1
 DT_PER_DOMAIN, DT_GLOBAL = 0, 1
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
@@ -140,7 +140,7 @@ class Solver:
         self.domains = list(domains)
         self.ndom = len(self.domains)
         self.nv = 2 + ndim if physics == EULER else 9
-        self.nstages = 3 if integrator == SSPRK3 else 5
+        self.nstages = {SSPRK3: 3, SSPRK54: 5, SSPRK43: 4}[integrator]
         self.nblocks = sum(int(d.nb[0]) * int(d.nb[1]) * int(d.nb[2]) for d in self.domains)
         self.nelem = max(int(d.offset) + self.nv * int(d.n[0]) * int(d.n[1]) * int(d.n[2]) for d in self.domains)
         doms = domains_c(self.domains)

@@ -43,6 +43,14 @@ int stage_table(int integrator, StageCoef co[kMaxStages]) {
     set(2, {{0, 1.0 / 3.0}, {2, 2.0 / 3.0}}, 2.0 / 3.0);
     return 3;
   }
+  if (integrator == AMRFD_SSPRK43) {
+    // SSPRK(4,3) of Sec. 2.3 (SSP up to CFL 2)
+    set(0, {{0, 1.0}}, 0.5);
+    set(1, {{1, 1.0}}, 0.5);
+    set(2, {{0, 2.0 / 3.0}, {2, 1.0 / 3.0}}, 1.0 / 6.0);
+    set(3, {{3, 1.0}}, 0.5);
+    return 4;
+  }
   const double a10 = 0.44437049406734, a11 = 0.55562950593266;
   const double a20 = 0.62010185138540, a22 = 0.37989814861460;
   const double a30 = 0.17807995410773, a33 = 0.82192004589227;
@@ -88,6 +96,7 @@ struct amrfd_handle {
   double* d_stage[kMaxStages] = {};
   double* d_L[3] = {};
   unsigned long long* d_slot = nullptr;  // [kNumSlots][ndom][4]
+  unsigned* d_tlow = nullptr;            // [kNumSlots][ndom][4] FP32 lower bounds of the speeds
   unsigned* d_err = nullptr;
   size_t nelem = 0;                 // elements of one state-shaped buffer
   cudaStream_t cap = nullptr;       // private stream for graph capture
@@ -271,6 +280,7 @@ int default_threads(int nv, int lines) {
 }
 
 unsigned long long* slot(amrfd_handle* h, int k) { return h->d_slot + (size_t)k * h->ndom * 4; }
+unsigned* tlow(amrfd_handle* h, int k) { return h->d_tlow + (size_t)k * h->ndom * 4; }
 
 enum { K_SPEEDS = 0, K_FLUX = 1, K_COMBINE = 2, K_DT = 3 };
 
@@ -325,6 +335,7 @@ CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
   p.dt = dt;
   p.co = h->co[i - 1];
   p.slot_out = (i < h->ns) ? slot(h, i) : nullptr;
+  p.tlow_out = (i < h->ns) ? tlow(h, i) : nullptr;
   p.araw0 = slot(h, 0);
   p.err = h->d_err;
   p.gamma = h->cfg.gamma;
@@ -340,6 +351,7 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   p.active = h->d_active;
   p.U = U;
   p.slot = slot(h, k);
+  p.tlow = tlow(h, k);
   p.err = h->d_err;
   p.gamma = h->cfg.gamma;
   p.ndim = h->cfg.ndim;
@@ -347,31 +359,61 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   return p;
 }
 
+// Domains with at least one active block (host copy of the flags).
+std::vector<int> live_domains(amrfd_handle* h) {
+  std::vector<int> live;
+  for (int d = 0; d < h->ndom; d++) {
+    bool any = false;
+    for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++)
+      any |= h->active_h[h->hdom[d].block0 + b] != 0;
+    if (any && h->dom_cbeg[d] >= 0) live.push_back(d);
+  }
+  return live;
+}
+
+// One launch of the speeds kernel over the active cells: the compacted list
+// (batched) or one launch per live domain.
+int launch_speeds_over(amrfd_handle* h, SpeedParams p, bool batched, const std::vector<int>& live, cudaStream_t s) {
+  if (batched) {
+    p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
+    Tick tk(h, K_SPEEDS, s);
+    CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+    return AMRFD_OK;
+  }
+  for (int d : live) {
+    p.items = h->d_call; p.item0 = h->dom_cbeg[d]; p.nitems = h->dom_cend[d] - h->dom_cbeg[d];
+    Tick tk(h, K_SPEEDS, s);
+    CK(launch_speeds(h->cfg.physics, h->nv, p, p.nitems, 256, s));
+  }
+  return AMRFD_OK;
+}
+
+// Exact per-domain speed maxima of U into slot k: bounds pass, then exact candidates.
+int speeds_from_scratch(amrfd_handle* h, const double* U, int k, int want_rate, bool batched,
+                        const std::vector<int>& live, cudaStream_t s) {
+  CK(cudaMemsetAsync(slot(h, k), 0, sizeof(unsigned long long) * h->ndom * 4, s));
+  CK(cudaMemsetAsync(tlow(h, k), 0, sizeof(unsigned) * h->ndom * 4, s));
+  SpeedParams p = speed_params(h, U, k, want_rate);
+  p.exact = 0;
+  int rc = launch_speeds_over(h, p, batched, live, s);
+  if (rc) return rc;
+  p.exact = 1;
+  return launch_speeds_over(h, p, batched, live, s);
+}
+
 // Enqueue one full step. batched: persistent launches over the compacted lists;
 // else one launch per domain (per pass) over that domain's items.
 int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, bool batched) {
   const int ph = h->cfg.physics, nv = h->nv;
   CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
+  CK(cudaMemsetAsync(h->d_tlow, 0, sizeof(unsigned) * h->ns * h->ndom * 4, s));
   if (batched) CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
   const int cgrid = 8 * h->nsm;
+  const std::vector<int> live = batched ? std::vector<int>() : live_domains(h);
   // speeds of U^n
   {
-    SpeedParams p = speed_params(h, U, 0, 0);
-    if (batched) {
-      p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
-      Tick tk(h, K_SPEEDS, s);
-      CK(launch_speeds(ph, nv, p, cgrid, 256, s));
-    } else {
-      for (int d = 0; d < h->ndom; d++) {
-        if (h->dom_cbeg[d] < 0) continue;
-        bool any = false;
-        for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++) any |= h->active_h[h->hdom[d].block0 + b] != 0;
-        if (!any) continue;
-        p.items = h->d_call; p.item0 = h->dom_cbeg[d]; p.nitems = h->dom_cend[d] - h->dom_cbeg[d];
-        Tick tk(h, K_SPEEDS, s);
-        CK(launch_speeds(ph, nv, p, p.nitems, 256, s));
-      }
-    }
+    int rc = speeds_from_scratch(h, U, 0, 0, batched, live, s);
+    if (rc) return rc;
   }
   for (int i = 1; i <= h->ns; i++) {
     const double* Uk = (i == 1) ? U : h->d_stage[i - 1];
@@ -389,14 +431,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
         CK(launch_combine(ph, nv, cp, cgrid, 256, s));
       }
     } else {
-      std::vector<int> live;
-      for (int d = 0; d < h->ndom; d++) {
-        bool any = false;
-        for (int b = 0; b < h->hdom[d].nb[0] * h->hdom[d].nb[1] * h->hdom[d].nb[2]; b++) any |= h->active_h[h->hdom[d].block0 + b] != 0;
-        if (any && h->dom_fbeg[d] >= 0) live.push_back(d);
-      }
-      // flux pass: items of passive blocks inside a live domain are skipped by
-      // compacting per domain on the host (same item order as the device list)
+      // flux pass: items of passive blocks inside a live domain are skipped in the kernel
       for (int d : live) {
         fp.items = h->d_fall; fp.item0 = h->dom_fbeg[d]; fp.nitems = h->dom_fend[d] - h->dom_fbeg[d];
         fp.counter = nullptr;
@@ -409,6 +444,13 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
         CK(launch_combine(ph, nv, cp, cp.nitems, 256, s));
       }
     }
+    if (i < h->ns) {
+      // exact speed maxima of U^(i); the combination published their lower bounds
+      SpeedParams sp = speed_params(h, h->d_stage[i], i, 0);
+      sp.exact = 1;
+      int rc = launch_speeds_over(h, sp, batched, live, s);
+      if (rc) return rc;
+    }
   }
   return AMRFD_OK;
 }
@@ -417,7 +459,8 @@ int validate(const amrfd_config* c, const amrfd_domain* d, int n) {
   if (!c || !d || n <= 0) return AMRFD_ERR_INVALID_ARG;
   if (c->physics != AMRFD_EULER && c->physics != AMRFD_MHD_GLM) return AMRFD_ERR_INVALID_ARG;
   if (c->ndim < 1 || c->ndim > 3) return AMRFD_ERR_INVALID_ARG;
-  if (c->integrator != AMRFD_SSPRK3 && c->integrator != AMRFD_SSPRK54) return AMRFD_ERR_INVALID_ARG;
+  if (c->integrator != AMRFD_SSPRK3 && c->integrator != AMRFD_SSPRK54 && c->integrator != AMRFD_SSPRK43)
+    return AMRFD_ERR_INVALID_ARG;
   if (c->dt_scope != AMRFD_DT_PER_DOMAIN && c->dt_scope != AMRFD_DT_GLOBAL) return AMRFD_ERR_INVALID_ARG;
   if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return AMRFD_ERR_INVALID_ARG;
   for (int i = 0; i < n; i++) {
@@ -513,6 +556,8 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
   CKH(cudaMalloc(&h->d_counts, sizeof(int) * 2));
   CKH(cudaMalloc(&h->d_counters, sizeof(int) * 2 * kMaxStages));
   CKH(cudaMalloc(&h->d_slot, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
+  CKH(cudaMalloc(&h->d_tlow, sizeof(unsigned) * kNumSlots * ndomain * 4));
+  CKH(cudaMemset(h->d_tlow, 0, sizeof(unsigned) * kNumSlots * ndomain * 4));
   CKH(cudaMemset(h->d_slot, 0, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
   CKH(cudaMalloc(&h->d_err, sizeof(unsigned)));
   CKH(cudaMemset(h->d_err, 0, sizeof(unsigned)));
@@ -545,14 +590,8 @@ int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double 
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   unsigned long long* sl = slot(h, kSlotDt);
-  CK(cudaMemsetAsync(sl, 0, sizeof(unsigned long long) * h->ndom * 4, s));
-  SpeedParams p = speed_params(h, U, kSlotDt, 1);
-  p.items = h->d_cact;
-  p.nitems_dev = h->d_counts + 1;
-  {
-    Tick tk(h, K_SPEEDS, s);
-    CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
-  }
+  int rc = speeds_from_scratch(h, U, kSlotDt, 1, true, std::vector<int>(), s);
+  if (rc) return rc;
   DtParams q{};
   q.doms = h->d_dom;
   q.slot = sl;
@@ -668,11 +707,11 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
   double* Un = const_cast<double*>(U_n);
   // forward recompute of U^(1..s-1) and of the splitting speeds of every stage input
   CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
+  CK(cudaMemsetAsync(h->d_tlow, 0, sizeof(unsigned) * h->ns * h->ndom * 4, s));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
   {
-    SpeedParams p = speed_params(h, U_n, 0, 0);
-    p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
-    CK(launch_speeds(ph, nv, p, cgrid, 256, s));
+    int rc = speeds_from_scratch(h, U_n, 0, 0, true, std::vector<int>(), s);
+    if (rc) return rc;
   }
   for (int i = 1; i <= h->ns; i++) {
     // every stage's flux pass records the limiter's pieces; states up to U^(s-1)
@@ -688,6 +727,10 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     CombParams cp = comb_params(h, Un, dt_dev, i);
     cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
     CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+    SpeedParams sp = speed_params(h, h->d_stage[i], i, 0);
+    sp.exact = 1;
+    int rc = launch_speeds_over(h, sp, true, std::vector<int>(), s);
+    if (rc) return rc;
   }
   CK(launch_psi_fac(slot(h, 0), dt_dev, h->d_psifac, h->ndom, h->cfg.ndim, h->cfg.glm_cr,
                     h->cfg.physics == AMRFD_MHD_GLM, s));
@@ -773,11 +816,9 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
   (void)dt_dev;
   cudaStream_t s = (cudaStream_t)stream;
   // sample state speeds (slot 0) so that the flux pass sees realistic c_max
-  CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ndom * 4, s));
   {
-    SpeedParams p = speed_params(h, U, 0, 0);
-    p.items = h->d_cact; p.nitems_dev = h->d_counts + 1;
-    CK(launch_speeds(h->cfg.physics, h->nv, p, 8 * h->nsm, 256, s));
+    int rc = speeds_from_scratch(h, U, 0, 0, true, std::vector<int>(), s);
+    if (rc) return rc;
   }
   const int segs[] = {16, 32, 64};
   const int lines_c[] = {8, 16, 32};
@@ -891,7 +932,7 @@ void amrfd_destroy(amrfd_handle* h) {
   cudaFree(h->d_tape);
   cudaFree(h->d_adj_items);
   for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
-  cudaFree(h->d_slot); cudaFree(h->d_err);
+  cudaFree(h->d_slot); cudaFree(h->d_tlow); cudaFree(h->d_err);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (auto e : h->tev) cudaEventDestroy(e);
   delete h;

@@ -97,11 +97,12 @@ __device__ __forceinline__ bool exact_speeds(const double* u, double gamma, int 
 }
 
 // ------------------------------------------------------------------ speeds
-// Two passes per chunk of K cells per thread: FP32 bounds of every cell's speeds,
-// the chunk's largest lower bound T, then the exact IEEE speeds only of the cells
-// whose upper bound reaches T (or that carry no bound). The chunk maximum, hence
-// every per-domain maximum, is the exact one: a cell left out lies below T, and
-// the cell holding the largest lower bound is at least T.
+// Exact per-domain maxima in two launches. The bounds launch (exact = 0) evaluates
+// FP32 bounds of every active cell's speeds and publishes, per domain, the largest
+// lower bound T (an integer max of the FP32 bits). The exact launch (exact = 1)
+// re-evaluates the bounds and computes the exact IEEE speeds only of the cells whose
+// upper bound reaches T, or that carry no bound. The maxima are exact: a cell left
+// out lies below T, and T is below the speed of the cell that set it.
 constexpr int kSpeedK = 4;
 
 template <int PHYS, int NV>
@@ -119,44 +120,42 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
     int o[3];
     block_coords(dm, ci.blk, o);
     const float rdx[3] = {(float)(1.0 / dm.dx[0]), (float)(1.0 / dm.dx[1]), (float)(1.0 / dm.dx[2])};
+    unsigned* tl = p.tlow + (size_t)ci.dom * 4;
+    float T[4] = {0.f, 0.f, 0.f, 0.f};
+    if (p.exact)
+#pragma unroll
+      for (int q = 0; q < 4; q++) T[q] = __uint_as_float(tl[q]);
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int base = 0; base < ci.cnt; base += kSpeedK * blockDim.x) {
-      float up[kSpeedK][4];
-      bool force[kSpeedK];
-      long long idxs[kSpeedK];
-      float lom[4] = {0.f, 0.f, 0.f, 0.f};
+    float lom[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      double u[NV];
 #pragma unroll
-      for (int k = 0; k < kSpeedK; k++) {
-        const int c = base + k * blockDim.x + threadIdx.x;
-        idxs[k] = -1;
-        force[k] = false;
-        if (c >= ci.cnt) continue;
-        const int l = ci.c0 + c;
-        const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
-        idxs[k] = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-        double u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = p.U[idxs[k] + (long long)v * dm.ncell];
-        float lo[4];
-        speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, want_rate, up[k], lo, force[k]);
-        if (!force[k])
+      for (int v = 0; v < NV; v++) u[v] = p.U[idx + (long long)v * dm.ncell];
+      float up[4], lo[4];
+      bool force;
+      speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, want_rate, up, lo, force);
+      if (!p.exact) {
+        if (!force)
 #pragma unroll
           for (int q = 0; q < 4; q++) lom[q] = fmaxf(lom[q], lo[q]);
+        continue;
       }
+      bool cand = force;
+#pragma unroll
+      for (int q = 0; q < 4; q++) cand |= (q < 3 || want_rate) && up[q] >= T[q];
+      if (!cand) continue;
+      if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, want_rate, mx)) atomicOr(p.err, kErrNonphysical);
+    }
+    if (!p.exact) {
       block_max4f_bcast(lom, redf, thr);
+      if (threadIdx.x == 0)
 #pragma unroll
-      for (int k = 0; k < kSpeedK; k++) {
-        if (idxs[k] < 0) continue;
-        bool cand = force[k];
-#pragma unroll
-        for (int q = 0; q < 4; q++) cand |= (q < 3 || want_rate) && up[k][q] >= thr[q];
-        if (!cand) continue;
-        double u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = p.U[idxs[k] + (long long)v * dm.ncell];
-        if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, want_rate, mx)) atomicOr(p.err, kErrNonphysical);
-      }
-      __syncthreads();  // thr is rewritten by the next chunk
+        for (int q = 0; q < 4; q++)
+          if (thr[q] > 0.f) atomicMax(tl + q, __float_as_uint(thr[q]));
+      continue;
     }
     block_max4(mx, red);
     if (threadIdx.x == 0) {
@@ -381,7 +380,6 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
 // ----------------------------------------------------------------- combine
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
-  __shared__ unsigned long long red[4][32];
   __shared__ float redf[4][32];
   __shared__ float thr[4];
   __shared__ double s_fac;
@@ -409,66 +407,39 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
     }
     const double fac = damp ? s_fac : 1.0;
     const float rdx[3] = {0.f, 0.f, 0.f};
-    unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
-    for (int base = 0; base < ci.cnt; base += kSpeedK * blockDim.x) {
-      float up[kSpeedK][4];
-      bool force[kSpeedK];
-      long long idxs[kSpeedK];
-      float lom[4] = {0.f, 0.f, 0.f, 0.f};
+    float lom[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      double u[NV];
 #pragma unroll
-      for (int k = 0; k < kSpeedK; k++) {
-        const int c = base + k * blockDim.x + threadIdx.x;
-        idxs[k] = -1;
-        force[k] = false;
-        if (c >= ci.cnt) continue;
-        const int l = ci.c0 + c;
-        const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
-        const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-        idxs[k] = idx;
-        double u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) {
-          const long long e = idx + (long long)v * dm.ncell;
-          double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
-          for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
-          acc = fma(w0, p.L[0][e], acc);
-          if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
-          if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
-          if (PHYS == PH_MHD && v == 8) acc *= fac;
-          u[v] = acc;
-          p.out[e] = acc;
-        }
-        if (p.slot_out) {
-          float lo[4];
-          speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up[k], lo, force[k]);
-          if (!force[k])
-#pragma unroll
-            for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
-        }
+      for (int v = 0; v < NV; v++) {
+        const long long e = idx + (long long)v * dm.ncell;
+        double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
+        for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
+        acc = fma(w0, p.L[0][e], acc);
+        if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
+        if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
+        if (PHYS == PH_MHD && v == 8) acc *= fac;
+        u[v] = acc;
+        p.out[e] = acc;
       }
-      if (!p.slot_out) continue;
-      block_max4f_bcast(lom, redf, thr);
+      if (p.tlow_out) {
+        float up[4], lo[4];
+        bool force;
+        speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
+        if (!force)
 #pragma unroll
-      for (int k = 0; k < kSpeedK; k++) {
-        if (idxs[k] < 0) continue;
-        bool cand = force[k];
-#pragma unroll
-        for (int q = 0; q < 3; q++) cand |= up[k][q] >= thr[q];
-        if (!cand) continue;
-        double u[NV];
-#pragma unroll
-        for (int v = 0; v < NV; v++) u[v] = p.out[idxs[k] + (long long)v * dm.ncell];
-        if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, false, mx)) atomicOr(p.err, kErrNonphysical);
+          for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
       }
-      __syncthreads();
     }
-    if (p.slot_out) {
-      block_max4(mx, red);
-      if (threadIdx.x == 0) {
+    if (p.tlow_out) {
+      block_max4f_bcast(lom, redf, thr);
+      if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 3; q++)
-          if (mx[q]) atomicMax(p.slot_out + (size_t)ci.dom * 4 + q, mx[q]);
-      }
+          if (thr[q] > 0.f) atomicMax(p.tlow_out + (size_t)ci.dom * 4 + q, __float_as_uint(thr[q]));
     } else if (damp) {
       __syncthreads();  // s_fac is rewritten by the next item
     }

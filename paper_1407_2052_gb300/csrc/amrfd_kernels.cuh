@@ -17,10 +17,12 @@ struct SpeedParams {
   int item0;
   const double* U;
   unsigned long long* slot;
+  unsigned* tlow;               // per domain x 4: largest lower bound (FP32 bits)
   unsigned* err;
   double gamma;
   int ndim;
   int want_rate;
+  int exact;                    // 0: publish lower bounds only; 1: exact maxima of the candidates
 };
 
 // One flux pass: L_d(U^(k)) for the items' lines.
@@ -59,6 +61,7 @@ struct CombParams {
   const double* dt;
   StageCoef co;
   unsigned long long* slot_out; // speeds of the output state (nullptr: none)
+  unsigned* tlow_out;           // lower bounds of those speeds (FP32 bits), per domain x 4
   const unsigned long long* araw0;
   unsigned* err;
   double gamma;

@@ -19,7 +19,7 @@ import numpy as np
 
 SEED0 = 14072052
 EULER, MHD_GLM = 0, 1
-SSPRK3, SSPRK54 = 0, 1
+SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW = 0, 1
 
 

@@ -93,6 +93,7 @@ CASES = [
     ("euler1d_outflow", lambda: _smooth(O.EULER, 1, (40, 1, 1), ((1, 1), (0, 0), (0, 0)), 1, O.SSPRK3), 2e-3),
     ("euler2d_mixed", lambda: _smooth(O.EULER, 2, (24, 20, 1), ((1, 1), (0, 0), (0, 0)), 2, O.SSPRK54), 2e-3),
     ("mhd3d_mixed", lambda: _smooth(O.MHD_GLM, 3, (12, 10, 8), ((0, 0), (1, 1), (0, 0)), 3, O.SSPRK3), 1e-3),
+    ("euler3d_ssprk43", lambda: _smooth(O.EULER, 3, (10, 8, 12), ((0, 0), (0, 0), (1, 1)), 4, O.SSPRK43), 2e-3),
 ]
 
 

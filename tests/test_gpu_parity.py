@@ -139,13 +139,33 @@ def test_sod_to_final_time_shocked():
     assert rel_l1(host(U, Uo.shape), Uo) <= 1e-10
 
 
-@pytest.mark.parametrize("integrator", [O.SSPRK54, O.SSPRK3])
+@pytest.mark.parametrize("integrator", [O.SSPRK54, O.SSPRK3, O.SSPRK43])
 def test_vortex_smooth_one_step(integrator):
     w = W.vortex2d(64, integrator=integrator)
     s, U, dts = run_gpu(w, 1)
     ref, odts = run_oracle(w, 1)
     assert float(dts[0][0].item()) == odts[0]
     assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("cfl", [0.4, 1.5])
+def test_brio_wu_shock_tube(cfl):
+    """1D MHD Brio-Wu tube (Sec. 4.5.2), SSPRK(5,4)-MP5 at CFL 0.4 and at the SSP limit 1.5,
+    to t = 0.2: same number of steps and relative L1 <= 1e-10 against the oracle."""
+    w = W.brio_wu(512)
+    c, d = ocfg(w), odom(w.domains[0])
+    Uo, t, n, fl = O.evolve(c, d, w.U, cfl, w.t_end)
+    assert fl == 0
+    s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, cfl, w.domains, glm_cr=w.glm_cr)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        s.step_batched(U, dt)
+        tg += float(dt[0].item())
+        ng += 1
+    assert s.error() == A().OK and ng == n
+    assert rel_l1(host(U, Uo.shape), Uo, 1.0) <= 1e-10
 
 
 def test_vortex_smooth_100_steps():

@@ -265,13 +265,20 @@ def test_ssprk_tables_order_and_ssp_coefficient():
     assert s == 5
     coef = _stability_poly(a, b)
     np.testing.assert_allclose(coef[:5], [1, 1, 1 / 2, 1 / 6, 1 / 24], rtol=0, atol=1e-10)
+    gold = dict((r[0], r[1]) for r in _golden("ssprk54_ssp.txt"))
+    s, a4, b4 = O.ssprk_table(O.SSPRK43)
+    assert s == 4
+    # SSPRK(4,3): third order, R(z) = 1 + z + z^2/2 + z^3/6 + z^4/48, SSP coefficient 2 (printed)
+    np.testing.assert_allclose(_stability_poly(a4, b4), [1, 1, 1 / 2, 1 / 6, 1 / 48], rtol=0, atol=1e-15)
+    r4 = [a4[i, k] / b4[i, k] for i in range(4) for k in range(4) if b4[i, k] != 0]
+    assert min(r4) == float(gold["ssp_cfl_43"])
     ratios = [a[i, k] / b[i, k] for i in range(5) for k in range(5) if b[i, k] != 0]
-    want = float(dict((r[0], r[1]) for r in _golden("ssprk54_ssp.txt"))["ssp_cfl_54"])
+    want = float(gold["ssp_cfl_54"])
     # the printed table is rounded to 14 digits, which moves the ratio by ~5e-11
     assert min(ratios) == pytest.approx(want, rel=1e-10)
 
 
-@pytest.mark.parametrize("integrator,order", [(O.SSPRK3, 3), (O.SSPRK54, 4)])
+@pytest.mark.parametrize("integrator,order", [(O.SSPRK3, 3), (O.SSPRK54, 4), (O.SSPRK43, 3)])
 def test_step_temporal_order(integrator, order):
     """orc_step itself (stage storage and combination) converges in dt at the scheme's order."""
     w = W.sine_advection(24)

@@ -140,6 +140,9 @@ def residual(U, dx, bc, physics, ndim, gamma, alpha, ch):
 def ssprk_table(integrator):
     if integrator == 0:
         return [[1.0], [0.75, 0.25], [1.0 / 3.0, 0.0, 2.0 / 3.0]], [[1.0], [0.0, 0.25], [0.0, 0.0, 2.0 / 3.0]]
+    if integrator == 2:
+        return ([[1.0], [0.0, 1.0], [2.0 / 3.0, 0.0, 1.0 / 3.0], [0.0, 0.0, 0.0, 1.0]],
+                [[0.5], [0.0, 0.5], [0.0, 0.0, 1.0 / 6.0], [0.0, 0.0, 0.0, 0.5]])
     a = [[1.0],
          [0.44437049406734, 0.55562950593266],
          [0.62010185138540, 0.0, 0.37989814861460],
