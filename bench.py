@@ -88,6 +88,17 @@ def clocks_summary(path, gpu_index):
     return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate(ms_local, cells_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of N independent replicas: the slowest rank's time over
+    the units all ranks processed. Returns (ms_max, cell-updates/s)."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if dist is not None and world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, cells_per_rank * steps * world / (ms_max * 1e-3)
+
+
 def cpu_baseline(cells_side=128, block=16):
     """The oracle as it stands: one SSPRK3 step of an n^3 blast on one host core."""
     import oracle as O
@@ -274,11 +285,7 @@ def run_ours(args, rank, world, local_rank):
         fh.close()
     clocks = clocks_summary(clk_path, gpu_index)
     assert s.error() == A.OK
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = ncell * args.steps * world / (ms_max * 1e-3)
+    ms_max, value = aggregate(ms, ncell, args.steps, world, dist, "cuda")
     launches = sum(v[1] for v in kt.values())
 
     # ---- the same K steps replayed from the captured CUDA graph
@@ -310,10 +317,7 @@ def run_ours(args, rank, world, local_rank):
     e1.record(stream)
     barrier()
     e2e_ms = e0.elapsed_time(e1)
-    t = torch.tensor([e2e_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = ncell * args.steps * world / (float(t.item()) * 1e-3)
+    _, e2e_value = aggregate(e2e_ms, ncell, args.steps, world, dist, "cuda")
 
     flux_ms, flux_n = kt["flux"]
     flux_avg_s = flux_ms / max(flux_n, 1) * 1e-3

@@ -278,7 +278,7 @@ __device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen,
 }
 
 template <int PHYS, int NV, int D, bool REC>
-__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm) {
+__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
   const DomDev dm = load_dom(p.doms + it.dom);
   int o[3];
   block_coords(dm, it.blk, o);
@@ -324,8 +324,10 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
     x[od1] = o[od1] + a1;
     x[od2] = o[od2] + a2;
     x[D] = o[D] + it.s0 + j;
-    const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
-    if (!p.active[nbk]) continue;  // a segment through several blocks may cross a passive one
+    if (!all_live) {  // a segment through several blocks may cross a passive one
+      const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
+      if (!p.active[nbk]) continue;
+    }
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
 #pragma unroll
     for (int v = 0; v < NV; v++) Ld[(long long)v * dm.ncell + idx] = sm[((0 * NV + v) * p.P + pl) * p.SS + j];
@@ -334,7 +336,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
 }
 
 template <int PHYS, int NV, bool REC>
-__global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
+__global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
   __shared__ int s_it;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
@@ -350,7 +352,7 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
   while (it < nitems) {
     const FluxItem item = p.items[p.item0 + it];
-    bool live;
+    bool live, all_live;
     {
       // the item's segment may run through several blocks along its direction
       const DomDev& dm = p.doms[item.dom];
@@ -361,11 +363,16 @@ __global__ void __launch_bounds__(384) flux_kernel(FluxParams p) {
       const int b0 = c0 / dm.be[d], b1 = (c0 + item.slen - 1) / dm.be[d];
       const int g0 = dm.block0 + item.blk + (b0 - bidx[d]) * stride;
       live = false;
-      for (int b = b0; b <= b1; b++) live |= p.active[g0 + (b - b0) * stride] != 0;
+      all_live = true;
+      for (int b = b0; b <= b1; b++) {
+        const bool a = p.active[g0 + (b - b0) * stride] != 0;
+        live |= a;
+        all_live &= a;
+      }
     }
-    if (live && item.d == 0) flux_item<PHYS, NV, 0, REC>(p, item, sm);
-    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), REC>(p, item, sm); }
-    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), REC>(p, item, sm); }
+    if (live && item.d == 0) flux_item<PHYS, NV, 0, REC>(p, item, sm, all_live);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), REC>(p, item, sm, all_live); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), REC>(p, item, sm, all_live); }
     if (p.counter) {
       if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
       __syncthreads();

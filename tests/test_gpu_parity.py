@@ -379,3 +379,48 @@ def test_blast_full_size_properties():
     b = U2.view(9, 256, 256, 256)
     assert torch.equal(torch.roll(a, shift, dims=(1, 2, 3)), b)
     assert s.error() == A().OK
+
+
+# ----------------------------------------------- GPU-only runs at full length
+def _run_to(w, t_end, cfl):
+    s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, cfl, w.domains, glm_cr=w.glm_cr)
+    U = dev(w.U.copy().ravel())
+    t, n = 0.0, 0
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    while t < t_end * (1 - 1e-14):
+        s.dt(U, t, t_end, out=dt)
+        s.step_batched(U, dt)
+        t += float(dt.item())
+        n += 1
+    assert s.error() == A().OK
+    return host(U, w.U.shape), n
+
+
+def test_alfven_wave_convergence_on_gpu():
+    """Circularly polarised Alfven wave (Sec. 4.5.1) on the diagonal of the periodic box,
+    one period, SSPRK(5,4)-MP5 with GLM: the L1 error of the state falls at about fifth
+    order from 64^2 to 512^2 (the paper observes 5 in 3D)."""
+    errs = []
+    for n in (64, 128, 256, 512):
+        w = W.alfven2d(n)
+        U, _ = _run_to(w, w.t_end, 0.2)
+        errs.append(np.mean(np.abs(U[:8] - w.U[:8])))
+    orders = [np.log2(errs[i] / errs[i + 1]) for i in range(len(errs) - 1)]
+    assert min(orders[:2]) > 4.3, (errs, orders)
+
+
+def test_vortex_1024_500_steps_stays_physical_and_conservative():
+    """The 2D MHD+GLM vortex at 1024^2 with SSPRK(5,4), CFL 0.4, 500 steps: no non-physical
+    state and totals of rho, m, E, B conserved to rounding."""
+    w = W.vortex2d(1024)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.copy().ravel())
+    V = U.view(9, -1)
+    tot0 = V[:8].sum(dim=1)
+    scale = V[:8].abs().sum(dim=1).max()
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(500):
+        s.dt(U, out=dt)
+        s.step_batched(U, dt)
+    assert s.error() == A().OK
+    assert torch.all((V[:8].sum(dim=1) - tot0).abs() <= 1e-11 * scale)
