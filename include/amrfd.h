@@ -46,6 +46,7 @@ extern "C" {
 #define AMRFD_SSPRK43 2
 #define AMRFD_BC_PERIODIC 0
 #define AMRFD_BC_OUTFLOW 1
+#define AMRFD_BC_SYMMETRIC 2 /* mirror ghosts, per-variable sign: see amrfd_domain.asym */
 #define AMRFD_DT_PER_DOMAIN 0
 #define AMRFD_DT_GLOBAL 1
 
@@ -71,6 +72,13 @@ typedef struct amrfd_domain {
   int nb[3];       /* blocks per dimension (n[d] % nb[d] == 0); a block is the unit of activity */
   double dx[3];    /* cell size per dimension (> 0) */
   int bc[3][2];    /* AMRFD_BC_* of the low and high face of each dimension; periodic must pair */
+  uint32_t asym[3][2]; /* AMRFD_BC_SYMMETRIC faces: bit v set = conserved variable v is odd
+                          (antisymmetric) across the face, clear = even (symmetric). Ghost
+                          layer m = 1..3 outside the face holds interior cell m-1 inside it,
+                          odd variables negated (the per-variable symmetric/antisymmetric
+                          ghost kinds of Sec. 4.5.10); a reflecting wall sets the normal
+                          momentum (MHD: and the tangential field and psi) odd. Ignored on
+                          other faces; bits >= nv are invalid. */
   int64_t offset;  /* element offset of U[0][0][0][0] of this domain in the state buffer */
 } amrfd_domain;
 
@@ -81,7 +89,8 @@ typedef struct amrfd_handle amrfd_handle;
    means all active (App. C: only active blocks are advanced). Allocates the
    workspace (stage states, per-direction residuals, speeds, work lists) with
    cudaMalloc on the current device. Constraints: n[d] >= 3 along periodic
-   dimensions, n[d] >= 1 otherwise; domains must not overlap. Returns
+   dimensions and at mirror (AMRFD_BC_SYMMETRIC) faces, n[d] >= 1 otherwise;
+   domains must not overlap. Returns
    AMRFD_ERR_INVALID_ARG on bad arguments, AMRFD_ERR_CUDA on allocation failure. */
 int amrfd_create(amrfd_handle **h, const amrfd_config *cfg, const amrfd_domain *domains, int ndomain,
                  const uint8_t *active_host, void *stream);
@@ -90,6 +99,30 @@ int amrfd_create(amrfd_handle **h, const amrfd_config *cfg, const amrfd_domain *
    and rebuild the device work lists of active blocks. Synchronises `stream`
    once to keep a host copy for the per-domain path. */
 int amrfd_set_active(amrfd_handle *h, const uint8_t *active_dev, void *stream);
+
+/* Dynamic grid activation, App. C step 1 with a built-in criterion: writes
+   flag_dev[b] = 1 (candidate for de-activation) for every block b whose cells
+   all lie within tol (absolute, every conserved variable) of U_ref, e.g. the
+   initial or an analytic stationary state, else 0 (a NaN counts as a
+   deviation). U, U_ref: device, state layout; flag_dev: device, one byte per
+   block (caller-owned). Asynchronous; every block is tested, active or not. */
+int amrfd_flag_steady(amrfd_handle *h, const double *U, const double *U_ref, double tol, uint8_t *flag_dev,
+                      void *stream);
+
+/* Dynamic grid activation, App. C steps 2 and 3: blocks with flag_dev[b] = 0
+   become active, candidates (flag 1) passive; then `belt` times (>= 0) every
+   passive block with an active neighbour (sharing a face, edge or corner in its
+   domain; neighbours wrap across periodic faces) is re-activated, each round
+   testing against the previous round's flags; the device work lists are then
+   rebuilt on the device. Asynchronous on `stream`, no host synchronisation; the
+   next amrfd_step or amrfd_adjoint synchronises once to refresh the host copy
+   of the flags (amrfd_step_batched and amrfd_dt need none). Returns
+   AMRFD_ERR_INVALID_ARG for belt < 0. */
+int amrfd_activate(amrfd_handle *h, const uint8_t *flag_dev, int belt, void *stream);
+
+/* Copy the current per-block active flags to active_dev (device, one byte per
+   block). Asynchronous. */
+int amrfd_get_active(amrfd_handle *h, uint8_t *active_dev, void *stream);
 
 /* CFL time step per domain (Sec. 4.4, unsplit multi-D form):
    dt = cfl / max over active cells of sum_d c_d/dx_d, where c_d = |v_d| + fast
@@ -116,7 +149,9 @@ int amrfd_step_batched(amrfd_handle *h, double *U, const double *dt_dev, void *s
    gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
    Splitting speeds c_max, c_h and the psi damping factor are held fixed at
    the values the forward step used; MP5 limiter branches are replayed from
-   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED where not built. */
+   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED for a domain that
+   is partly active, a periodic dimension of fewer than 6 cells, or a mirror
+   dimension whose blocks hold fewer than 3 cells along it. */
 int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,
                   double *gU_n, void *stream);
 

@@ -19,7 +19,7 @@ from . import build as _build
 
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
 FLAG_NONPHYSICAL = 1
 
 
@@ -30,7 +30,7 @@ class Cfg(ctypes.Structure):
 
 class Dom(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("nb", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
-                ("bc", (ctypes.c_int * 2) * 3)]
+                ("bc", (ctypes.c_int * 2) * 3), ("asym", (ctypes.c_uint * 2) * 3)]
 
 
 _lib = None
@@ -63,6 +63,10 @@ def lib():
         L.orc_step.argtypes = [cp, mp, dp, ctypes.c_double, u8p, dp, dp]
         L.orc_dt.argtypes = [cp, mp, dp, u8p, ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         L.orc_step_frozen.argtypes = [cp, mp, dp, ctypes.c_double, u8p, dp, ctypes.c_double]
+        L.orc_flag_steady.argtypes = [cp, mp, dp, dp, ctypes.c_double, u8p]
+        L.orc_flag_steady.restype = None
+        L.orc_activate.argtypes = [mp, u8p, ctypes.c_int, u8p]
+        L.orc_activate.restype = None
         _lib = L
     return _lib
 
@@ -81,9 +85,10 @@ def cfg(physics, ndim, integrator=SSPRK3, gamma=1.4, glm_cr=0.18):
     return Cfg(physics, ndim, integrator, 0, gamma, glm_cr)
 
 
-def dom(n, dx, bc=PERIODIC, nb=(1, 1, 1)):
+def dom(n, dx, bc=PERIODIC, nb=(1, 1, 1), asym=None):
     """n, dx: per-dimension sequences (padded with 1 / 1.0); bc: one kind for all
-    faces, or a 3x2 nested sequence."""
+    faces, or a 3x2 nested sequence; asym: 3x2 bit masks of the variables that are
+    odd across a SYMMETRIC face (None = all even)."""
     n = list(n) + [1] * (3 - len(n))
     dx = list(dx) + [1.0] * (3 - len(dx))
     if isinstance(bc, int):
@@ -92,6 +97,8 @@ def dom(n, dx, bc=PERIODIC, nb=(1, 1, 1)):
     for k in range(3):
         d.n[k], d.nb[k], d.dx[k] = n[k], nb[k], dx[k]
         d.bc[k][0], d.bc[k][1] = bc[k][0], bc[k][1]
+        if asym is not None:
+            d.asym[k][0], d.asym[k][1] = int(asym[k][0]), int(asym[k][1])
     return d
 
 
@@ -105,6 +112,8 @@ def _check(c, d, U):
     for k in range(c.ndim):
         if d.bc[k][0] == PERIODIC and d.n[k] < 3:
             raise ValueError("periodic direction needs at least 3 cells")
+        if SYMMETRIC in (d.bc[k][0], d.bc[k][1]) and d.n[k] < 3:
+            raise ValueError("a mirror face needs at least 3 cells")
     return U
 
 
@@ -215,3 +224,20 @@ def evolve(c, d, U, cfl, t_end, max_steps=100000, fixed_dt=None):
         t += h
         n += 1
     return U, t, n, flags
+
+
+def flag_steady(c, d, U, Uref, tol):
+    """App. C step 1 criterion: 1 per block whose cells all lie within tol of Uref."""
+    U = _check(c, d, U)
+    R = _check(c, d, Uref)
+    f = np.zeros(d.nb[0] * d.nb[1] * d.nb[2], np.uint8)
+    lib().orc_flag_steady(ctypes.byref(c), ctypes.byref(d), _dp(U), _dp(R), float(tol), _u8(f))
+    return f
+
+
+def activate(d, flag, belt):
+    """App. C steps 2-3: active flags from the candidates `flag` and `belt` safety layers."""
+    f = _active(d, flag)
+    a = np.zeros_like(f)
+    lib().orc_activate(ctypes.byref(d), _u8(f), int(belt), _u8(a))
+    return a

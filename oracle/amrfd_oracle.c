@@ -252,21 +252,29 @@ int orc_residual(const orc_cfg *c, const orc_dom *dm, const double *U, const dou
             E[(long)v * NE + ((long)(z + o[2]) * ne[1] + (y + o[1])) * ne[0] + (x + o[0])] =
                 U[(long)v * N + ((long)z * dm->n[1] + y) * dm->n[0] + x];
   }
-  /* ghost cells, one direction at a time: periodic wrap or zero-gradient copy */
+  /* ghost cells, one direction at a time: periodic wrap, zero-gradient copy, or
+     mirror image (ghost -1-m copies interior cell m, odd variables negated) */
   for (d = 0; d < nd; d++) {
     int x[3], g, n = dm->n[d];
     for (x[2] = 0; x[2] < ne[2]; x[2]++)
       for (x[1] = 0; x[1] < ne[1]; x[1]++)
         for (x[0] = 0; x[0] < ne[0]; x[0]++) {
-          int src[3] = {x[0], x[1], x[2]}, phys;
+          int src[3] = {x[0], x[1], x[2]}, phys, face, kind;
+          unsigned odd = 0;
           g = x[d] - NG; /* physical index along d */
           if (g >= 0 && g < n) continue;
-          if (g < 0) phys = dm->bc[d][0] == ORC_BC_PERIODIC ? g + n : 0;
-          else phys = dm->bc[d][1] == ORC_BC_PERIODIC ? g - n : n - 1;
+          face = g < 0 ? 0 : 1;
+          kind = dm->bc[d][face];
+          if (kind == ORC_BC_PERIODIC) phys = g < 0 ? g + n : g - n;
+          else if (kind == ORC_BC_SYMMETRIC) {
+            phys = g < 0 ? -1 - g : 2 * n - 1 - g;
+            odd = dm->asym[d][face];
+          } else phys = g < 0 ? 0 : n - 1;
           src[d] = phys + NG;
-          for (v = 0; v < nv; v++)
-            E[(long)v * NE + ((long)x[2] * ne[1] + x[1]) * ne[0] + x[0]] =
-                E[(long)v * NE + ((long)src[2] * ne[1] + src[1]) * ne[0] + src[0]];
+          for (v = 0; v < nv; v++) {
+            const double val = E[(long)v * NE + ((long)src[2] * ne[1] + src[1]) * ne[0] + src[0]];
+            E[(long)v * NE + ((long)x[2] * ne[1] + x[1]) * ne[0] + x[0]] = ((odd >> v) & 1u) ? -val : val;
+          }
         }
   }
 
@@ -412,4 +420,54 @@ int orc_dt(const orc_cfg *c, const orc_dom *dm, const double *U, const uint8_t *
   dt = rate > 0.0 ? cfl / rate : INFINITY;
   *dt_out = fmin(dt, t_end - t);
   return flags;
+}
+
+/* ------------------------------------------------------------------ App. C */
+
+void orc_flag_steady(const orc_cfg *c, const orc_dom *dm, const double *U, const double *Uref, double tol,
+                     uint8_t *flag) {
+  const int nv = orc_nvar(c);
+  const long N = ncells(dm);
+  int be[3], k, v, x, y, z;
+  for (k = 0; k < 3; k++) be[k] = dm->n[k] / dm->nb[k];
+  for (k = 0; k < dm->nb[0] * dm->nb[1] * dm->nb[2]; k++) flag[k] = 1;
+  for (z = 0; z < dm->n[2]; z++)
+    for (y = 0; y < dm->n[1]; y++)
+      for (x = 0; x < dm->n[0]; x++) {
+        const long i = ((long)z * dm->n[1] + y) * dm->n[0] + x;
+        const int b = ((z / be[2]) * dm->nb[1] + y / be[1]) * dm->nb[0] + x / be[0];
+        for (v = 0; v < nv; v++)
+          if (!(fabs(U[(long)v * N + i] - Uref[(long)v * N + i]) <= tol)) flag[b] = 0;
+      }
+}
+
+void orc_activate(const orc_dom *dm, const uint8_t *flag, int belt, uint8_t *active) {
+  const int nbl = dm->nb[0] * dm->nb[1] * dm->nb[2];
+  uint8_t *prev = (uint8_t *)malloc((size_t)nbl);
+  int b, r, k;
+  for (b = 0; b < nbl; b++) active[b] = flag[b] ? 0 : 1;
+  for (r = 0; r < belt; r++) {
+    memcpy(prev, active, (size_t)nbl);
+    for (b = 0; b < nbl; b++) {
+      int i[3], o[3];
+      if (prev[b]) continue;
+      i[0] = b % dm->nb[0];
+      i[1] = (b / dm->nb[0]) % dm->nb[1];
+      i[2] = b / (dm->nb[0] * dm->nb[1]);
+      for (o[2] = -1; o[2] <= 1; o[2]++)
+        for (o[1] = -1; o[1] <= 1; o[1]++)
+          for (o[0] = -1; o[0] <= 1; o[0]++) {
+            int j[3], ok = 1;
+            for (k = 0; k < 3; k++) {
+              j[k] = i[k] + o[k];
+              if (j[k] < 0 || j[k] >= dm->nb[k]) {
+                if (dm->bc[k][0] == ORC_BC_PERIODIC) j[k] = (j[k] + dm->nb[k]) % dm->nb[k];
+                else ok = 0;
+              }
+            }
+            if (ok && prev[(j[2] * dm->nb[1] + j[1]) * dm->nb[0] + j[0]]) active[b] = 1;
+          }
+    }
+  }
+  free(prev);
 }

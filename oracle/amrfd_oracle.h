@@ -25,6 +25,7 @@
 #define ORC_SSPRK43 2
 #define ORC_BC_PERIODIC 0
 #define ORC_BC_OUTFLOW 1
+#define ORC_BC_SYMMETRIC 2 /* mirror ghosts; variables flagged in asym[d][f] change sign */
 
 /* flags reported by orc_step / orc_speeds */
 #define ORC_FLAG_NONPHYSICAL 1
@@ -43,6 +44,7 @@ typedef struct orc_dom {
   int nb[3];      /* blocks per dimension (block edge = n[d]/nb[d]) */
   double dx[3];
   int bc[3][2];   /* ORC_BC_* for the low and high face of each dimension */
+  unsigned asym[3][2]; /* ORC_BC_SYMMETRIC: bit v set = variable v is odd across the face */
 } orc_dom;
 
 int orc_nvar(const orc_cfg *c);
@@ -83,5 +85,17 @@ int orc_step_frozen(const orc_cfg *c, const orc_dom *dm, double *U, double dt, c
 /* CFL time step of one domain; returns flags. */
 int orc_dt(const orc_cfg *c, const orc_dom *dm, const double *U, const uint8_t *block_active,
            double cfl, double t, double t_end, double *dt_out);
+
+/* Dynamic grid activation (App. C). Step 1, a criterion: flag[b] = 1 when every
+   cell and variable of block b lies within tol (absolute) of the reference state
+   Uref (the block is a candidate for de-activation), else 0. */
+void orc_flag_steady(const orc_cfg *c, const orc_dom *dm, const double *U, const double *Uref, double tol,
+                     uint8_t *flag);
+
+/* Steps 2 and 3: blocks not flagged are active; then, `belt` times, every
+   candidate block with an active neighbour (face, edge or corner; across periodic
+   faces) becomes active, all candidates tested against the previous round's
+   flags. Writes the final active flags. */
+void orc_activate(const orc_dom *dm, const uint8_t *flag, int belt, uint8_t *active);
 
 #endif

@@ -15,14 +15,14 @@ LIB_PATH = os.path.join(HERE, "libamrfd.so")
 
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
 DT_PER_DOMAIN, DT_GLOBAL = 0, 1
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
 
 EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
            "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
-           "amrfd_dt_noalloc")
+           "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active")
 
 
 class Config(ctypes.Structure):
@@ -33,7 +33,7 @@ class Config(ctypes.Structure):
 
 class DomainC(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("nb", ctypes.c_int * 3), ("dx", ctypes.c_double * 3),
-                ("bc", (ctypes.c_int * 2) * 3), ("offset", ctypes.c_int64)]
+                ("bc", (ctypes.c_int * 2) * 3), ("asym", (ctypes.c_uint32 * 2) * 3), ("offset", ctypes.c_int64)]
 
 
 class AmrfdError(RuntimeError):
@@ -56,6 +56,9 @@ def load():
     vp, dp, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
     L.amrfd_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), ctypes.POINTER(DomainC), i, vp, vp]
     L.amrfd_set_active.argtypes = [vp, vp, vp]
+    L.amrfd_flag_steady.argtypes = [vp, vp, vp, dp, vp, vp]
+    L.amrfd_activate.argtypes = [vp, vp, i, vp]
+    L.amrfd_get_active.argtypes = [vp, vp, vp]
     L.amrfd_dt.argtypes = [vp, vp, vp, dp, dp, vp]
     L.amrfd_step.argtypes = [vp, vp, vp, vp]
     L.amrfd_step_batched.argtypes = [vp, vp, vp, vp]
@@ -114,6 +117,10 @@ def domains_c(domains):
             arr[i].dx[k] = float(d.dx[k])
             arr[i].bc[k][0] = int(d.bc[k][0])
             arr[i].bc[k][1] = int(d.bc[k][1])
+            asym = getattr(d, "asym", None)
+            if asym is not None:
+                arr[i].asym[k][0] = int(asym[k][0])
+                arr[i].asym[k][1] = int(asym[k][1])
         arr[i].offset = int(d.offset)
     return arr
 
@@ -178,6 +185,32 @@ class Solver:
             raise TypeError("expected a CUDA uint8 tensor with one flag per block")
         _check(load().amrfd_set_active(self._h, ctypes.c_void_p(active_dev.data_ptr()), _stream(stream)),
                "amrfd_set_active")
+
+    def _flags(self, t):
+        import torch
+        if t.dtype != torch.uint8 or not t.is_cuda or t.numel() != self.nblocks or not t.is_contiguous():
+            raise TypeError("expected a contiguous CUDA uint8 tensor with one flag per block")
+        return ctypes.c_void_p(t.data_ptr())
+
+    def flag_steady(self, U, U_ref, tol, out=None, stream=None):
+        """amrfd_flag_steady: 1 per block whose cells all lie within tol of U_ref."""
+        import torch
+        if out is None:
+            out = torch.empty(self.nblocks, dtype=torch.uint8, device=U.device)
+        _check(load().amrfd_flag_steady(self._h, _ptr(U), _ptr(U_ref), float(tol), self._flags(out),
+                                        _stream(stream)), "amrfd_flag_steady")
+        return out
+
+    def activate(self, flag, belt=1, stream=None):
+        """amrfd_activate: passive candidates `flag`, `belt` safety layers, device work lists rebuilt."""
+        _check(load().amrfd_activate(self._h, self._flags(flag), int(belt), _stream(stream)), "amrfd_activate")
+
+    def active(self, stream=None):
+        """Current per-block active flags (CUDA uint8 tensor)."""
+        import torch
+        out = torch.empty(self.nblocks, dtype=torch.uint8, device="cuda")
+        _check(load().amrfd_get_active(self._h, self._flags(out), _stream(stream)), "amrfd_get_active")
+        return out
 
     def dt(self, U, t=0.0, t_end=float("inf"), out=None, stream=None):
         import torch

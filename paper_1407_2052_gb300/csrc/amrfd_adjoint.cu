@@ -220,8 +220,8 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
   __syncthreads();
   // ---- phase B: one thread per (line, variable) walks the faces within reach
   int kb = s0 - 2, ke = s0 + slen + 2;
-  if (dm.bc[D][0] == 1 && kb < 0) kb = 0;
-  if (dm.bc[D][1] == 1 && ke > n) ke = n;
+  if (dm.bc[D][0] != 0 && kb < 0) kb = 0;
+  if (dm.bc[D][1] != 0 && ke > n) ke = n;
   const long long nlines = (long long)dm.n[od1] * dm.n[od2];
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
@@ -276,6 +276,26 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
       gmv[v] = gGm[(v * P + pl) * SA + j + 5];
     }
     split_flux_adj<PHYS, NV, D>(u, p.gm1, alpha, ch2, gpv, gmv, gu);
+    // mirror faces: the ghost image of this cell (odd variables negated) fed the
+    // split fluxes too; its gradient goes through the Jacobian at the image state
+    // and back through the sign flip (the segment at a mirror face holds >= 3 cells)
+    for (int side = 0; side < 2; side++) {
+      int q = -1;
+      if (side == 0 && dm.bc[D][0] == 2 && s0 == 0 && j < 3) q = 4 - j;
+      if (side == 1 && dm.bc[D][1] == 2 && s0 + slen == n && j >= slen - 3) q = 2 * slen + 4 - j;
+      if (q < 0) continue;
+      const unsigned odd = dm.asym[D][side];
+      double ui[NV], gi[NV];
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        ui[v] = ((odd >> v) & 1u) ? -u[v] : u[v];
+        gpv[v] = gGp[(v * P + pl) * SA + q];
+        gmv[v] = gGm[(v * P + pl) * SA + q];
+      }
+      split_flux_adj<PHYS, NV, D>(ui, p.gm1, alpha, ch2, gpv, gmv, gi);
+#pragma unroll
+      for (int v = 0; v < NV; v++) gu[v] += ((odd >> v) & 1u) ? -gi[v] : gi[v];
+    }
 #pragma unroll
     for (int v = 0; v < NV; v++) p.gL[D][dm.off + idx + (long long)v * dm.ncell] = gu[v];
   }

@@ -89,6 +89,9 @@ struct amrfd_handle {
   // device
   DomDev* d_dom = nullptr;
   unsigned char* d_active = nullptr;
+  int* d_bdom = nullptr;                // domain of every block
+  unsigned char* d_act_tmp[2] = {};     // safety-belt rounds (App. C)
+  bool active_h_stale = false;          // device flags changed by amrfd_activate
   FluxItem *d_fall = nullptr, *d_fact = nullptr;
   CellItem *d_call = nullptr, *d_cact = nullptr;
   int* d_counts = nullptr;          // counts[0] = flux items, [1] = cell items
@@ -359,6 +362,16 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   return p;
 }
 
+// Bring the host copy of the active flags up to date after amrfd_activate
+// (synchronises the stream once).
+int refresh_active_host(amrfd_handle* h, cudaStream_t s) {
+  if (!h->active_h_stale) return AMRFD_OK;
+  CK(cudaMemcpyAsync(h->active_h.data(), h->d_active, h->nblocks, cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  h->active_h_stale = false;
+  return AMRFD_OK;
+}
+
 // Domains with at least one active block (host copy of the flags).
 std::vector<int> live_domains(amrfd_handle* h) {
   std::vector<int> live;
@@ -463,14 +476,18 @@ int validate(const amrfd_config* c, const amrfd_domain* d, int n) {
     return AMRFD_ERR_INVALID_ARG;
   if (c->dt_scope != AMRFD_DT_PER_DOMAIN && c->dt_scope != AMRFD_DT_GLOBAL) return AMRFD_ERR_INVALID_ARG;
   if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return AMRFD_ERR_INVALID_ARG;
+  const int nv = c->physics == AMRFD_EULER ? 2 + c->ndim : 9;
   for (int i = 0; i < n; i++) {
     for (int k = 0; k < 3; k++) {
       if (d[i].n[k] < 1 || d[i].nb[k] < 1 || d[i].n[k] % d[i].nb[k]) return AMRFD_ERR_INVALID_ARG;
       if (k >= c->ndim && (d[i].n[k] != 1 || d[i].nb[k] != 1)) return AMRFD_ERR_INVALID_ARG;
       if (k < c->ndim) {
         if (!(d[i].dx[k] > 0.0)) return AMRFD_ERR_INVALID_ARG;
-        for (int f = 0; f < 2; f++)
-          if (d[i].bc[k][f] != AMRFD_BC_PERIODIC && d[i].bc[k][f] != AMRFD_BC_OUTFLOW) return AMRFD_ERR_INVALID_ARG;
+        for (int f = 0; f < 2; f++) {
+          const int b = d[i].bc[k][f];
+          if (b != AMRFD_BC_PERIODIC && b != AMRFD_BC_OUTFLOW && b != AMRFD_BC_SYMMETRIC) return AMRFD_ERR_INVALID_ARG;
+          if (b == AMRFD_BC_SYMMETRIC && (d[i].n[k] < 3 || (d[i].asym[k][f] >> nv))) return AMRFD_ERR_INVALID_ARG;
+        }
         if ((d[i].bc[k][0] == AMRFD_BC_PERIODIC) != (d[i].bc[k][1] == AMRFD_BC_PERIODIC)) return AMRFD_ERR_INVALID_ARG;
         if (d[i].bc[k][0] == AMRFD_BC_PERIODIC && d[i].n[k] < 3) return AMRFD_ERR_INVALID_ARG;
         if (d[i].n[k] / d[i].nb[k] > 32767) return AMRFD_ERR_INVALID_ARG;
@@ -480,7 +497,6 @@ int validate(const amrfd_config* c, const amrfd_domain* d, int n) {
     if ((long long)d[i].n[0] * d[i].n[1] * d[i].n[2] > 0x7fffffffLL) return AMRFD_ERR_INVALID_ARG;
   }
   // overlap check: sort by offset
-  const int nv = c->physics == AMRFD_EULER ? 2 + c->ndim : 9;
   std::vector<std::pair<int64_t, int64_t>> r;
   for (int i = 0; i < n; i++) r.push_back({d[i].offset, d[i].offset + (int64_t)nv * d[i].n[0] * d[i].n[1] * d[i].n[2]});
   std::sort(r.begin(), r.end());
@@ -526,8 +542,10 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
       dm.n[k] = domains[i].n[k];
       dm.nb[k] = domains[i].nb[k];
       dm.be[k] = domains[i].n[k] / domains[i].nb[k];
-      dm.bc[k][0] = domains[i].bc[k][0];
-      dm.bc[k][1] = domains[i].bc[k][1];
+      for (int f = 0; f < 2; f++) {
+        dm.bc[k][f] = domains[i].bc[k][f];
+        dm.asym[k][f] = domains[i].bc[k][f] == AMRFD_BC_SYMMETRIC ? domains[i].asym[k][f] : 0u;
+      }
       dm.dx[k] = domains[i].dx[k];
     }
     dm.block0 = nb;
@@ -553,6 +571,15 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
   CKH(cudaMemcpy(h->d_dom, h->hdom.data(), sizeof(DomDev) * ndomain, cudaMemcpyHostToDevice));
   CKH(cudaMalloc(&h->d_active, nb));
   CKH(cudaMemcpy(h->d_active, h->active_h.data(), nb, cudaMemcpyHostToDevice));
+  {
+    std::vector<int> bdom(nb);
+    for (int i = 0; i < ndomain; i++)
+      for (int b = 0; b < h->hdom[i].nb[0] * h->hdom[i].nb[1] * h->hdom[i].nb[2]; b++) bdom[h->hdom[i].block0 + b] = i;
+    CKH(cudaMalloc(&h->d_bdom, sizeof(int) * nb));
+    CKH(cudaMemcpy(h->d_bdom, bdom.data(), sizeof(int) * nb, cudaMemcpyHostToDevice));
+    CKH(cudaMalloc(&h->d_act_tmp[0], nb));
+    CKH(cudaMalloc(&h->d_act_tmp[1], nb));
+  }
   CKH(cudaMalloc(&h->d_counts, sizeof(int) * 2));
   CKH(cudaMalloc(&h->d_counters, sizeof(int) * 2 * kMaxStages));
   CKH(cudaMalloc(&h->d_slot, sizeof(unsigned long long) * kNumSlots * ndomain * 4));
@@ -583,6 +610,54 @@ int amrfd_set_active(amrfd_handle* h, const uint8_t* active_dev, void* stream) {
   int rc = compact(h, s);
   if (rc) return rc;
   CK(cudaStreamSynchronize(s));
+  h->active_h_stale = false;
+  return AMRFD_OK;
+}
+
+int amrfd_flag_steady(amrfd_handle* h, const double* U, const double* U_ref, double tol, uint8_t* flag_dev,
+                      void* stream) {
+  if (!h || !U || !U_ref || !flag_dev || !(tol >= 0.0)) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  CK(cudaMemsetAsync(flag_dev, 1, h->nblocks, s));
+  FlagParams p{};
+  p.doms = h->d_dom;
+  p.items = h->d_call;
+  p.nitems = h->nci;
+  p.U = U;
+  p.R = U_ref;
+  p.tol = tol;
+  p.flag = flag_dev;
+  p.nv = h->nv;
+  CK(launch_flag_steady(p, std::max(1, std::min(h->nci, 8 * h->nsm)), s));
+  return AMRFD_OK;
+}
+
+int amrfd_activate(amrfd_handle* h, const uint8_t* flag_dev, int belt, void* stream) {
+  if (!h || !flag_dev || belt < 0) return AMRFD_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  ActParams p{};
+  p.doms = h->d_dom;
+  p.bdom = h->d_bdom;
+  p.nblocks = h->nblocks;
+  p.in = flag_dev;
+  p.out = belt == 0 ? h->d_active : h->d_act_tmp[0];
+  p.first = 1;
+  CK(launch_activate(p, s));
+  p.first = 0;
+  for (int r = 0; r < belt; r++) {
+    p.in = p.out;
+    p.out = r == belt - 1 ? h->d_active : h->d_act_tmp[(r + 1) & 1];
+    CK(launch_activate(p, s));
+  }
+  int rc = compact(h, s);
+  if (rc) return rc;
+  h->active_h_stale = true;
+  return AMRFD_OK;
+}
+
+int amrfd_get_active(amrfd_handle* h, uint8_t* active_dev, void* stream) {
+  if (!h || !active_dev) return AMRFD_ERR_INVALID_ARG;
+  CK(cudaMemcpyAsync(active_dev, h->d_active, h->nblocks, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return AMRFD_OK;
 }
 
@@ -610,6 +685,8 @@ int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double 
 
 int amrfd_step(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  int rc = refresh_active_host(h, (cudaStream_t)stream);
+  if (rc) return rc;
   return enqueue_step(h, U, dt_dev, (cudaStream_t)stream, false);
 }
 
@@ -653,10 +730,12 @@ int build_adjoint_items(amrfd_handle* h) {
         const int nlines = dm.be[od1] * dm.be[od2];
         const int ext = dm.be[dir];
         const int nseg = (ext + h->adj_seg - 1) / h->adj_seg;
-        const int slen0 = (ext + nseg - 1) / nseg;
-        maxseg = std::max(maxseg, slen0);
+        maxseg = std::max(maxseg, (ext + nseg - 1) / nseg);
         for (int sg = 0; sg < nseg; sg++) {
-          const int s0 = sg * slen0, sl = std::min(slen0, ext - s0);
+          // lengths floor or ceil of ext/nseg: with two or more segments every one
+          // holds >= adj_seg/2 cells (mirror faces need their 3 image cells in one)
+          const int s0 = (int)((long long)sg * ext / nseg);
+          const int sl = (int)((long long)(sg + 1) * ext / nseg) - s0;
           for (int l0 = 0; l0 < nlines; l0 += h->adj_lines) {
             FluxItem it{};
             it.dom = d; it.blk = b; it.l0 = l0;
@@ -684,15 +763,23 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
                   void* stream) {
   if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  // supported: every domain entirely active or entirely passive; periodic lines >= 6 cells
+  {
+    int rc = refresh_active_host(h, s);
+    if (rc) return rc;
+  }
+  // supported: every domain entirely active or entirely passive; periodic lines >= 6
+  // cells; blocks >= 3 cells along a dimension with a mirror face
   for (int d = 0; d < h->ndom; d++) {
     const DomDev& dm = h->hdom[d];
     const int nbl = dm.nb[0] * dm.nb[1] * dm.nb[2];
     int na = 0;
     for (int b = 0; b < nbl; b++) na += h->active_h[dm.block0 + b] != 0;
     if (na != 0 && na != nbl) return AMRFD_ERR_UNSUPPORTED;
-    for (int k = 0; k < h->cfg.ndim; k++)
+    for (int k = 0; k < h->cfg.ndim; k++) {
       if (dm.bc[k][0] == AMRFD_BC_PERIODIC && dm.n[k] < 6) return AMRFD_ERR_UNSUPPORTED;
+      if ((dm.bc[k][0] == AMRFD_BC_SYMMETRIC || dm.bc[k][1] == AMRFD_BC_SYMMETRIC) && dm.be[k] < 3)
+        return AMRFD_ERR_UNSUPPORTED;
+    }
   }
   if (!h->d_adj_items) {
     for (int k = 1; k < h->ns; k++) CK(cudaMalloc(&h->d_gstage[k], sizeof(double) * h->nelem));
@@ -922,7 +1009,8 @@ void amrfd_destroy(amrfd_handle* h) {
   if (!h) return;
   cudaDeviceSynchronize();
   free_graphs(h);
-  cudaFree(h->d_dom); cudaFree(h->d_active);
+  cudaFree(h->d_dom); cudaFree(h->d_active); cudaFree(h->d_bdom);
+  cudaFree(h->d_act_tmp[0]); cudaFree(h->d_act_tmp[1]);
   cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
   for (int k = 0; k < 12; k++) cudaFree(h->d_grp[k]);
   cudaFree(h->d_counts); cudaFree(h->d_counters);

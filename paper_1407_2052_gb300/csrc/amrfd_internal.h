@@ -15,7 +15,8 @@ struct DomDev {
   int n[3];          // interior cells
   int be[3];         // block edge (n / nb)
   int nb[3];         // blocks per dimension
-  int bc[3][2];      // 0 periodic, 1 outflow
+  int bc[3][2];      // 0 periodic, 1 outflow, 2 mirror
+  unsigned asym[3][2];  // mirror faces: bit v = variable v odd across the face
   int block0;        // global index of the first block of this domain
   int ncell;         // n0*n1*n2
   long long off;     // element offset in every state-shaped buffer

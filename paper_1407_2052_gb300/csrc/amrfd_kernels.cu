@@ -192,8 +192,16 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
     x[od1] = o[od1] + a1;
     x[od2] = o[od2] + a2;
     int g = o[D] + it.s0 + j - kGhost;
-    if (g < 0) g = dm.bc[D][0] == 0 ? g + dm.n[D] : 0;
-    else if (g >= dm.n[D]) g = dm.bc[D][1] == 0 ? g - dm.n[D] : dm.n[D] - 1;
+    unsigned odd = 0u;  // mirror ghosts: variables negated
+    if (g < 0) {
+      const int b = dm.bc[D][0];
+      odd = dm.asym[D][0];
+      g = b == 0 ? g + dm.n[D] : (b == 1 ? 0 : -1 - g);
+    } else if (g >= dm.n[D]) {
+      const int b = dm.bc[D][1];
+      odd = dm.asym[D][1];
+      g = b == 0 ? g - dm.n[D] : (b == 1 ? dm.n[D] - 1 : 2 * dm.n[D] - 1 - g);
+    }
     x[D] = g;
     const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
     const double* base = p.active[nbk] ? p.Uk : p.Un;
@@ -202,6 +210,11 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
     double u[NV], gp[NV], gmn[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
+    if (odd) {
+#pragma unroll
+      for (int v = 0; v < NV; v++)
+        if ((odd >> v) & 1u) u[v] = -u[v];
+    }
     split_flux<PHYS, NV, D>(u, gm1, alpha, ch2, gp, gmn);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -295,7 +308,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
   const int f0 = o[D] + it.s0;
-  const int fend = f0 + slen + ((dm.bc[D][1] == 1 && f0 + slen == dm.n[D]) ? 1 : 0);
+  const int fend = f0 + slen + ((dm.bc[D][1] != 0 && f0 + slen == dm.n[D]) ? 1 : 0);
   const long long nlines = (long long)dm.n[od1] * dm.n[od2];
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
@@ -603,6 +616,75 @@ cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, i
 #define CALL(PH, NVV) combine_kernel<PH, NVV><<<grid, block, 0, s>>>(p)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
+  return cudaGetLastError();
+}
+
+// One round of App. C's safety belt: a candidate block becomes active when one of
+// its (up to 26) neighbours was active in the previous round; neighbours wrap across
+// periodic faces and do not exist beyond other faces. The first pass only inverts
+// the candidate flags.
+__global__ void activate_kernel(ActParams p) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < p.nblocks; b += gridDim.x * blockDim.x) {
+    if (p.first) { p.out[b] = p.in[b] ? 0 : 1; continue; }
+    unsigned char a = p.in[b];
+    if (!a) {
+      const DomDev& dm = p.doms[p.bdom[b]];
+      const int l = b - dm.block0;
+      const int i[3] = {l % dm.nb[0], (l / dm.nb[0]) % dm.nb[1], l / (dm.nb[0] * dm.nb[1])};
+      int lo[3], hi[3];
+#pragma unroll
+      for (int k = 0; k < 3; k++) { lo[k] = dm.nb[k] > 1 ? -1 : 0; hi[k] = -lo[k]; }
+      for (int oz = lo[2]; oz <= hi[2] && !a; oz++)
+        for (int oy = lo[1]; oy <= hi[1] && !a; oy++)
+          for (int ox = lo[0]; ox <= hi[0] && !a; ox++) {
+            const int o[3] = {ox, oy, oz};
+            int j[3];
+            bool ok = true;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+              j[k] = i[k] + o[k];
+              if (j[k] < 0 || j[k] >= dm.nb[k]) {
+                if (dm.bc[k][0] == 0) j[k] = j[k] < 0 ? j[k] + dm.nb[k] : j[k] - dm.nb[k];
+                else ok = false;
+              }
+            }
+            if (ok && p.in[dm.block0 + (j[2] * dm.nb[1] + j[1]) * dm.nb[0] + j[0]]) a = 1;
+          }
+    }
+    p.out[b] = a;
+  }
+}
+
+// Steady-state criterion over cell items; flag[] was set to 1 beforehand. NaN counts as
+// a deviation.
+__global__ void __launch_bounds__(256) flag_steady_kernel(FlagParams p) {
+  for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
+    const CellItem ci = p.items[it];
+    const DomDev dm = load_dom(p.doms + ci.dom);
+    int o[3];
+    block_coords(dm, ci.blk, o);
+    int dev = 0;
+    for (int c = threadIdx.x; c < ci.cnt && !dev; c += blockDim.x) {
+      const int l = ci.c0 + c;
+      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+      for (int v = 0; v < p.nv; v++) {
+        const long long e = idx + (long long)v * dm.ncell;
+        if (!(fabs(p.U[e] - p.R[e]) <= p.tol)) { dev = 1; break; }
+      }
+    }
+    if (__syncthreads_or(dev) && threadIdx.x == 0) p.flag[dm.block0 + ci.blk] = 0;
+  }
+}
+
+cudaError_t launch_activate(const ActParams& p, cudaStream_t s) {
+  const int grid = p.nblocks > 0 ? (p.nblocks + 255) / 256 : 1;
+  activate_kernel<<<grid < 1024 ? grid : 1024, 256, 0, s>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_flag_steady(const FlagParams& p, int grid, cudaStream_t s) {
+  flag_steady_kernel<<<grid, 256, 0, s>>>(p);
   return cudaGetLastError();
 }
 

@@ -138,6 +138,31 @@ struct AdjCombParams {
   int nv;
 };
 
+// Dynamic activation (App. C): one pass of the safety belt over all blocks.
+struct ActParams {
+  const DomDev* doms;
+  const int* bdom;               // domain of every block
+  int nblocks;
+  const unsigned char* in;       // first pass: the candidate flags; later: the previous active flags
+  unsigned char* out;
+  int first;
+};
+
+// Steady-state criterion: clears flag[b] when a cell of block b is farther than tol from R.
+struct FlagParams {
+  const DomDev* doms;
+  const CellItem* items;         // every block's cell items
+  int nitems;
+  const double* U;
+  const double* R;
+  double tol;
+  unsigned char* flag;
+  int nv;
+};
+
+cudaError_t launch_activate(const ActParams& p, cudaStream_t s);
+cudaError_t launch_flag_steady(const FlagParams& p, int grid, cudaStream_t s);
+
 // launch wrappers (dispatch on physics / number of variables)
 cudaError_t launch_adj_flux(int physics, int nv, const AdjFluxParams& p, int grid, int block, size_t smem,
                             cudaStream_t s);

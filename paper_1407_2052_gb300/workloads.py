@@ -20,7 +20,7 @@ import numpy as np
 SEED0 = 14072052
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
-PERIODIC, OUTFLOW = 0, 1
+PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
 
 
 @dataclass
@@ -30,6 +30,7 @@ class Domain:
     bc: tuple = ((PERIODIC, PERIODIC),) * 3
     nb: tuple = (1, 1, 1)  # blocks per dimension
     offset: int = 0     # element offset of this domain in a batched state buffer
+    asym: tuple = ((0, 0),) * 3  # SYMMETRIC faces: bit mask of the odd variables
 
     @property
     def ncell(self):
@@ -90,6 +91,39 @@ def sod(n=512):
                     extra={"x": x})
 
 
+def closed_sod(n=400):
+    """Sod's data in a closed tube [0,1] with reflecting walls at both ends (mirror
+    ghosts, m_x odd), SSPRK3, CFL 0.4, t = 0.4: the shock reflects off x = 1."""
+    w = sod(n)
+    d = w.domains[0]
+    dom = Domain(d.n, d.dx, bc=((SYMMETRIC, SYMMETRIC),) + d.bc[1:], asym=((2, 2), (0, 0), (0, 0)))
+    return Workload("closed_sod", EULER, 1, SSPRK3, 1.4, 0.4, [dom], w.U, t_end=0.4, extra=w.extra)
+
+
+# reflecting wall normal to y for MHD+GLM: m_y, B_x, B_z and psi odd (B a pseudovector)
+MHD_WALL_Y = (1 << 2) | (1 << 5) | (1 << 7) | (1 << 8)
+
+
+def wall_blast2d(n=128, block=32, integrator=SSPRK3, seed_index=5):
+    """2D MHD+GLM blast next to reflecting walls: [-0.5,0.5]^2, periodic in x, mirror
+    walls at y = -0.5 and 0.5; p = 10 inside r < 0.1 around (0.1, -0.35), 0.1 outside;
+    rho = 1 (1 + 1e-3 (2u - 1)), B = (1, 1, 0)/sqrt(2), gamma 5/3, CFL 0.3."""
+    rng = np.random.default_rng(SEED0 + seed_index)
+    x, dx = centres(n, -0.5, 0.5)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    r = np.hypot(X - 0.1, Y + 0.35)
+    rho = 1.0 + 1e-3 * (2.0 * rng.random((n, n)) - 1.0)
+    p = np.where(r < 0.1, 10.0, 0.1)
+    zero = np.zeros_like(rho)
+    b = 1.0 / np.sqrt(2.0)
+    U = conserved_mhd(rho, [zero, zero, zero], p, [zero + b, zero + b, zero], 5.0 / 3.0).reshape(9, 1, n, n)
+    nb = n // block
+    dom = Domain((n, n, 1), (dx, dx, 1.0), bc=((PERIODIC, PERIODIC), (SYMMETRIC, SYMMETRIC), (PERIODIC, PERIODIC)),
+                 nb=(nb, nb, 1), asym=((0, 0), (MHD_WALL_Y, MHD_WALL_Y), (0, 0)))
+    return Workload("wall_blast2d", MHD_GLM, 2, integrator, 5.0 / 3.0, 0.3, [dom], U,
+                    active=np.ones(nb * nb, np.uint8))
+
+
 def vortex2d(n=1024, integrator=SSPRK54):
     """2D MHD+GLM smooth vortex on periodic [0,2pi]^2, gamma 5/3."""
     x, dx = centres(n, 0.0, 2 * np.pi)
@@ -103,13 +137,15 @@ def vortex2d(n=1024, integrator=SSPRK54):
     return Workload("vortex2d", MHD_GLM, 2, integrator, 5.0 / 3.0, 0.4, [dom], U, nsteps=500)
 
 
-def blast3d(n=256, block=16, seed_index=2):
-    """3D MHD+GLM blast on periodic [-0.5,0.5]^3, gamma 5/3, SSPRK3, CFL 0.3."""
+def blast3d(n=256, block=16, seed_index=2, noise=1e-3):
+    """3D MHD+GLM blast on periodic [-0.5,0.5]^3, gamma 5/3, SSPRK3, CFL 0.3.
+    noise = 0 gives a uniform background, exactly steady away from the blast (the
+    dynamic-activation case of App. C)."""
     rng = np.random.default_rng(SEED0 + seed_index)
     x, dx = centres(n, -0.5, 0.5)
     Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
     r = np.sqrt(X * X + Y * Y + Z * Z)
-    rho = 1.0 * (1.0 + 1e-3 * (2.0 * rng.random((n, n, n)) - 1.0))
+    rho = 1.0 * (1.0 + noise * (2.0 * rng.random((n, n, n)) - 1.0))
     p = np.where(r < 0.1, 10.0, 0.1)
     zero = np.zeros_like(rho)
     b = 1.0 / np.sqrt(2.0)

@@ -41,7 +41,7 @@ def _torchref():
 
 
 def _odom(d):
-    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb)
+    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb, asym=d.asym)
 
 
 def _gpu_adjoint(w, dt, g):
@@ -62,12 +62,12 @@ def _ref_grad(w, dt, g):
     _, fl, al, ch = O.step(c, _odom(w.domains[0]), w.U, dt)
     U = torch.from_numpy(w.U.copy()).requires_grad_(True)
     out = T.step(U, dt, w.domains[0].dx, w.domains[0].bc, w.physics, w.ndim, w.gamma, w.integrator, al, ch,
-                 w.glm_cr)
+                 w.glm_cr, asym=w.domains[0].asym)
     (out * torch.from_numpy(g)).sum().backward()
     return U.grad.numpy(), al, ch
 
 
-def _smooth(physics, ndim, n, bc, seed, integrator):
+def _smooth(physics, ndim, n, bc, seed, integrator, asym=((0, 0),) * 3, nb=(1, 1, 1)):
     rng = np.random.default_rng(seed)
     g = 1.4 if physics == O.EULER else 5 / 3
     dx = [1.0 / n[0], 1.0 / max(n[1], 1), 1.0 / max(n[2], 1)]
@@ -83,8 +83,9 @@ def _smooth(physics, ndim, n, bc, seed, integrator):
         U = W.conserved_euler(rho, vel[:ndim], p, g)
     else:
         U = W.conserved_mhd(rho, vel, p, [0.5 + f(0.1), 0.2 + f(0.1), 0.1 + f(0.1)], g, psi=f(0.01))
-    dom = W.Domain(tuple(n), tuple(dx), bc=bc)
-    return W.Workload("smooth", physics, ndim, integrator, g, 0.4, [dom], U, active=np.ones(1, np.uint8))
+    dom = W.Domain(tuple(n), tuple(dx), bc=bc, asym=asym, nb=nb)
+    return W.Workload("smooth", physics, ndim, integrator, g, 0.4, [dom], U,
+                      active=np.ones(nb[0] * nb[1] * nb[2], np.uint8))
 
 
 CASES = [
@@ -94,6 +95,15 @@ CASES = [
     ("euler2d_mixed", lambda: _smooth(O.EULER, 2, (24, 20, 1), ((1, 1), (0, 0), (0, 0)), 2, O.SSPRK54), 2e-3),
     ("mhd3d_mixed", lambda: _smooth(O.MHD_GLM, 3, (12, 10, 8), ((0, 0), (1, 1), (0, 0)), 3, O.SSPRK3), 1e-3),
     ("euler3d_ssprk43", lambda: _smooth(O.EULER, 3, (10, 8, 12), ((0, 0), (0, 0), (1, 1)), 4, O.SSPRK43), 2e-3),
+    # mirror faces: a closed 1D tube, MHD walls normal to y, and mixed mirror / outflow
+    # faces with a no-slip mask on 3 x 2 blocks
+    ("euler1d_walls", lambda: _smooth(O.EULER, 1, (40, 1, 1), ((2, 2), (0, 0), (0, 0)), 5, O.SSPRK3,
+                                      asym=((2, 2), (0, 0), (0, 0))), 2e-3),
+    ("mhd2d_wall_y", lambda: _smooth(O.MHD_GLM, 2, (24, 20, 1), ((0, 0), (2, 2), (0, 0)), 6, O.SSPRK54,
+                                     asym=((0, 0), (W.MHD_WALL_Y, W.MHD_WALL_Y), (0, 0))), 1e-3),
+    ("euler2d_mirror_outflow_blocks", lambda: _smooth(O.EULER, 2, (36, 16, 1), ((2, 1), (2, 2), (0, 0)), 7,
+                                                      O.SSPRK3, asym=((6, 0), (6, 6), (0, 0)), nb=(3, 2, 1)),
+     2e-3),
 ]
 
 

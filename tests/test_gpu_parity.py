@@ -69,7 +69,7 @@ def ocfg(w):
 
 
 def odom(d):
-    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb)
+    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb, asym=d.asym)
 
 
 def dev(x):
@@ -424,3 +424,79 @@ def test_vortex_1024_500_steps_stays_physical_and_conservative():
         s.step_batched(U, dt)
     assert s.error() == A().OK
     assert torch.all((V[:8].sum(dim=1) - tot0).abs() <= 1e-11 * scale)
+
+
+# --------------------------------------------------------------- mirror faces
+def test_closed_sod_reflection_to_final_time():
+    """Sod's data in a closed tube (mirror walls, m_x odd) to t = 0.4, after the shock has
+    reflected off x = 1: same step count as the oracle, relative L1 <= 1e-10, and the walls
+    pass no mass."""
+    w = W.closed_sod(400)
+    c, d = ocfg(w), odom(w.domains[0])
+    Uo, t, n, fl = O.evolve(c, d, w.U, w.cfl, w.t_end)
+    assert fl == 0
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        s.step_batched(U, dt)
+        tg += float(dt[0].item())
+        ng += 1
+    assert s.error() == A().OK and ng == n
+    got = host(U, Uo.shape)
+    assert rel_l1(got, Uo) <= 1e-10
+    assert abs(got[0].sum() - w.U[0].sum()) <= 1e-12 * w.U[0].sum()
+    assert got[0, 0, 0, -1] > 0.3  # the reflected shock has compressed the gas at x = 1
+
+
+@pytest.mark.parametrize("batched", [True, False])
+def test_wall_blast_multiblock_vs_oracle(batched):
+    """2D MHD blast next to reflecting walls (m_y, B_x, B_z, psi odd), 4 x 4 blocks of 32^2,
+    20 SSPRK3 steps with the CFL dt: first dt bitwise, relative L1 <= 1e-10."""
+    w = W.wall_blast2d(128, 32)
+    s, U, dts = run_gpu(w, 20, batched=batched)
+    ref, odts = run_oracle(w, 20)
+    # dt of U^n bitwise; later states differ by rounding, their dt by an ulp or so
+    got = [float(x[0].item()) for x in dts]
+    assert got[0] == odts[0]
+    assert np.allclose(got, odts, rtol=1e-13, atol=0.0)
+    assert rel_l1(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-10
+
+
+MIRROR = [
+    # closed 1D tube, no-slip walls in x of a 3D box, mixed mirror / outflow faces with
+    # arbitrary sign masks over the momenta, fields and psi (the halo rule must hold for
+    # any mask; rho and E stay even so that the ghosts stay physical)
+    (O.EULER, 1, (37, 1, 1), ((2, 2), (0, 0), (0, 0)), ((2, 2), (0, 0), (0, 0)), (1, 1, 1)),
+    (O.EULER, 3, (13, 11, 9), ((2, 2), (0, 0), (1, 1)), ((14, 14), (0, 0), (0, 0)), (1, 1, 1)),
+    (O.MHD_GLM, 2, (45, 70, 1), ((2, 1), (1, 2), (0, 0)), ((0x1A6, 0), (0, 0x0E0), (0, 0)), (1, 1, 1)),
+    (O.MHD_GLM, 3, (24, 12, 16), ((2, 2), (0, 0), (2, 1)), ((0x1EE, 0x002), (0, 0), (0x1A4, 0)), (3, 2, 2)),
+]
+
+
+@pytest.mark.parametrize("case", range(len(MIRROR)))
+@pytest.mark.parametrize("batched", [True, False])
+def test_mirror_faces_smooth_one_step(case, batched):
+    physics, ndim, n, bc, asym, nb = MIRROR[case]
+    w = _smooth_domain(physics, ndim, n, bc, seed=30 + case, nb=nb)
+    w.domains[0].asym = asym
+    s, U, dts = run_gpu(w, 1, batched=batched)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+def test_mirror_faces_tile_invariance():
+    """Segments that end on a mirror face give the same bits under every tile."""
+    w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((2, 2), (2, 1), (0, 0)), seed=41, nb=(5, 3, 2))
+    w.domains[0].asym = ((0x1A2, 0x1A2), (0x1A4, 0x004), (0, 0))
+    base = None
+    for tile in [(16, 8, 128), (32, 16, 160), (64, 4, 64), (8, 32, 288)]:
+        s = A().Solver.from_workload(w)
+        s.set_tile(*tile)
+        _, U, _ = run_gpu(w, 2, solver=s)
+        out = U.cpu()
+        if base is None:
+            base = out
+        assert torch.equal(out, base), tile

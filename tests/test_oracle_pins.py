@@ -31,7 +31,7 @@ def _golden(name):
 
 
 def _odom(d):
-    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb)
+    return O.dom(d.n, d.dx, bc=[list(b) for b in d.bc], nb=d.nb, asym=d.asym)
 
 
 def _ocfg(w, integrator=None):
@@ -430,3 +430,167 @@ def test_dt_closed_form_uniform():
     wm, _ = O.cons2prim(cm, um)
     chh = max(O.char_speed(cm, wm, 0), O.char_speed(cm, wm, 1))
     assert O.dt(cm, d, Um, 0.4)[0] == pytest.approx(0.4 / (chh / 0.1 + chh / 0.3), rel=1e-14)
+
+
+def _mirror_double(U, axis, sgn):
+    """Periodic data of twice the length: U followed by its mirror image times sgn."""
+    return np.concatenate([U, sgn * np.flip(U, axis=axis)], axis=axis)
+
+
+# (physics, ndim, mirror dimension, odd variables): reflections under which the
+# equations are invariant -- Euler: the normal momentum; MHD (B a pseudovector):
+# the normal momentum, the tangential field and psi (whose flux is c_h^2 B_d)
+MIRROR_CASES = [
+    (O.EULER, 1, 0, [1]),
+    (O.EULER, 3, 2, [3]),
+    (O.MHD_GLM, 2, 1, [2, 5, 7, 8]),
+    (O.MHD_GLM, 2, 0, [1, 6, 7, 8]),
+]
+
+
+@pytest.mark.parametrize("physics,ndim,md,odd", MIRROR_CASES)
+def test_symmetric_walls_equal_mirror_doubled_periodic_domain(physics, ndim, md, odd):
+    """A domain with mirror (symmetric/antisymmetric) ghosts on both faces of dimension md
+    evolves exactly like the first half of the periodic domain of twice the length holding
+    the data followed by its mirror image: both see the same values at every face, and the
+    update commutes with the reflection. Five SSPRK3 steps, compared bitwise."""
+    rng = np.random.default_rng(40 + md + 10 * physics)
+    g = 1.4 if physics == O.EULER else 5 / 3
+    n = [12 if k < ndim else 1 for k in range(3)]
+    n[md] = 10
+    shape = (n[2], n[1], n[0])
+    rho = 1.0 + 0.3 * rng.random(shape)
+    p = 1.0 + 0.3 * rng.random(shape)
+    vel = [0.5 * rng.standard_normal(shape) for _ in range(3)]
+    if physics == O.EULER:
+        U = W.conserved_euler(rho, vel[:ndim], p, g)
+    else:
+        U = W.conserved_mhd(rho, vel, p, [0.6 + 0.2 * rng.standard_normal(shape) for _ in range(3)], g,
+                            psi=0.05 * rng.standard_normal(shape))
+    nv = U.shape[0]
+    sgn = np.ones((nv, 1, 1, 1))
+    sgn[odd] = -1.0
+    mask = sum(1 << v for v in odd)
+    axis = 3 - md
+    bc = [[O.PERIODIC, O.PERIODIC] for _ in range(3)]
+    bc[md] = [O.SYMMETRIC, O.SYMMETRIC]
+    asym = [[0, 0] for _ in range(3)]
+    asym[md] = [mask, mask]
+    dx = [0.1, 0.07, 0.05]
+    c = O.cfg(physics, ndim, O.SSPRK3, g)
+    dw = O.dom(n, dx, bc=bc, asym=asym)
+    n2 = list(n)
+    n2[md] *= 2
+    dp = O.dom(n2, dx)
+    Uw, Up = U.copy(), _mirror_double(U, axis, sgn)
+    for _ in range(5):
+        hw, _ = O.dt(c, dw, Uw, 0.4)
+        hp, _ = O.dt(c, dp, Up, 0.4)
+        assert hw == hp
+        Uw, fw, _, _ = O.step(c, dw, Uw, hw)
+        Up, fp, _, _ = O.step(c, dp, Up, hp)
+        assert fw == 0 and fp == 0
+    half = np.split(Up, 2, axis=axis)[0]
+    assert np.array_equal(Uw, half)
+    # and the doubled run itself kept its mirror symmetry
+    assert np.array_equal(Up, _mirror_double(half, axis, sgn))
+
+
+def test_symmetric_ghost_kinds_differ_from_outflow():
+    """Mirror ghosts are not the zero-gradient copy: with a flow into the wall the
+    reflecting face builds up pressure, the outflow face lets the flow leave."""
+    n = 32
+    U = W.conserved_euler(np.ones(n), [np.full(n, 0.5)], np.ones(n), 1.4).reshape(3, 1, 1, n)
+    c = O.cfg(O.EULER, 1)
+    dw = O.dom([n], [1.0 / n], bc=[[O.OUTFLOW, O.SYMMETRIC], [0, 0], [0, 0]], asym=[[0, 2], [0, 0], [0, 0]])
+    do = O.dom([n], [1.0 / n], bc=O.OUTFLOW)
+    Uw, Uo = U.copy(), U.copy()
+    for _ in range(10):
+        Uw, _, _, _ = O.step(c, dw, Uw, 0.2 / n)
+        Uo, _, _, _ = O.step(c, do, Uo, 0.2 / n)
+    assert np.array_equal(Uo, U)                    # uniform outflow state is exactly steady
+    assert Uw[0, 0, 0, -1] > 1.05 and abs(Uw[1, 0, 0, -1]) < 0.5 * 0.5  # compressed, slowed at the wall
+
+
+def test_brio_wu_contact_overshoot_matches_paper_magnitude():
+    """Sec. 4.5.2: SSPRK(5,4)-MP5-FD overshoots the density at the contact of the
+    Brio-Wu tube by +2.7% (512 cells on [-1,1]). The plateau left of the contact is taken
+    from the same scheme at 1024 cells (the mean over 0 < x < 0.09 at t = 0.2); the
+    overshoot is the maximum of the 512-cell density near the contact relative to it.
+    This reading gives +2.1-2.2% (the paper's reference was a 65536-cell TVD run and
+    the time is not printed); the pin holds the sign and magnitude: 1% .. 4%."""
+    def run(n):
+        w = W.brio_wu(n)
+        c = _ocfg(w)
+        d = _odom(w.domains[0])
+        U, _, _, fl = O.evolve(c, d, w.U, 0.4, w.t_end)
+        assert fl == 0
+        return w.extra["x"], U[0, 0, 0]
+    x, r = run(512)
+    xr, rr = run(1024)
+    plateau = rr[(xr > 0.0) & (xr < 0.09)].mean()
+    over = r[(x > 0.05) & (x < 0.14)].max() / plateau - 1.0
+    assert 0.01 <= over <= 0.04, over
+
+
+# ------------------------------------------------------- dynamic activation (App. C)
+def _chebyshev_activate(d, flag, belt):
+    """Independent statement of the belt: a block is active when some unflagged block lies
+    within Chebyshev distance <= belt (block units; distances wrap across periodic faces)."""
+    nb = [d.nb[k] for k in range(3)]
+    idx = np.array([(b % nb[0], (b // nb[0]) % nb[1], b // (nb[0] * nb[1])) for b in range(np.prod(nb))])
+    src = idx[np.asarray(flag) == 0]
+    out = np.zeros(len(idx), np.uint8)
+    for b, i in enumerate(idx):
+        if len(src) == 0:
+            break
+        dist = np.abs(src - i)
+        for k in range(3):
+            if d.bc[k][0] == O.PERIODIC:
+                dist[:, k] = np.minimum(dist[:, k], nb[k] - dist[:, k])
+        out[b] = np.any(dist.max(axis=1) <= belt)
+    return out
+
+
+def test_activate_hand_cases():
+    d = O.dom([40], [0.1], bc=O.OUTFLOW, nb=(10, 1, 1))
+    flag = np.ones(10, np.uint8)
+    flag[4] = 0
+    assert O.activate(d, flag, 0).tolist() == [0, 0, 0, 0, 1, 0, 0, 0, 0, 0]
+    assert O.activate(d, flag, 1).tolist() == [0, 0, 0, 1, 1, 1, 0, 0, 0, 0]
+    assert O.activate(d, flag, 2).tolist() == [0, 0, 1, 1, 1, 1, 1, 0, 0, 0]
+    flag = np.ones(10, np.uint8)
+    flag[0] = 0
+    assert O.activate(d, flag, 1).tolist() == [1, 1, 0, 0, 0, 0, 0, 0, 0, 0]  # no wrap at outflow
+    dp = O.dom([40], [0.1], bc=O.PERIODIC, nb=(10, 1, 1))
+    assert O.activate(dp, flag, 1).tolist() == [1, 1, 0, 0, 0, 0, 0, 0, 0, 1]  # wrap
+    # a corner neighbour counts
+    d3 = O.dom([12, 12, 12], [0.1] * 3, bc=O.OUTFLOW, nb=(3, 3, 3))
+    f3 = np.ones(27, np.uint8)
+    f3[0] = 0
+    a3 = O.activate(d3, f3, 1).reshape(3, 3, 3)
+    assert a3[1, 1, 1] == 1 and a3[2, 2, 2] == 0 and a3[:2, :2, :2].all() and a3.sum() == 8
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_activate_equals_chebyshev_distance_rule(seed):
+    rng = np.random.default_rng(seed)
+    nb = [int(x) for x in rng.integers(1, 7, 3)]
+    bc = [[int(b)] * 2 for b in rng.integers(0, 3, 3)]
+    d = O.dom([4 * x for x in nb], [0.1] * 3, bc=bc, nb=nb)
+    flag = (rng.random(int(np.prod(nb))) > 0.08).astype(np.uint8)
+    for belt in range(4):
+        assert np.array_equal(O.activate(d, flag, belt), _chebyshev_activate(d, flag, belt)), (belt, nb, bc)
+
+
+def test_flag_steady_blockwise():
+    w = W.blast3d(16, 8)
+    c = _ocfg(w)
+    d = _odom(w.domains[0])
+    R = w.U.copy()
+    U = R.copy()
+    assert O.flag_steady(c, d, U, R, 0.0).tolist() == [1] * 8
+    U[4, 3, 9, 2] += 1e-9         # block (x 0, y 1, z 0) = 2
+    U[8, 12, 12, 12] = np.nan     # block 7
+    assert O.flag_steady(c, d, U, R, 1e-10).tolist() == [1, 1, 0, 1, 1, 1, 1, 0]
+    assert O.flag_steady(c, d, U, R, 1e-8).tolist() == [1, 1, 1, 1, 1, 1, 1, 0]

@@ -13,13 +13,23 @@ import torch
 EULER, MHD_GLM = 0, 1
 
 
-def _pad(u, axis, n_ghost, bc):
+def _signs(u, mask):
+    s = torch.tensor([-1.0 if (mask >> v) & 1 else 1.0 for v in range(u.shape[0])], dtype=u.dtype)
+    return s.view(-1, *([1] * (u.dim() - 1)))
+
+
+def _pad(u, axis, n_ghost, bc, asym=(0, 0)):
+    """Ghost layers: 0 periodic wrap, 1 zero-gradient copy, 2 mirror image with the
+    variables flagged in the face's mask negated."""
     lo, hi = bc
     idx = [slice(None)] * u.dim()
     parts = []
     if lo == 0:
         idx[axis] = slice(-n_ghost, None)
         parts.append(u[tuple(idx)])
+    elif lo == 2:
+        idx[axis] = slice(0, n_ghost)
+        parts.append(torch.flip(u[tuple(idx)], dims=[axis]) * _signs(u, asym[0]))
     else:
         idx[axis] = slice(0, 1)
         parts.append(u[tuple(idx)].expand(*[n_ghost if k == axis else -1 for k in range(u.dim())]))
@@ -27,6 +37,9 @@ def _pad(u, axis, n_ghost, bc):
     if hi == 0:
         idx[axis] = slice(0, n_ghost)
         parts.append(u[tuple(idx)])
+    elif hi == 2:
+        idx[axis] = slice(-n_ghost, None)
+        parts.append(torch.flip(u[tuple(idx)], dims=[axis]) * _signs(u, asym[1]))
     else:
         idx[axis] = slice(-1, None)
         parts.append(u[tuple(idx)].expand(*[n_ghost if k == axis else -1 for k in range(u.dim())]))
@@ -114,12 +127,12 @@ def _flux(U, d, physics, ndim, gamma, ch):
     return torch.stack(f)
 
 
-def residual(U, dx, bc, physics, ndim, gamma, alpha, ch):
+def residual(U, dx, bc, physics, ndim, gamma, alpha, ch, asym=None):
     """L(U) for U of shape (nv, nz, ny, nx); alpha[d] fixed splitting speeds."""
     L = torch.zeros_like(U)
     for d in range(ndim):
         axis = 3 - d  # x is the last axis
-        Ue = _pad(U, axis, 3, bc[d])
+        Ue = _pad(U, axis, 3, bc[d], asym[d] if asym is not None else (0, 0))
         F = _flux(Ue, d, physics, ndim, gamma, ch)
         Fp = 0.5 * (F + alpha[d] * Ue)
         Fm = 0.5 * (F - alpha[d] * Ue)
@@ -156,13 +169,13 @@ def ssprk_table(integrator):
     return a, b
 
 
-def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18):
+def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18, asym=None):
     """One SSPRK step with frozen per-stage splitting speeds alpha_stage[s][3] and c_h."""
     a, b = ssprk_table(integrator)
     stages = [U]
     Ls = []
     for i in range(len(a)):
-        Ls.append(residual(stages[i], dx, bc, physics, ndim, gamma, alpha_stage[i], ch))
+        Ls.append(residual(stages[i], dx, bc, physics, ndim, gamma, alpha_stage[i], ch, asym))
         acc = torch.zeros_like(U)
         for k in range(i + 1):
             if a[i][k] != 0.0:
