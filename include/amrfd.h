@@ -44,6 +44,8 @@ extern "C" {
 #define AMRFD_SSPRK3 0
 #define AMRFD_SSPRK54 1
 #define AMRFD_SSPRK43 2
+#define AMRFD_MP5 0
+#define AMRFD_LIMO3 1
 #define AMRFD_BC_PERIODIC 0
 #define AMRFD_BC_OUTFLOW 1
 #define AMRFD_BC_SYMMETRIC 2 /* mirror ghosts, per-variable sign: see amrfd_domain.asym */
@@ -65,6 +67,10 @@ typedef struct amrfd_config {
   double gamma;   /* ratio of specific heats, > 1 */
   double cfl;     /* Courant number used by amrfd_dt */
   double glm_cr;  /* MHD: psi damping length c_r = c_p^2/c_h (Sec. 4.2); <= 0 disables damping */
+  int recon;      /* AMRFD_MP5 (Suresh & Huynh, Sec. 2.2) | AMRFD_LIMO3 (Cada & Torrilhon, Sec. 2.2) */
+  int reserved_;  /* set to 0 */
+  double limo3_r; /* LIMO3: radius r of the asymptotic region, > 0; the switch compares
+                     (delta_-^2 + delta_+^2) of the split fluxes with (r dx)^2 */
 } amrfd_config;
 
 typedef struct amrfd_domain {
@@ -149,7 +155,8 @@ int amrfd_step_batched(amrfd_handle *h, double *U, const double *dt_dev, void *s
    gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
    Splitting speeds c_max, c_h and the psi damping factor are held fixed at
    the values the forward step used; MP5 limiter branches are replayed from
-   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED for a domain that
+   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED with LIMO3
+   reconstruction (the adjoint covers MP5), for a domain that
    is partly active, a periodic dimension of fewer than 6 cells, or a mirror
    dimension whose blocks hold fewer than 3 cells along it. */
 int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,

@@ -20,12 +20,14 @@ from . import build as _build
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
+MP5, LIMO3 = 0, 1
 FLAG_NONPHYSICAL = 1
 
 
 class Cfg(ctypes.Structure):
     _fields_ = [("physics", ctypes.c_int), ("ndim", ctypes.c_int), ("integrator", ctypes.c_int),
-                ("pad_", ctypes.c_int), ("gamma", ctypes.c_double), ("glm_cr", ctypes.c_double)]
+                ("recon", ctypes.c_int), ("gamma", ctypes.c_double), ("glm_cr", ctypes.c_double),
+                ("limo3_r", ctypes.c_double)]
 
 
 class Dom(ctypes.Structure):
@@ -53,6 +55,8 @@ def lib():
         for fn in ("orc_mp5",):
             getattr(L, fn).argtypes = [ctypes.c_double] * 5
             getattr(L, fn).restype = ctypes.c_double
+        L.orc_limo3.argtypes = [ctypes.c_double] * 4
+        L.orc_limo3.restype = ctypes.c_double
         L.orc_minmod.argtypes = [ctypes.c_double] * 2
         L.orc_minmod.restype = ctypes.c_double
         L.orc_minmod4.argtypes = [ctypes.c_double] * 4
@@ -81,8 +85,8 @@ def _u8(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
 
 
-def cfg(physics, ndim, integrator=SSPRK3, gamma=1.4, glm_cr=0.18):
-    return Cfg(physics, ndim, integrator, 0, gamma, glm_cr)
+def cfg(physics, ndim, integrator=SSPRK3, gamma=1.4, glm_cr=0.18, recon=MP5, limo3_r=1.0):
+    return Cfg(physics, ndim, integrator, recon, gamma, glm_cr, limo3_r)
 
 
 def dom(n, dx, bc=PERIODIC, nb=(1, 1, 1), asym=None):
@@ -148,6 +152,10 @@ def flux(c, u, d, ch=0.0):
 
 def mp5(a, b, cc, d, e):
     return lib().orc_mp5(a, b, cc, d, e)
+
+
+def limo3(um, u0, up, rdx):
+    return lib().orc_limo3(um, u0, up, rdx)
 
 
 def minmod(a, b):

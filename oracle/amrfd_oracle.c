@@ -147,6 +147,37 @@ double orc_mp5(double fm2, double fm1, double f0, double fp1, double fp2) {
   return f_or + orc_minmod(f_min - f_or, f_max - f_or); /* median(f_or, f_min, f_max) */
 }
 
+/* LIMO3 (Cada & Torrilhon 2009, cited in Sec. 2.2 and used with RK3 in Sec. 4.5):
+   left-biased value at the face i+1/2 from (u_{i-1}, u_i, u_{i+1}),
+   u_i + delta_{i+1/2} phi(theta) / 2 with theta = delta_{i-1/2} / delta_{i+1/2}.
+   phi_3 = (2 + theta)/3 is the unlimited third-order reconstruction; the limited
+   phi^_3 = max(0, min(phi_3, max(-theta/2, min(2 theta, phi_3, 1.6)))). The switch
+   eta = (delta_{i-1/2}^2 + delta_{i+1/2}^2) / (r dx)^2 selects phi_3 inside the
+   asymptotic region (eta <= 1 - eps), phi^_3 outside (eta >= 1 + eps), and blends
+   linearly in between, eps = 1e-12. At delta_{i+1/2} = 0 the limits are taken:
+   delta phi_3 -> delta_{i-1/2}, delta phi^_3 -> 0. The right-biased value at i+1/2
+   is orc_limo3(u_{i+2}, u_{i+1}, u_i, rdx). rdx = r dx. */
+double orc_limo3(double um, double u0, double up, double rdx) {
+  const double eps = 1e-12;
+  const double dm = u0 - um, dp = up - u0; /* delta_{i-1/2}, delta_{i+1/2} */
+  const double eta = (dm * dm + dp * dp) / (rdx * rdx);
+  double dphi3, dphil, dphi;
+  if (dp != 0.0) {
+    const double th = dm / dp;
+    const double phi3 = (2.0 + th) / 3.0;
+    const double phil = fmax(0.0, fmin(phi3, fmax(-0.5 * th, fmin(fmin(2.0 * th, phi3), 1.6))));
+    dphi3 = dp * phi3;
+    dphil = dp * phil;
+  } else {
+    dphi3 = dm / 3.0;
+    dphil = 0.0;
+  }
+  if (eta <= 1.0 - eps) dphi = dphi3;
+  else if (eta >= 1.0 + eps) dphi = dphil;
+  else dphi = 0.5 * ((1.0 - (eta - 1.0) / eps) * dphi3 + (1.0 + (eta - 1.0) / eps) * dphil);
+  return u0 + 0.5 * dphi;
+}
+
 /* ---- SSPRK tables (Sec. 2.3) -------------------------------------------- */
 int orc_ssprk_table(int integrator, double a[5][5], double b[5][5]) {
   memset(a, 0, sizeof(double) * 25);
@@ -309,10 +340,17 @@ int orc_residual(const orc_cfg *c, const orc_dom *dm, const double *U, const dou
         /* interface fluxes at faces k = 0..n (face k sits between cells k-1 and k) */
         for (v = 0; v < nv; v++) {
           const double *P = Fp + v * m, *M = Fm + v * m;
+          const double rdx = c->limo3_r * dm->dx[d];
           for (k = 0; k <= n; k++) {
             int ii = k - 1 + NG; /* extended index of the cell left of the face */
-            double left = orc_mp5(P[ii - 2], P[ii - 1], P[ii], P[ii + 1], P[ii + 2]);
-            double right = orc_mp5(M[ii + 3], M[ii + 2], M[ii + 1], M[ii], M[ii - 1]);
+            double left, right;
+            if (c->recon == ORC_LIMO3) {
+              left = orc_limo3(P[ii - 1], P[ii], P[ii + 1], rdx);
+              right = orc_limo3(M[ii + 2], M[ii + 1], M[ii], rdx);
+            } else {
+              left = orc_mp5(P[ii - 2], P[ii - 1], P[ii], P[ii + 1], P[ii + 2]);
+              right = orc_mp5(M[ii + 3], M[ii + 2], M[ii + 1], M[ii], M[ii - 1]);
+            }
             Fh[v * (n + 1) + k] = left + right;
           }
         }

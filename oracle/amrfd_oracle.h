@@ -23,6 +23,8 @@
 #define ORC_SSPRK3 0
 #define ORC_SSPRK54 1
 #define ORC_SSPRK43 2
+#define ORC_MP5 0
+#define ORC_LIMO3 1
 #define ORC_BC_PERIODIC 0
 #define ORC_BC_OUTFLOW 1
 #define ORC_BC_SYMMETRIC 2 /* mirror ghosts; variables flagged in asym[d][f] change sign */
@@ -34,9 +36,10 @@ typedef struct orc_cfg {
   int physics;    /* ORC_EULER | ORC_MHD_GLM */
   int ndim;       /* 1..3 */
   int integrator; /* ORC_SSPRK3 | ORC_SSPRK54 | ORC_SSPRK43 */
-  int pad_;
+  int recon;      /* ORC_MP5 | ORC_LIMO3 */
   double gamma;
   double glm_cr;  /* psi damping length c_r = c_p^2/c_h; <= 0 disables damping */
+  double limo3_r; /* LIMO3: radius r of the asymptotic region (eta uses r dx) */
 } orc_cfg;
 
 typedef struct orc_dom {
@@ -54,6 +57,7 @@ int orc_cons2prim(const orc_cfg *c, const double *u, double *w /* rho,vx,vy,vz,p
 double orc_char_speed(const orc_cfg *c, const double *w, int d);
 void orc_flux(const orc_cfg *c, const double *u, const double *w, int d, double ch, double *f);
 double orc_mp5(double a, double b, double cc, double d, double e);
+double orc_limo3(double um, double u0, double up, double rdx);
 double orc_minmod(double a, double b);
 double orc_minmod4(double w, double x, double y, double z);
 

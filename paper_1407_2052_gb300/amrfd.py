@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libamrfd.so")
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
+MP5, LIMO3 = 0, 1
 DT_PER_DOMAIN, DT_GLOBAL = 0, 1
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
 
@@ -28,7 +29,8 @@ EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_
 class Config(ctypes.Structure):
     _fields_ = [("physics", ctypes.c_int), ("ndim", ctypes.c_int), ("integrator", ctypes.c_int),
                 ("dt_scope", ctypes.c_int), ("gamma", ctypes.c_double), ("cfl", ctypes.c_double),
-                ("glm_cr", ctypes.c_double)]
+                ("glm_cr", ctypes.c_double), ("recon", ctypes.c_int), ("reserved_", ctypes.c_int),
+                ("limo3_r", ctypes.c_double)]
 
 
 class DomainC(ctypes.Structure):
@@ -141,9 +143,9 @@ class Solver:
     """One amrfd handle: a set of domains advanced together on the current GPU."""
 
     def __init__(self, physics, ndim, integrator, gamma, cfl, domains, active=None, glm_cr=0.18,
-                 dt_scope=DT_PER_DOMAIN, stream=None):
+                 dt_scope=DT_PER_DOMAIN, stream=None, recon=MP5, limo3_r=1.0):
         L = load()
-        self.cfg = Config(physics, ndim, integrator, dt_scope, gamma, cfl, glm_cr)
+        self.cfg = Config(physics, ndim, integrator, dt_scope, gamma, cfl, glm_cr, recon, 0, limo3_r)
         self.domains = list(domains)
         self.ndom = len(self.domains)
         self.nv = 2 + ndim if physics == EULER else 9
@@ -166,7 +168,7 @@ class Solver:
     @classmethod
     def from_workload(cls, w, **kw):
         return cls(w.physics, w.ndim, w.integrator, w.gamma, w.cfl, w.domains, active=w.active,
-                   glm_cr=w.glm_cr, **kw)
+                   glm_cr=w.glm_cr, recon=w.recon, limo3_r=w.limo3_r, **kw)
 
     def close(self):
         if getattr(self, "_h", None):

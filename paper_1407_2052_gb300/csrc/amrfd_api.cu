@@ -268,7 +268,7 @@ int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
   h->flux_smem = smem;
   CK(flux_set_smem(h->cfg.physics, h->nv, smem));
   int per_sm = 0;
-  CK(flux_occupancy(h->cfg.physics, h->nv, threads, smem, &per_sm));
+  CK(flux_occupancy(h->cfg.physics, h->nv, h->cfg.recon == AMRFD_LIMO3, threads, smem, &per_sm));
   if (per_sm < 1) return AMRFD_ERR_INVALID_ARG;
   h->flux_grid = per_sm * h->nsm;
   free_graphs(h);
@@ -306,6 +306,8 @@ struct Tick {
 
 FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int stage_in) {
   FluxParams p{};
+  p.limo3 = h->cfg.recon == AMRFD_LIMO3;
+  p.limo3_r = h->cfg.limo3_r;
   p.doms = h->d_dom;
   p.active = h->d_active;
   p.Uk = Uk;
@@ -476,6 +478,8 @@ int validate(const amrfd_config* c, const amrfd_domain* d, int n) {
     return AMRFD_ERR_INVALID_ARG;
   if (c->dt_scope != AMRFD_DT_PER_DOMAIN && c->dt_scope != AMRFD_DT_GLOBAL) return AMRFD_ERR_INVALID_ARG;
   if (!(c->gamma > 1.0) || !(c->cfl > 0.0)) return AMRFD_ERR_INVALID_ARG;
+  if (c->recon != AMRFD_MP5 && c->recon != AMRFD_LIMO3) return AMRFD_ERR_INVALID_ARG;
+  if (c->recon == AMRFD_LIMO3 && !(c->limo3_r > 0.0)) return AMRFD_ERR_INVALID_ARG;
   const int nv = c->physics == AMRFD_EULER ? 2 + c->ndim : 9;
   for (int i = 0; i < n; i++) {
     for (int k = 0; k < 3; k++) {
@@ -762,6 +766,7 @@ int build_adjoint_items(amrfd_handle* h) {
 int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
                   void* stream) {
   if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
+  if (h->cfg.recon != AMRFD_MP5) return AMRFD_ERR_UNSUPPORTED;
   cudaStream_t s = (cudaStream_t)stream;
   {
     int rc = refresh_active_host(h, s);

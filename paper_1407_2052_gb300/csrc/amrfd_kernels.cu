@@ -290,8 +290,58 @@ __device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen,
   (void)Mk3;
 }
 
-template <int PHYS, int NV, int D, bool REC>
+// LIMO3 (Cada & Torrilhon 2009) in product form: with a = delta_{i-1/2} and
+// b = delta_{i+1/2} (G units), the correction b phi(theta) of u_i + b phi / 2 is
+//   unlimited  b phi_3 = (2 b + a) / 3,
+//   limited    b phi^_3 = s max(0, min(y3, max(-a'/2, min(2 a', y3, 1.6 |b|))))
+// evaluated on a' = s a, y3' = s y3, s = sign(b): multiplying the limiter's terms by
+// |b| keeps their order, so no theta = a/b is formed (b = 0 gives 0, the limit). The
+// switch eta = (a^2 + b^2) / (4 (r dx)^2) (G = 2 F^{+-}) picks the unlimited value
+// inside the asymptotic region, the limited one outside, and blends linearly over
+// |eta - 1| < 1e-12.
+__device__ __forceinline__ double limo3_y(double a, double b, double esc) {
+  const double eta = fma(a, a, b * b) * esc;  // >= 0: its bit pattern orders like its value
+  const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
+  const long long lo = dbits(1.0 - 1e-12), hi = dbits(1.0 + 1e-12), be = dbits(eta);
+  if (be <= lo) return y3;
+  const bool neg = dbits(b) < 0;
+  const double ap = neg ? dneg(a) : a;
+  const double y3p = neg ? dneg(y3) : y3;
+  const double bp = neg ? dneg(b) : b;
+  double t = imin(imin(dscale<1>(ap), y3p), 1.6 * bp);
+  t = imax(dscale<-1>(dneg(ap)), t);
+  t = imin(y3p, t);
+  t = imax(0.0, t);
+  const double yl = neg ? dneg(t) : t;
+  if (be >= hi) return yl;
+  const double z = (eta - 1.0) * 1e12;
+  return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
+}
+
+// LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep; G^+ from
+// cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k).
+__device__ __forceinline__ void limo3_sweep(double* g, const double* h, int slen, double esc) {
+  double Pa = g[2] - g[1], Pb = g[3] - g[2];   // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
+  double Mb = h[3] - h[2], Ma = h[4] - h[3];   // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
+  double Fprev = 0.0;
+  const int kend = slen + 3;
+  for (int k = 3; k <= kend; ++k) {
+    const double Yp = limo3_y(Pa, Pb, esc);
+    const double Ym = -limo3_y(Ma, Mb, esc);
+    const double F = fma(0.5, Yp + Ym, g[k - 1] + h[k]);
+    if (k > 3) g[k - 4] = Fprev - F;
+    Fprev = F;
+    if (k < kend) {
+      Pa = Pb; Pb = g[k + 1] - g[k];
+      Mb = Ma; Ma = h[k + 2] - h[k + 1];
+    }
+  }
+}
+
+// MODE 0: MP5; 1: MP5 recording the limiter pieces; 2: LIMO3.
+template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
+  constexpr bool REC = MODE == 1;
   const DomDev dm = load_dom(p.doms + it.dom);
   int o[3];
   block_coords(dm, it.blk, o);
@@ -322,7 +372,12 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
       tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
       tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
     }
-    flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend);
+    if constexpr (MODE == 2) {
+      const double rdx = p.limo3_r * dm.dx[D];
+      limo3_sweep(g, h, slen, 0.25 / (rdx * rdx));
+    } else {
+      flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend);
+    }
   }
   __syncthreads();
   // coalesced write-out of L_D for the segment's interior cells
@@ -348,7 +403,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   __syncthreads();
 }
 
-template <int PHYS, int NV, bool REC>
+template <int PHYS, int NV, int MODE>
 __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
   __shared__ int s_it;
@@ -383,9 +438,9 @@ __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
         all_live &= a;
       }
     }
-    if (live && item.d == 0) flux_item<PHYS, NV, 0, REC>(p, item, sm, all_live);
-    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), REC>(p, item, sm, all_live); }
-    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), REC>(p, item, sm, all_live); }
+    if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live); }
     if (p.counter) {
       if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
       __syncthreads();
@@ -583,30 +638,39 @@ cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, i
 }
 
 cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-#define CALL(PH, NVV)                                                   \
-  if (p.tape) flux_kernel<PH, NVV, true><<<grid, block, smem, s>>>(p); \
-  else flux_kernel<PH, NVV, false><<<grid, block, smem, s>>>(p)
+#define CALL(PH, NVV)                                                     \
+  if (p.tape) flux_kernel<PH, NVV, 1><<<grid, block, smem, s>>>(p);      \
+  else if (p.limo3) flux_kernel<PH, NVV, 2><<<grid, block, smem, s>>>(p); \
+  else flux_kernel<PH, NVV, 0><<<grid, block, smem, s>>>(p)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaGetLastError();
 }
 
 cudaError_t flux_set_smem(int physics, int nv, size_t smem) {
-#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+#define CALL(PH, NVV)                                                                                     \
+  do {                                                                                                     \
+    cudaError_t e = cudaFuncSetAttribute(flux_kernel<PH, NVV, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                       \
+    if (e != cudaSuccess) return e;                                                                        \
+    return cudaFuncSetAttribute(flux_kernel<PH, NVV, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  } while (0)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;
 }
 
 cudaError_t flux_rec_set_smem(int physics, int nv, size_t smem) {
-#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;
 }
 
-cudaError_t flux_occupancy(int physics, int nv, int block, size_t smem, int* per_sm) {
-#define CALL(PH, NVV) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV, false>, block, smem)
+cudaError_t flux_occupancy(int physics, int nv, int limo3, int block, size_t smem, int* per_sm) {
+#define CALL(PH, NVV)                                                                                        \
+  return limo3 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV, 2>, block, smem) \
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, flux_kernel<PH, NVV, 0>, block, smem)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;

@@ -45,6 +45,8 @@ struct FluxParams {
   int SS;                       // smem stride of one line (>= max segment + 6, odd)
   int glm;
   unsigned short* tape;         // limiter pieces of every face (recording pass) or nullptr
+  int limo3;                    // reconstruction: 0 MP5, 1 LIMO3
+  double limo3_r;               // LIMO3 radius of the asymptotic region
 };
 
 // One stage combination, optionally with the speeds of the new state.
@@ -177,6 +179,6 @@ cudaError_t launch_combine(int physics, int nv, const CombParams& p, int grid, i
 cudaError_t launch_dt(const DtParams& p, cudaStream_t s);
 cudaError_t launch_compact(const CompactParams& p, cudaStream_t s);
 cudaError_t flux_set_smem(int physics, int nv, size_t smem);
-cudaError_t flux_occupancy(int physics, int nv, int block, size_t smem, int* per_sm);
+cudaError_t flux_occupancy(int physics, int nv, int limo3, int block, size_t smem, int* per_sm);
 
 }  // namespace amrfd

@@ -50,6 +50,8 @@ class Workload:
     active: Optional[np.ndarray] = None  # uint8 per block (all blocks of all domains, in order)
     glm_cr: float = 0.18
     t_end: float = 0.0
+    recon: int = 0                    # 0 MP5, 1 LIMO3
+    limo3_r: float = 1.0
     nsteps: int = 0
     extra: dict = field(default_factory=dict)
 

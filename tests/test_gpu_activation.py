@@ -112,7 +112,9 @@ def test_dynamic_activation_run_vs_oracle_and_full_update(batched):
         act = O.activate(d, O.flag_steady(c, d, U, w.U, tol), belt)
         assert np.array_equal(acts[k], act), k
         h, _ = O.dt(c, d, U, w.cfl, active=act)
-        assert dts[k] == h if k == 0 else abs(dts[k] - h) <= 1e-13 * h, k
+        # dt of U^0 bitwise; later states differ by rounding, most at the strong blast
+        # front where the largest speed sits
+        assert dts[k] == h if k == 0 else abs(dts[k] - h) <= 1e-11 * h, (k, dts[k], h)
         U, fl, _, ch = O.step(c, d, U, h, active=act)
         assert fl == 0
     assert 0 < acts[0].sum() < acts[0].size          # the blast starts with a passive rim

@@ -65,7 +65,7 @@ def rel_l1(a, b, ch=0.0):
 
 
 def ocfg(w):
-    return O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    return O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr, recon=w.recon, limo3_r=w.limo3_r)
 
 
 def odom(d):
@@ -500,3 +500,92 @@ def test_mirror_faces_tile_invariance():
         if base is None:
             base = out
         assert torch.equal(out, base), tile
+
+
+# --------------------------------------------------------------- LIMO3 reconstruction
+def _limo(w, integrator=O.SSPRK3, r=1.0):
+    w.recon, w.limo3_r, w.integrator = O.LIMO3, r, integrator
+    return w
+
+
+@pytest.mark.parametrize("r", [1.0, 0.05])
+def test_limo3_vortex_one_step(r):
+    """2D MHD vortex at 64^2 with RK3 + LIMO3 (both sides of the asymptotic switch):
+    one step, dt bitwise, relative L-inf <= 1e-12."""
+    w = _limo(W.vortex2d(64), r=r)
+    s, U, dts = run_gpu(w, 1)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+def test_limo3_sod_and_blast_shocked():
+    w = _limo(W.sod(512))
+    c, d = ocfg(w), odom(w.domains[0])
+    Uo, t, n, fl = O.evolve(c, d, w.U, w.cfl, w.t_end)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        s.step_batched(U, dt)
+        tg += float(dt[0].item())
+        ng += 1
+    assert s.error() == A().OK and ng == n
+    assert rel_l1(host(U, Uo.shape), Uo) <= 1e-10
+    w = _limo(W.blast3d(32, 8))
+    s, U, dts = run_gpu(w, 5, batched=False)
+    ref, odts = run_oracle(w, 5)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_l1(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-10
+
+
+@pytest.mark.parametrize("case", range(len(RAGGED)))
+def test_limo3_ragged_boxes(case):
+    physics, ndim, n, bc = RAGGED[case]
+    w = _limo(_smooth_domain(physics, ndim, n, bc, seed=50 + case), integrator=O.SSPRK43)
+    s, U, dts = run_gpu(w, 1)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+def test_limo3_brio_wu_ssprk43_at_cfl_2():
+    """SSPRK(4,3)-LIMO3 Brio-Wu at its SSP limit CFL 2.0 (Sec. 4.5.2): same step count as
+    the oracle; the result within ten times the oracle's own sensitivity to a 1e-15
+    perturbation of its input (and at least 1e-10)."""
+    w = _limo(W.brio_wu(512), integrator=O.SSPRK43)
+    c, d = ocfg(w), odom(w.domains[0])
+    Uo, t, n, fl = O.evolve(c, d, w.U, 2.0, w.t_end)
+    Up, _, n2, _ = O.evolve(c, d, w.U * (1 + 1e-15), 2.0, w.t_end)
+    assert fl == 0 and n2 == n
+    tol = 10 * rel_l1(Up, Uo, 1.0) + 1e-10
+    s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, 2.0, w.domains, glm_cr=w.glm_cr, recon=O.LIMO3)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        s.step_batched(U, dt)
+        tg += float(dt[0].item())
+        ng += 1
+    assert s.error() == A().OK and ng == n
+    assert rel_l1(host(U, Uo.shape), Uo, 1.0) <= tol
+
+
+def test_limo3_tiles_and_adjoint_unsupported():
+    w = _limo(_smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((2, 2), (0, 0), (1, 1)), seed=61, nb=(5, 3, 2)))
+    w.domains[0].asym = ((0x1A2, 0x1A2), (0, 0), (0, 0))
+    base = None
+    for tile in [(16, 8, 128), (32, 16, 160), (64, 4, 64)]:
+        s = A().Solver.from_workload(w)
+        s.set_tile(*tile)
+        _, U, _ = run_gpu(w, 2, solver=s)
+        out = U.cpu()
+        if base is None:
+            base = out
+        assert torch.equal(out, base), tile
+    g = torch.zeros_like(U)
+    dt = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
+    with pytest.raises(A().AmrfdError) as e:
+        s.adjoint(U, dt, g, torch.empty_like(U))
+    assert e.value.code == A().ERR_UNSUPPORTED

@@ -35,7 +35,8 @@ def _odom(d):
 
 
 def _ocfg(w, integrator=None):
-    return O.cfg(w.physics, w.ndim, w.integrator if integrator is None else integrator, w.gamma, w.glm_cr)
+    return O.cfg(w.physics, w.ndim, w.integrator if integrator is None else integrator, w.gamma, w.glm_cr,
+                 recon=w.recon, limo3_r=w.limo3_r)
 
 
 # ------------------------------------------------------------ point-wise pieces
@@ -594,3 +595,87 @@ def test_flag_steady_blockwise():
     U[8, 12, 12, 12] = np.nan     # block 7
     assert O.flag_steady(c, d, U, R, 1e-10).tolist() == [1, 1, 0, 1, 1, 1, 1, 0]
     assert O.flag_steady(c, d, U, R, 1e-8).tolist() == [1, 1, 1, 1, 1, 1, 1, 0]
+
+
+# ---------------------------------------------------------------- LIMO3 (Sec. 2.2, 4.5)
+def test_limo3_unlimited_is_exact_for_quadratic_cell_averages():
+    """Inside the asymptotic region (eta < 1) LIMO3 is the unlimited third-order
+    reconstruction: exact face values from cell averages of any quadratic."""
+    rng = np.random.default_rng(5)
+    h = 0.1
+    for _ in range(50):
+        a, b, c = rng.standard_normal(3)
+
+        def avg(x0):  # average of a + b x + c x^2 over [x0, x0 + h]
+            F = lambda x: a * x + b * x * x / 2 + c * x ** 3 / 3  # noqa: E731
+            return (F(x0 + h) - F(x0)) / h
+        x0 = rng.uniform(-1, 1)
+        um, u0, up = avg(x0 - h), avg(x0), avg(x0 + h)
+        face = a + b * (x0 + h) + c * (x0 + h) ** 2
+        got = O.limo3(um, u0, up, 1e6)
+        assert abs(got - face) <= 1e-12 * max(1.0, abs(face))
+        # the right-biased value at the same face from the cells on its right
+        face_l = a + b * x0 + c * x0 * x0
+        assert abs(O.limo3(up, u0, um, 1e6) - face_l) <= 1e-12 * max(1.0, abs(face_l))
+
+
+def test_limo3_limited_properties():
+    """Outside the asymptotic region (eta > 1) the limited function: values of monotone
+    data stay between u_i and u_{i+1}; smooth profiles (theta in [0.4, 2.8], and smooth
+    extrema with theta in [-2, -0.8]) keep the third-order value; steps and sharp
+    extrema (theta <= -2) give u_i; a flat right neighbour gives u_i; the slope is
+    capped at 1.6 delta_+ / 2 for steep left data; odd and translation symmetric."""
+    rng = np.random.default_rng(6)
+    tiny = 1e-9  # r dx: eta >> 1
+    for _ in range(200):
+        u0 = rng.standard_normal()
+        dp = rng.uniform(0.1, 2.0) * rng.choice([-1, 1])
+        th = rng.uniform(-4, 6)
+        um, up = u0 - th * dp, u0 + dp
+        v = O.limo3(um, u0, up, tiny)
+        full = O.limo3(um, u0, up, 1e9)
+        if th >= 0:
+            assert min(u0, up) - 1e-15 <= v <= max(u0, up) + 1e-15
+        if 0.4 <= th <= 2.8 or -2 <= th <= -0.8:
+            assert abs(v - full) <= 1e-13
+        if th <= -2:
+            assert v == u0
+        if th >= 3.0:
+            assert abs(v - (u0 + 0.8 * dp)) <= 1e-13
+        assert abs(O.limo3(-um, -u0, -up, tiny) + v) <= 1e-15
+        assert abs(O.limo3(um + 3.0, u0 + 3.0, up + 3.0, tiny) - (v + 3.0)) <= 1e-13
+    assert O.limo3(0.0, 0.0, 1.0, tiny) == 0.0      # theta = 0: first-order at the step
+    assert O.limo3(0.0, 1.0, 1.0, tiny) == 1.0      # delta_+ = 0
+
+
+def test_limo3_rk3_third_order():
+    """RK3 + LIMO3 on smooth periodic advection converges at third order (Sec. 4.5.1
+    reports third order for this pairing on the Alfven wave)."""
+    errs = []
+    for n in (32, 64, 128):
+        w = W.sine_advection(n)
+        c = O.cfg(w.physics, w.ndim, O.SSPRK3, w.gamma, recon=O.LIMO3, limo3_r=1.0)
+        U, t, _, fl = O.evolve(c, _odom(w.domains[0]), w.U, 0.4, 1.0)
+        assert fl == 0
+        errs.append(np.mean(np.abs(U[0] - w.U[0])))
+    orders = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(2.8 < o < 3.3 for o in orders), (errs, orders)
+
+
+def test_brio_wu_limo3_contact_and_max_ssp_cfl():
+    """Sec. 4.5.2: RK3-LIM03-FD barely moves the contact density (-0.001% in the paper;
+    this reading: a small undershoot, within -1% .. +0.5% of the 1024-cell MP5 plateau),
+    and SSPRK(4,3)-LIMO3 runs the tube at its SSP limit, CFL 2.0, staying physical."""
+    def run(n, integ, recon, cfl):
+        w = W.brio_wu(n)
+        c = O.cfg(w.physics, w.ndim, integ, w.gamma, w.glm_cr, recon=recon, limo3_r=1.0)
+        U, _, ns, fl = O.evolve(c, _odom(w.domains[0]), w.U, cfl, w.t_end)
+        assert fl == 0
+        return w.extra["x"], U, ns
+    xr, Ur, _ = run(1024, O.SSPRK54, O.MP5, 0.4)
+    plateau = Ur[0, 0, 0][(xr > 0.0) & (xr < 0.09)].mean()
+    x, U, _ = run(512, O.SSPRK3, O.LIMO3, 0.4)
+    over = U[0, 0, 0][(x > 0.05) & (x < 0.14)].max() / plateau - 1.0
+    assert -0.01 <= over <= 0.005, over
+    x, U, ns = run(512, O.SSPRK43, O.LIMO3, 2.0)
+    assert ns < 110 and U[0].min() > 0.1 and U[0].max() < 1.01
