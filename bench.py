@@ -182,6 +182,77 @@ def adjoint_extra(torch, A, W, reps=3):
             "ratio": adj / fwd}
 
 
+def _time_steps(torch, fn, steps):
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def schemes_extra(torch, A, W, tile, steps=2):
+    """Cost of one step of the blast (256^3 in 16^3 blocks) under the paper's scheme
+    pairings (Sec. 4.5.2 times SSPRK(5,4)-MP5 against RK3-LIMO3 at 2.2 : 1)."""
+    w = W.blast3d(256, 16)
+    U0 = torch.from_numpy(w.U.ravel()).cuda()
+    out = {"workload": "blast3d 256^3 in 16^3 blocks, MHD+GLM, dt from CFL 0.3 of U^0"}
+    for name, integ, recon in (("ssprk54_mp5", A.SSPRK54, A.MP5), ("ssprk3_mp5", A.SSPRK3, A.MP5),
+                               ("rk3_limo3", A.SSPRK3, A.LIMO3)):
+        s = A.Solver(w.physics, w.ndim, integ, w.gamma, w.cfl, w.domains, active=w.active, glm_cr=w.glm_cr,
+                     recon=recon)
+        s.set_tile(*tile)
+        U = U0.clone()
+        dt = s.dt(U)
+        ms = _time_steps(torch, lambda: s.step_batched(U, dt), steps)
+        assert s.error() == A.OK
+        out[name] = {"ms_per_step": ms, "cell_updates_per_s": w.domains[0].ncell / (ms * 1e-3)}
+        s.close()
+        del U
+    out["ratio_ssprk54_mp5_to_rk3_limo3"] = out["ssprk54_mp5"]["ms_per_step"] / out["rk3_limo3"]["ms_per_step"]
+    del U0
+    torch.cuda.empty_cache()
+    return out
+
+
+def activation_extra(torch, A, W, tile, steps=3):
+    """Dynamic grid activation (App. C) on the quiet blast (uniform background), 256^3 in
+    16^3 blocks: criterion |U - U_background| <= 1e-12, a two-block belt and the device
+    work-list rebuild before every step, against all blocks active. Early in the run most
+    of the box is still at rest, so most blocks are passive."""
+    w = W.blast3d(256, 16, noise=0.0)
+    U0 = torch.from_numpy(w.U.ravel()).cuda()
+    R = torch.from_numpy(w.extra["background"].ravel()).cuda()
+    ncell = w.domains[0].ncell
+    out = {"workload": "quiet blast3d 256^3 in 16^3 blocks, MHD+GLM SSPRK3, belt 2, first steps"}
+    for mode in ("all_active", "dynamic"):
+        s = A.Solver.from_workload(w)
+        s.set_tile(*tile)
+        U = U0.clone()
+        dt = torch.empty(1, dtype=torch.float64, device="cuda")
+        flag = torch.empty(s.nblocks, dtype=torch.uint8, device="cuda")
+
+        def one():
+            if mode == "dynamic":
+                s.activate(s.flag_steady(U, R, 1e-12, out=flag), 2)
+            s.dt(U, out=dt)
+            s.step_batched(U, dt)
+        ms = _time_steps(torch, one, steps)
+        assert s.error() == A.OK
+        frac = float(s.active().float().mean().item())
+        out[mode] = {"ms_per_step": ms, "active_block_fraction": frac,
+                     "domain_cells_per_s": ncell / (ms * 1e-3)}
+        s.close()
+        del U
+    out["speedup"] = out["all_active"]["ms_per_step"] / out["dynamic"]["ms_per_step"]
+    del U0, R
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -362,12 +433,15 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": nbytes},
         "clocks": clocks,
     }
+    tile = list(s.get_tile())
     s.close()
     del U, U0
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
         out["batched"] = batched_extra(torch, A, W)
         out["adjoint"] = adjoint_extra(torch, A, W)
+        out["schemes"] = schemes_extra(torch, A, W, tile)
+        out["activation"] = activation_extra(torch, A, W, tile)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     if dist is not None:

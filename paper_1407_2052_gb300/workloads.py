@@ -154,8 +154,12 @@ def blast3d(n=256, block=16, seed_index=2, noise=1e-3):
     U = conserved_mhd(rho, [zero, zero, zero], p, [zero + b, zero + b, zero], 5.0 / 3.0)
     nb = n // block
     dom = Domain((n, n, n), (dx, dx, dx), nb=(nb, nb, nb))
+    extra = {}
+    if noise == 0.0:  # the stationary background the blast runs into
+        extra["background"] = conserved_mhd(zero + 1.0, [zero, zero, zero], zero + 0.1, [zero + b, zero + b, zero],
+                                            5.0 / 3.0)
     return Workload("blast3d", MHD_GLM, 3, SSPRK3, 5.0 / 3.0, 0.3, [dom], U, nsteps=200,
-                    active=np.ones(nb ** 3, np.uint8))
+                    active=np.ones(nb ** 3, np.uint8), extra=extra)
 
 
 def _kset3():
