@@ -200,7 +200,7 @@ void amrfd_destroy(amrfd_handle *h);
    a deployment variant of amrfd_dt. Inputs as for amrfd_create plus amrfd_dt:
    `domains[ndomain]` (host), optional per-block `active_dev` (device, NULL = all
    active), state `U` and output `dt_dev[ndomain]` (device). Scratch is a fixed
-   ~143 KB __device__ array inside the library, held by every GPU that loads it
+   ~190 KB __device__ array inside the library, held by every GPU that loads it
    until the process exits; ndomain is limited to 1024 (AMRFD_ERR_INVALID_ARG,
    with a message on stderr, beyond). The first call on a device looks up the
    array's device address and should come before any stream capture. All calls

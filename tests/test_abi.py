@@ -43,7 +43,8 @@ def test_strerror(lib):
     assert b"non-physical" in lib.amrfd_strerror(4)
 
 
-@pytest.mark.parametrize("bad", ["physics", "ndim", "gamma", "periodic_small", "overlap", "nb", "unpaired_bc"])
+@pytest.mark.parametrize("bad", ["physics", "ndim", "gamma", "periodic_small", "overlap", "nb", "unpaired_bc",
+                                 "bc_kind", "mirror_small", "mirror_mask", "recon", "limo3_r"])
 def test_create_rejects_bad_arguments_on_host(lib, bad):
     """Validation happens before any CUDA call, so this needs no GPU."""
     from paper_1407_2052_gb300 import amrfd as A
@@ -64,6 +65,17 @@ def test_create_rejects_bad_arguments_on_host(lib, bad):
         doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, nb=(3, 1, 1))
     elif bad == "unpaired_bc":
         doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, bc=((A.PERIODIC, A.OUTFLOW),) * 3)
+    elif bad == "bc_kind":
+        doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, bc=((A.OUTFLOW, 3),) * 3)
+    elif bad == "mirror_small":
+        doms[0] = W.Domain((8, 2, 8), (0.1,) * 3, bc=((0, 0), (A.SYMMETRIC, A.OUTFLOW), (0, 0)))
+    elif bad == "mirror_mask":  # MHD has 9 variables: bit 9 does not exist
+        doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, bc=((A.SYMMETRIC, A.SYMMETRIC), (0, 0), (0, 0)),
+                           asym=((1 << 9, 0), (0, 0), (0, 0)))
+    elif bad == "recon":
+        cfg.recon = 2
+    elif bad == "limo3_r":
+        cfg.recon, cfg.limo3_r = A.LIMO3, 0.0
     h = ctypes.c_void_p()
     rc = lib.amrfd_create(ctypes.byref(h), ctypes.byref(cfg), A.domains_c(doms), len(doms), None, None)
     assert rc == A.ERR_INVALID_ARG

@@ -228,3 +228,50 @@ def test_adjoint_passive_blocks_pass_through():
         (o * torch.from_numpy(gg[sl].reshape(shape))).sum().backward()
         want = Ut.grad.numpy().ravel()
         assert np.abs(got[sl] - want).max() / np.abs(want).max() <= 1e-10, i
+
+
+def test_adjoint_matches_autograd_at_128():
+    """The torch-reference comparison at 128^2 (MHD+GLM, SSPRK3, dt 1e-3)."""
+    w = W.adjoint2d(128)
+    g = np.random.default_rng(17).standard_normal(w.U.shape)
+    got, _ = _gpu_adjoint(w, 1e-3, g)
+    want, _, _ = _ref_grad(w, 1e-3, g)
+    assert np.abs(got - want).max() / np.abs(want).max() <= 1e-10
+
+
+def test_rollout_gradient_against_oracle_central_differences():
+    """dJ/dU^0 of J = sum |B|^2/2 dx dy after 10 steps (checkpoints every 4) at 128^2,
+    against central differences (h = 1e-6) of the oracle's frozen-speed steps along five
+    random unit directions, each step with the speeds of the oracle's own trajectory."""
+    from paper_1407_2052_gb300 import autodiff
+    A = _A()
+    w = W.adjoint2d(128)
+    dtv, nsteps = 1e-3, 10
+    area = w.domains[0].dx[0] * w.domains[0].dx[1]
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel().copy()).cuda().requires_grad_(True)
+    dt = torch.full((1,), dtv, dtype=torch.float64, device="cuda")
+    Uf = autodiff.rollout(s, U0, dt, nsteps, 4)
+    B = Uf.view(9, -1)[5:8]
+    (0.5 * (B * B).sum() * area).backward()
+    grad = U0.grad.cpu().numpy().reshape(w.U.shape)
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    d = _odom(w.domains[0])
+    frozen, U = [], w.U.copy()
+    for _ in range(nsteps):
+        U, fl, al, ch = O.step(c, d, U, dtv)
+        assert fl == 0
+        frozen.append((al, ch))
+
+    def J(U):
+        for al, ch in frozen:
+            U, _ = O.step_frozen(c, d, U, dtv, al, ch)
+        return 0.5 * float(np.sum(U[5:8] ** 2)) * area
+    rng = np.random.default_rng(23)
+    h = 1e-6
+    for _ in range(5):
+        v = rng.standard_normal(w.U.shape)
+        v /= np.linalg.norm(v)
+        fd = (J(w.U + h * v) - J(w.U - h * v)) / (2 * h)
+        ad = float(np.sum(grad * v))
+        assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
