@@ -263,15 +263,17 @@ def test_rollout_gradient_against_oracle_central_differences():
         assert fl == 0
         frozen.append((al, ch))
 
-    def J(U):
+    def final(U):
         for al, ch in frozen:
             U, _ = O.step_frozen(c, d, U, dtv, al, ch)
-        return 0.5 * float(np.sum(U[5:8] ** 2)) * area
+        return U
     rng = np.random.default_rng(23)
     h = 1e-6
     for _ in range(5):
         v = rng.standard_normal(w.U.shape)
         v /= np.linalg.norm(v)
-        fd = (J(w.U + h * v) - J(w.U - h * v)) / (2 * h)
+        Bp, Bm = final(w.U + h * v)[5:8], final(w.U - h * v)[5:8]
+        # J(+) - J(-) as sum (B+ - B-)(B+ + B-)/2: no cancellation between two large totals
+        fd = 0.5 * float(np.sum((Bp - Bm) * (Bp + Bm))) * area / (2 * h)
         ad = float(np.sum(grad * v))
         assert abs(fd - ad) <= 1e-6 * abs(fd), (fd, ad)
