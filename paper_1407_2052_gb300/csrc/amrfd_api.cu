@@ -98,6 +98,8 @@ struct amrfd_handle {
   int* d_counters = nullptr;        // one per persistent launch
   double* d_stage[kMaxStages] = {};
   double* d_L[3] = {};
+  double* d_W = nullptr;            // derived quantities (velocity, pressure terms) of the flux input
+  size_t nw_elem = 0;
   unsigned long long* d_slot = nullptr;  // [kNumSlots][ndom][4]
   unsigned* d_tlow = nullptr;            // [kNumSlots][ndom][4] FP32 lower bounds of the speeds
   unsigned* d_err = nullptr;
@@ -326,6 +328,7 @@ FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int 
   if (SS % 2 == 0) SS++;
   p.SS = SS;
   p.glm = h->cfg.physics == AMRFD_MHD_GLM;
+  p.W = h->d_W;
   return p;
 }
 
@@ -347,6 +350,8 @@ CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
   p.glm_cr = h->cfg.glm_cr;
   p.ndim = h->cfg.ndim;
   p.final_stage = (i == h->ns);
+  p.W = (i < h->ns) ? h->d_W : nullptr;  // the next flux pass reads them
+  p.gm1 = h->cfg.gamma - 1.0;
   return p;
 }
 
@@ -361,6 +366,7 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   p.gamma = h->cfg.gamma;
   p.ndim = h->cfg.ndim;
   p.want_rate = want_rate;
+  p.gm1 = h->cfg.gamma - 1.0;
   return p;
 }
 
@@ -410,9 +416,11 @@ int speeds_from_scratch(amrfd_handle* h, const double* U, int k, int want_rate, 
   CK(cudaMemsetAsync(tlow(h, k), 0, sizeof(unsigned) * h->ndom * 4, s));
   SpeedParams p = speed_params(h, U, k, want_rate);
   p.exact = 0;
+  p.W = k == 0 ? h->d_W : nullptr;  // U^n of a step: the first flux pass reads them
   int rc = launch_speeds_over(h, p, batched, live, s);
   if (rc) return rc;
   p.exact = 1;
+  p.W = nullptr;
   return launch_speeds_over(h, p, batched, live, s);
 }
 
@@ -555,6 +563,8 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
     dm.block0 = nb;
     dm.ncell = dm.n[0] * dm.n[1] * dm.n[2];
     dm.off = domains[i].offset;
+    dm.woff = (long long)h->nw_elem;
+    h->nw_elem += (size_t)(cfg->physics == AMRFD_EULER ? 1 + cfg->ndim : 5) * dm.ncell;
     h->nelem = std::max(h->nelem, (size_t)(dm.off + (long long)h->nv * dm.ncell));
     nb += dm.nb[0] * dm.nb[1] * dm.nb[2];
     for (int k = 0; k < 3; k++) {
@@ -594,6 +604,7 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
   CKH(cudaMemset(h->d_err, 0, sizeof(unsigned)));
   for (int k = 1; k < h->ns; k++) CKH(cudaMalloc(&h->d_stage[k], sizeof(double) * h->nelem));
   for (int d = 0; d < cfg->ndim; d++) CKH(cudaMalloc(&h->d_L[d], sizeof(double) * h->nelem));
+  CKH(cudaMalloc(&h->d_W, sizeof(double) * std::max<size_t>(1, h->nw_elem)));
   CKH(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   const int lines = cfg->ndim == 1 ? 1 : 32;
   rc = configure_tile(h, 32, lines, default_threads(h->nv, lines));
@@ -1025,6 +1036,7 @@ void amrfd_destroy(amrfd_handle* h) {
   cudaFree(h->d_tape);
   cudaFree(h->d_adj_items);
   for (int d = 0; d < 3; d++) cudaFree(h->d_L[d]);
+  cudaFree(h->d_W);
   cudaFree(h->d_slot); cudaFree(h->d_tlow); cudaFree(h->d_err);
   if (h->cap) cudaStreamDestroy(h->cap);
   for (auto e : h->tev) cudaEventDestroy(e);

@@ -476,43 +476,56 @@ __device__ __forceinline__ void speed_bounds(const double* u, float gam, int ndi
 // G^{+-} = F_d +- alpha_d U = 2 F^{+-}: the factor 1/2 of the splitting is
 // applied once to the final flux difference (MP5 commutes with scaling by 2
 // when its acceptance threshold is scaled by 4).
-template <int PHYS, int NV, int D>
-__device__ __forceinline__ void split_flux(const double* u, double gm1, double alpha, double ch2,
-                                           double* gp, double* gm) {
-  double f[NV];
-  const double rho = u[0];
-  const double ir = frcp(rho);
+// Number of per-cell derived quantities the flux needs besides U: MHD v_x, v_y, v_z,
+// p_tot = p + B^2/2, v.B; Euler v_1..v_ndim, p.
+template <int PHYS, int NV>
+struct NumW { static constexpr int value = PHYS == PH_EULER ? NV - 1 : 5; };
+
+// The derived quantities of one cell (the FP64 part of cons -> prim the flux needs).
+template <int PHYS, int NV>
+__device__ __forceinline__ void prim_w(const double* u, double gm1, double* w) {
+  const double ir = frcp(u[0]);
   if (PHYS == PH_EULER) {
     constexpr int nm = NV - 2;
-    double v[nm];
     double mv = 0.0;
 #pragma unroll
-    for (int k = 0; k < nm; k++) { v[k] = u[1 + k] * ir; mv = fma(u[1 + k], v[k], mv); }
-    const double E = u[NV - 1];
-    const double p = gm1 * fma(-0.5, mv, E);
-    const double vd = v[D];
+    for (int k = 0; k < nm; k++) { w[k] = u[1 + k] * ir; mv = fma(u[1 + k], w[k], mv); }
+    w[nm] = gm1 * fma(-0.5, mv, u[NV - 1]);
+  } else {
+    const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
+    const double b2 = fma(u[7], u[7], fma(u[6], u[6], u[5] * u[5]));
+    const double mv = fma(u[3], v[2], fma(u[2], v[1], u[1] * v[0]));
+    const double p = gm1 * fma(-0.5, mv + b2, u[4]);
+    w[0] = v[0]; w[1] = v[1]; w[2] = v[2];
+    w[3] = fma(0.5, b2, p);
+    w[4] = fma(v[2], u[7], fma(v[1], u[6], v[0] * u[5]));
+  }
+}
+
+// Physical flux along D from U and its derived quantities, then the Lax-Friedrichs
+// split in doubled form G^{+-} = F +- alpha U (= 2 F^{+-}); psi's flux is c_h^2 B_D.
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void split_flux_w(const double* u, const double* w, double alpha, double ch2,
+                                             double* gp, double* gm) {
+  double f[NV];
+  if (PHYS == PH_EULER) {
+    constexpr int nm = NV - 2;
+    const double p = w[nm], vd = w[D];
     f[0] = u[1 + D];
 #pragma unroll
     for (int k = 0; k < nm; k++) f[1 + k] = (k == D) ? fma(vd, u[1 + k], p) : vd * u[1 + k];
-    f[NV - 1] = vd * (E + p);
+    f[NV - 1] = vd * (u[NV - 1] + p);
   } else {
-    const double E = u[4], psi = u[8];
-    const double B[3] = {u[5], u[6], u[7]};
-    const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
-    const double b2 = fma(B[2], B[2], fma(B[1], B[1], B[0] * B[0]));
-    const double mv = fma(u[3], v[2], fma(u[2], v[1], u[1] * v[0]));
-    const double p = gm1 * fma(-0.5, mv + b2, E);
-    const double ptot = fma(0.5, b2, p);
-    const double vb = fma(v[2], B[2], fma(v[1], B[1], v[0] * B[0]));
-    const double vd = v[D], bd = B[D];
+    const double ptot = w[3], vb = w[4];
+    const double vd = w[D], bd = u[5 + D];
     f[0] = u[1 + D];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      f[1 + k] = fma(vd, u[1 + k], -bd * B[k]);
+      f[1 + k] = fma(vd, u[1 + k], -bd * u[5 + k]);
       if (k == D) f[1 + k] += ptot;
-      f[5 + k] = (k == D) ? psi : fma(vd, B[k], -bd * v[k]);
+      f[5 + k] = (k == D) ? u[8] : fma(vd, u[5 + k], -bd * w[k]);
     }
-    f[4] = fma(vd, E + ptot, -bd * vb);
+    f[4] = fma(vd, u[4] + ptot, -bd * vb);
     f[8] = ch2 * bd;
   }
 #pragma unroll
@@ -520,6 +533,14 @@ __device__ __forceinline__ void split_flux(const double* u, double gm1, double a
     gp[v] = fma(alpha, u[v], f[v]);
     gm[v] = fma(-alpha, u[v], f[v]);
   }
+}
+
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void split_flux(const double* u, double gm1, double alpha, double ch2,
+                                           double* gp, double* gm) {
+  double w[NumW<PHYS, NV>::value];
+  prim_w<PHYS, NV>(u, gm1, w);
+  split_flux_w<PHYS, NV, D>(u, w, alpha, ch2, gp, gm);
 }
 
 // ------------------------------------------------------------- block reductions

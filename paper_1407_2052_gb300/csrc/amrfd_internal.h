@@ -20,6 +20,7 @@ struct DomDev {
   int block0;        // global index of the first block of this domain
   int ncell;         // n0*n1*n2
   long long off;     // element offset in every state-shaped buffer
+  long long woff;    // element offset in the derived-quantity buffer (NumW values per cell)
   double dx[3];
   long long tape_off[3];  // offset (records) of this domain's limiter tape, per direction
 };

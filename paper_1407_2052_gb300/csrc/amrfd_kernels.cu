@@ -134,6 +134,14 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
       double u[NV];
 #pragma unroll
       for (int v = 0; v < NV; v++) u[v] = p.U[idx + (long long)v * dm.ncell];
+      if (p.W) {
+        constexpr int NW = NumW<PHYS, NV>::value;
+        double w[NW];
+        prim_w<PHYS, NV>(u, p.gm1, w);
+        const long long wi = dm.woff + (idx - dm.off);
+#pragma unroll
+        for (int q = 0; q < NW; q++) p.W[wi + (long long)q * dm.ncell] = w[q];
+      }
       float up[4], lo[4];
       bool force;
       speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, want_rate, up, lo, force);
@@ -204,10 +212,12 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
     }
     x[D] = g;
     const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
-    const double* base = p.active[nbk] ? p.Uk : p.Un;
+    const bool act = p.active[nbk] != 0;
+    const double* base = act ? p.Uk : p.Un;
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
     const double* src = base + dm.off + idx;
-    double u[NV], gp[NV], gmn[NV];
+    constexpr int NW = NumW<PHYS, NV>::value;
+    double u[NV], w[NW], gp[NV], gmn[NV];
 #pragma unroll
     for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
     if (odd) {
@@ -215,7 +225,16 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
       for (int v = 0; v < NV; v++)
         if ((odd >> v) & 1u) u[v] = -u[v];
     }
-    split_flux<PHYS, NV, D>(u, gm1, alpha, ch2, gp, gmn);
+    // derived quantities: stored by the pass that produced U^(k) for active cells;
+    // recomputed for passive neighbours (U^n) and mirror images
+    if (p.W && act && !odd) {
+      const double* ws = p.W + dm.woff + idx;
+#pragma unroll
+      for (int q = 0; q < NW; q++) w[q] = ws[(long long)q * dm.ncell];
+    } else {
+      prim_w<PHYS, NV>(u, gm1, w);
+    }
+    split_flux_w<PHYS, NV, D>(u, w, alpha, ch2, gp, gmn);
 #pragma unroll
     for (int v = 0; v < NV; v++) {
       sm[((0 * NV + v) * P + pl) * SS + j] = gp[v];
@@ -499,6 +518,14 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
         if (PHYS == PH_MHD && v == 8) acc *= fac;
         u[v] = acc;
         p.out[e] = acc;
+      }
+      if (p.W) {
+        constexpr int NW = NumW<PHYS, NV>::value;
+        double w[NW];
+        prim_w<PHYS, NV>(u, p.gm1, w);
+        const long long wi = dm.woff + (idx - dm.off);
+#pragma unroll
+        for (int q = 0; q < NW; q++) p.W[wi + (long long)q * dm.ncell] = w[q];
       }
       if (p.tlow_out) {
         float up[4], lo[4];

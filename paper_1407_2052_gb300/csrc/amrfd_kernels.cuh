@@ -23,6 +23,8 @@ struct SpeedParams {
   int ndim;
   int want_rate;
   int exact;                    // 0: publish lower bounds only; 1: exact maxima of the candidates
+  double* W;                    // bounds pass: also write the derived quantities of U (or nullptr)
+  double gm1;
 };
 
 // One flux pass: L_d(U^(k)) for the items' lines.
@@ -47,6 +49,7 @@ struct FluxParams {
   unsigned short* tape;         // limiter pieces of every face (recording pass) or nullptr
   int limo3;                    // reconstruction: 0 MP5, 1 LIMO3
   double limo3_r;               // LIMO3 radius of the asymptotic region
+  const double* W;              // derived quantities of Uk in active blocks (nullptr: compute)
 };
 
 // One stage combination, optionally with the speeds of the new state.
@@ -70,6 +73,8 @@ struct CombParams {
   double glm_cr;
   int ndim;
   int final_stage;
+  double* W;                    // derived quantities of the output state (or nullptr)
+  double gm1;
 };
 
 struct DtParams {
