@@ -103,7 +103,6 @@ __device__ __forceinline__ bool exact_speeds(const double* u, double gamma, int 
 // re-evaluates the bounds and computes the exact IEEE speeds only of the cells whose
 // upper bound reaches T, or that carry no bound. The maxima are exact: a cell left
 // out lies below T, and T is below the speed of the cell that set it.
-constexpr int kSpeedK = 4;
 
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
@@ -251,8 +250,9 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 // (3 bits) and the pieces of the two curvature limiters it read (3 bits each):
 // tp/tm point at the line's records, face k goes to index f0 + k - 3 if below fend.
 template <bool REC>
-__device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen, double eps16, unsigned short* tp,
-                                           unsigned short* tm, int f0, int fend) {
+__device__ __forceinline__ void flux_sweep(const double* g, const double* h, int slen, double eps16, unsigned short* tp,
+                                           unsigned short* tm, int f0, int fend, double* out, long long ostr,
+                                           unsigned long long wmask) {
   int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
   double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
@@ -284,7 +284,7 @@ __device__ __forceinline__ void flux_sweep(double* g, const double* h, int slen,
       Ym = mp5_rel2<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16);
     }
     const double F = fma(0.5, Yp + Ym, cp + cm);
-    if (k > 3) g[k - 4] = Fprev - F;
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
     Fprev = F;
     if (k < kend) {
       Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
@@ -339,7 +339,8 @@ __device__ __forceinline__ double limo3_y(double a, double b, double esc) {
 
 // LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep; G^+ from
 // cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k).
-__device__ __forceinline__ void limo3_sweep(double* g, const double* h, int slen, double esc) {
+__device__ __forceinline__ void limo3_sweep(const double* g, const double* h, int slen, double esc, double* out,
+                                            long long ostr, unsigned long long wmask) {
   double Pa = g[2] - g[1], Pb = g[3] - g[2];   // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
   double Mb = h[3] - h[2], Ma = h[4] - h[3];   // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
   double Fprev = 0.0;
@@ -348,7 +349,7 @@ __device__ __forceinline__ void limo3_sweep(double* g, const double* h, int slen
     const double Yp = limo3_y(Pa, Pb, esc);
     const double Ym = -limo3_y(Ma, Mb, esc);
     const double F = fma(0.5, Yp + Ym, g[k - 1] + h[k]);
-    if (k > 3) g[k - 4] = Fprev - F;
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
     Fprev = F;
     if (k < kend) {
       Pa = Pb; Pb = g[k + 1] - g[k];
@@ -379,45 +380,41 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   const int f0 = o[D] + it.s0;
   const int fend = f0 + slen + ((dm.bc[D][1] != 0 && f0 + slen == dm.n[D]) ? 1 : 0);
   const long long nlines = (long long)dm.n[od1] * dm.n[od2];
+  // cells of the segment inside active blocks (a segment through several blocks may
+  // cross a passive one; every line of the item crosses the same blocks)
+  unsigned long long wmask = slen >= 64 ? ~0ull : ((1ull << slen) - 1ull);
+  if (!all_live) {
+    const int bstride = D == 0 ? 1 : (D == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+    const int bo = it.blk - (o[D] / dm.be[D]) * bstride;  // block index with coordinate D = 0
+    for (int j = 0; j < slen; j++)
+      if (!p.active[dm.block0 + bo + ((o[D] + it.s0 + j) / dm.be[D]) * bstride]) wmask &= ~(1ull << j);
+  }
+  const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
+  double* Ld = p.L[D] + dm.off;
+  // one thread per (line, variable): sweep the faces and store L_D of the segment's cells
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
-    double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
+    const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
     const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    x[D] = o[D] + it.s0;
+    double* out = Ld + (long long)v * dm.ncell + ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
     unsigned short *tp = nullptr, *tm = nullptr;
     if (REC) {
-      const int line = it.l0 + pl;
-      const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
       const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
       tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
       tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
     }
     if constexpr (MODE == 2) {
       const double rdx = p.limo3_r * dm.dx[D];
-      limo3_sweep(g, h, slen, 0.25 / (rdx * rdx));
+      limo3_sweep(g, h, slen, 0.25 / (rdx * rdx), out, ostr, wmask);
     } else {
-      flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend);
+      flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend, out, ostr, wmask);
     }
-  }
-  __syncthreads();
-  // coalesced write-out of L_D for the segment's interior cells
-  double* Ld = p.L[D] + dm.off;
-  for (int c = threadIdx.x; c < nl * slen; c += blockDim.x) {
-    int pl, j;
-    if (D == 0) { pl = c / slen; j = c - pl * slen; }
-    else { j = c / nl; pl = c - j * nl; }
-    const int line = it.l0 + pl;
-    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
-    int x[3];
-    x[od1] = o[od1] + a1;
-    x[od2] = o[od2] + a2;
-    x[D] = o[D] + it.s0 + j;
-    if (!all_live) {  // a segment through several blocks may cross a passive one
-      const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
-      if (!p.active[nbk]) continue;
-    }
-    const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
-#pragma unroll
-    for (int v = 0; v < NV; v++) Ld[(long long)v * dm.ncell + idx] = sm[((0 * NV + v) * p.P + pl) * p.SS + j];
   }
   __syncthreads();
 }
