@@ -79,8 +79,9 @@ struct amrfd_handle {
   int dev = 0, nsm = 0;
   // tile of the flux pass
   int seg = 32, lines = 32, threads = 0;
-  size_t flux_smem = 0;
+  size_t flux_smem = 0;             // dynamic shared memory of one flux launch
   int flux_grid = 0;
+  int launch_threads = 0;           // threads of one flux CTA
   // work lists (full, grouped per block in work order) and per-block ranges
   std::vector<int> dom_fbeg, dom_fend, dom_cbeg, dom_cend;  // per domain, in the full lists
   int nfgroups = 0;
@@ -267,8 +268,10 @@ int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
   h->seg = seg;
   h->lines = lines;
   h->threads = threads;
+  h->launch_threads = threads;
   h->flux_smem = smem;
   CK(flux_set_smem(h->cfg.physics, h->nv, smem));
+  CK(flux_rec_set_smem(h->cfg.physics, h->nv, smem));
   int per_sm = 0;
   CK(flux_occupancy(h->cfg.physics, h->nv, h->cfg.recon == AMRFD_LIMO3, threads, smem, &per_sm));
   if (per_sm < 1) return AMRFD_ERR_INVALID_ARG;
@@ -446,7 +449,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
       fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
       {
         Tick tk(h, K_FLUX, s);
-        CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+        CK(launch_flux(ph, nv, fp, h->flux_grid, h->launch_threads, h->flux_smem, s));
       }
       cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
       {
@@ -459,7 +462,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
         fp.items = h->d_fall; fp.item0 = h->dom_fbeg[d]; fp.nitems = h->dom_fend[d] - h->dom_fbeg[d];
         fp.counter = nullptr;
         Tick tk(h, K_FLUX, s);
-        CK(launch_flux(ph, nv, fp, std::min(fp.nitems, h->flux_grid), h->threads, h->flux_smem, s));
+        CK(launch_flux(ph, nv, fp, std::min(fp.nitems, h->flux_grid), h->launch_threads, h->flux_smem, s));
       }
       for (int d : live) {
         cp.items = h->d_call; cp.item0 = h->dom_cbeg[d]; cp.nitems = h->dom_cend[d] - h->dom_cbeg[d];
@@ -801,7 +804,6 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     for (int k = 1; k < h->ns; k++) CK(cudaMalloc(&h->d_gstage[k], sizeof(double) * h->nelem));
     CK(cudaMalloc(&h->d_psifac, sizeof(double) * h->ndom));
     CK(cudaMalloc(&h->d_tape, sizeof(unsigned short) * std::max<long long>(1, h->tape_len) * h->ns));
-    CK(flux_rec_set_smem(h->cfg.physics, h->nv, h->flux_smem));
     int rc = build_adjoint_items(h);
     if (rc) return rc;
   }
@@ -824,7 +826,7 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     fp.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
     {
       Tick tk(h, K_FLUX, s);
-      CK(launch_flux(ph, nv, fp, h->flux_grid, h->threads, h->flux_smem, s));
+      CK(launch_flux(ph, nv, fp, h->flux_grid, h->launch_threads, h->flux_smem, s));
     }
     if (i == h->ns) break;
     CombParams cp = comb_params(h, Un, dt_dev, i);
@@ -945,7 +947,7 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
         for (int rep = 0; rep < 5 && ok; rep++) {
           if (cudaMemsetAsync(h->d_counters, 0, sizeof(int), s) != cudaSuccess) ok = false;
           cudaEventRecord(e0, s);
-          if (launch_flux(h->cfg.physics, h->nv, fp, h->flux_grid, h->threads, h->flux_smem, s) != cudaSuccess) ok = false;
+          if (launch_flux(h->cfg.physics, h->nv, fp, h->flux_grid, h->launch_threads, h->flux_smem, s) != cudaSuccess) ok = false;
           cudaEventRecord(e1, s);
           if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
           float ms = 0.f;

@@ -180,16 +180,19 @@ __device__ __forceinline__ double glm_speed(const unsigned long long* s0, int nd
   return ch;
 }
 
+// Phase A of a flux item: the tile's G^{+-} (lines x segment + halo) into shared
+// memory, cells start, start + stride, ... of the tile.
 template <int PHYS, int NV, int D>
 __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                             const int o[3], double alpha, double ch2, double* sm) {
+                                             const int o[3], double alpha, double ch2, double* sm, int start,
+                                             int stride) {
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
   const int W = it.slen + 2 * kGhost;
   const int nl = it.nl;
   const int P = p.P, SS = p.SS;
   const double gm1 = p.gm1;
-  for (int c = threadIdx.x; c < nl * W; c += blockDim.x) {
+  for (int c = start; c < nl * W; c += stride) {
     int pl, j;
     if (D == 0) { pl = c / W; j = c - pl * W; }
     else { j = c / nl; pl = c - j * nl; }
@@ -358,19 +361,43 @@ __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, in
   }
 }
 
-// MODE 0: MP5; 1: MP5 recording the limiter pieces; 2: LIMO3.
-template <int PHYS, int NV, int D, int MODE>
-__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
-  constexpr bool REC = MODE == 1;
-  const DomDev dm = load_dom(p.doms + it.dom);
-  int o[3];
-  block_coords(dm, it.blk, o);
+// Splitting speed of an item's direction (raised to c_h with GLM) and c_h^2.
+template <int D>
+__device__ __forceinline__ double item_alpha(const FluxParams& p, const FluxItem& it, double& ch2) {
   const unsigned long long* sk = p.araw + (size_t)it.dom * 4;
   const unsigned long long* s0 = p.araw0 + (size_t)it.dom * 4;
   const double ch = p.glm ? glm_speed(s0, p.ndim) : 0.0;
-  const double alpha = imax(bitsd((long long)sk[D]), ch);
-  flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch * ch, sm);
-  __syncthreads();
+  ch2 = ch * ch;
+  return imax(bitsd((long long)sk[D]), ch);
+}
+
+// Whether any / every block the item's segment runs through is active.
+__device__ __forceinline__ bool item_live(const FluxParams& p, const FluxItem& item, bool& all_live) {
+  const DomDev& dm = p.doms[item.dom];
+  const int d = item.d;
+  const int bidx[3] = {item.blk % dm.nb[0], (item.blk / dm.nb[0]) % dm.nb[1], item.blk / (dm.nb[0] * dm.nb[1])};
+  const int stride = d == 0 ? 1 : (d == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+  const int c0 = bidx[d] * dm.be[d] + item.s0;
+  const int b0 = c0 / dm.be[d], b1 = (c0 + item.slen - 1) / dm.be[d];
+  const int g0 = dm.block0 + item.blk + (b0 - bidx[d]) * stride;
+  bool live = false;
+  all_live = true;
+  for (int b = b0; b <= b1; b++) {
+    const bool a = p.active[g0 + (b - b0) * stride] != 0;
+    live |= a;
+    all_live &= a;
+  }
+  return live;
+}
+
+// Phase B of a flux item: one thread per (line, variable) sweeps the faces and stores
+// L_D of the segment's cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
+// 2: LIMO3). Sweeps start, start + stride, ...
+template <int PHYS, int NV, int D, int MODE>
+__device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
+                                             const int o[3], bool all_live, const double* sm, int start,
+                                             int stride) {
+  constexpr bool REC = MODE == 1;
   const int nl = it.nl, slen = it.slen;
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
   // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
@@ -391,8 +418,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   }
   const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
   double* Ld = p.L[D] + dm.off;
-  // one thread per (line, variable): sweep the faces and store L_D of the segment's cells
-  for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
+  for (int t = start; t < nl * NV; t += stride) {
     const int v = t / nl, pl = t - v * nl;
     const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
     const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
@@ -416,6 +442,19 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
       flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend, out, ostr, wmask);
     }
   }
+}
+
+// One flux item by the whole CTA: phase A, barrier, phase B, barrier.
+template <int PHYS, int NV, int D, int MODE>
+__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
+  const DomDev dm = load_dom(p.doms + it.dom);
+  int o[3];
+  block_coords(dm, it.blk, o);
+  double ch2;
+  const double alpha = item_alpha<D>(p, it, ch2);
+  flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch2, sm, threadIdx.x, blockDim.x);
+  __syncthreads();
+  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm, threadIdx.x, blockDim.x);
   __syncthreads();
 }
 
@@ -436,24 +475,8 @@ __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
   while (it < nitems) {
     const FluxItem item = p.items[p.item0 + it];
-    bool live, all_live;
-    {
-      // the item's segment may run through several blocks along its direction
-      const DomDev& dm = p.doms[item.dom];
-      const int d = item.d;
-      const int bidx[3] = {item.blk % dm.nb[0], (item.blk / dm.nb[0]) % dm.nb[1], item.blk / (dm.nb[0] * dm.nb[1])};
-      const int stride = d == 0 ? 1 : (d == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
-      const int c0 = bidx[d] * dm.be[d] + item.s0;
-      const int b0 = c0 / dm.be[d], b1 = (c0 + item.slen - 1) / dm.be[d];
-      const int g0 = dm.block0 + item.blk + (b0 - bidx[d]) * stride;
-      live = false;
-      all_live = true;
-      for (int b = b0; b <= b1; b++) {
-        const bool a = p.active[g0 + (b - b0) * stride] != 0;
-        live |= a;
-        all_live &= a;
-      }
-    }
+    bool all_live;
+    const bool live = item_live(p, item, all_live);
     if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live);
     if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live); }
     if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live); }

@@ -280,3 +280,23 @@ def test_rollout_gradient_against_oracle_central_differences():
         ad = float(np.sum(grad * v))
         # relative to the gradient's norm, the scale of a derivative along a unit direction
         assert abs(fd - ad) <= 1e-6 * gnorm, (fd, ad, gnorm)
+
+
+def test_adjoint_independent_of_flux_tile():
+    """The forward recomputation inside the adjoint records the same limiter pieces under
+    every flux tile: bitwise equal gradients."""
+    A = _A()
+    w = W.adjoint2d(64)
+    U = torch.from_numpy(w.U.ravel().copy()).cuda()
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    g = torch.from_numpy(np.random.default_rng(29).standard_normal(w.U.size)).cuda()
+    outs = []
+    for tile in [None, (16, 8, 128), (32, 16, 160)]:
+        s = A.Solver.from_workload(w)
+        if tile:
+            s.set_tile(*tile)
+        out = torch.empty_like(U)
+        s.adjoint(U, dt, g, out)
+        assert s.error() == A.OK
+        outs.append(out.cpu())
+    assert all(torch.equal(o, outs[0]) for o in outs[1:])
