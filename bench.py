@@ -30,19 +30,20 @@ NV = 9
 # U^n, U^(k) and the output, (2 + 3 + 3) * nv * 8 = 64 nv = 576 bytes.
 BYTES_PER_CELL_UPDATE = 64 * NV
 # Minimal HBM bytes of one flux pass per cell: read U^(k) (nv doubles) and write
-# the three per-direction residuals (3 nv doubles).
+# the three per-direction residuals (3 nv doubles). The kernel also reads five
+# derived quantities per cell (40 B), traffic spent to save FP64 work.
 FLUX_BYTES_PER_CELL = 4 * NV * 8
 # FP64 work of one flux pass per cell and direction, counted by ncu on the blast
 # (profiles/flux_kernel_blast3d.md): DADD + DMUL + 2 DFMA thread instructions = flop,
 # and DADD + DMUL + DFMA = FP64 pipe instructions.
-FLUX_FLOPS_PER_CELL_DIR = 395.7
-FLUX_FP64_INST_PER_CELL_DIR = 276.6
+FLUX_FLOPS_PER_CELL_DIR = 351.7
+FLUX_FP64_INST_PER_CELL_DIR = 249.1
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (profiling recipe table)
 # FP64 pipe: 2 thread instructions / clock / SM (ncu peak_sustained) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write, 128^3 capture,
 # scaled by cells): traffic grows with the cells processed
-FLUX_TRAFFIC_BYTES_PER_CELL = (191.273472 + 397.252352) * 1e6 / 128 ** 3
+FLUX_TRAFFIC_BYTES_PER_CELL = (312.969216 + 408.904192) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):
