@@ -151,6 +151,13 @@ int amrfd_step(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
    first call for a given (U, dt_dev) pair. */
 int amrfd_step_batched(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
 
+/* One CFL-limited step: writes dt_dev[ndomain] (device) exactly as
+   amrfd_dt(h, U, dt_dev, t, t_end) would and advances U with it, bitwise as
+   amrfd_dt followed by amrfd_step_batched, with the speed maxima of U^n (Sec. 2.2,
+   4.4) evaluated once for both. Persistent launches, no graph (t and t_end are
+   arguments of every call). */
+int amrfd_step_cfl(amrfd_handle *h, double *U, double *dt_dev, double t, double t_end, void *stream);
+
 /* Discrete adjoint of one amrfd_step with the same U^n and dt: given
    gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
    Splitting speeds c_max, c_h and the psi damping factor are held fixed at

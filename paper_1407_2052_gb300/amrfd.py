@@ -23,7 +23,8 @@ OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
 EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
            "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
-           "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active")
+           "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active",
+           "amrfd_step_cfl")
 
 
 class Config(ctypes.Structure):
@@ -64,6 +65,7 @@ def load():
     L.amrfd_dt.argtypes = [vp, vp, vp, dp, dp, vp]
     L.amrfd_step.argtypes = [vp, vp, vp, vp]
     L.amrfd_step_batched.argtypes = [vp, vp, vp, vp]
+    L.amrfd_step_cfl.argtypes = [vp, vp, vp, dp, dp, vp]
     L.amrfd_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     L.amrfd_autotune.argtypes = [vp, vp, vp, vp]
     L.amrfd_set_tile.argtypes = [vp, i, i, i]
@@ -228,6 +230,15 @@ class Solver:
     def step_batched(self, U, dt, stream=None):
         _check(load().amrfd_step_batched(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step_batched")
         return U
+
+    def step_cfl(self, U, t=0.0, t_end=float("inf"), out=None, stream=None):
+        """amrfd_step_cfl: CFL dt of U (returned, also in `out`) and one step with it."""
+        import torch
+        if out is None:
+            out = torch.empty(self.ndom, dtype=torch.float64, device=U.device)
+        _check(load().amrfd_step_cfl(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)),
+               "amrfd_step_cfl")
+        return out
 
     def adjoint(self, U_n, dt, gU_np1, gU_n, stream=None):
         _check(load().amrfd_adjoint(self._h, _ptr(U_n), _ptr(dt), _ptr(gU_np1), _ptr(gU_n), _stream(stream)),

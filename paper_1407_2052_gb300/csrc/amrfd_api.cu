@@ -427,19 +427,45 @@ int speeds_from_scratch(amrfd_handle* h, const double* U, int k, int want_rate, 
   return launch_speeds_over(h, p, batched, live, s);
 }
 
+// The CFL time step per domain from the exact speed maxima (and rate) in slot sl.
+int launch_dt_from(amrfd_handle* h, const unsigned long long* sl, double* dt_dev, double t, double t_end,
+                   cudaStream_t s) {
+  DtParams q{};
+  q.doms = h->d_dom;
+  q.slot = sl;
+  q.dt_out = dt_dev;
+  q.ndom = h->ndom;
+  q.cfl = h->cfg.cfl;
+  q.t = t;
+  q.t_end = t_end;
+  q.glm = h->cfg.physics == AMRFD_MHD_GLM;
+  q.ndim = h->cfg.ndim;
+  q.global_min = h->cfg.dt_scope == AMRFD_DT_GLOBAL;
+  Tick tk(h, K_DT, s);
+  CK(launch_dt(q, s));
+  return AMRFD_OK;
+}
+
 // Enqueue one full step. batched: persistent launches over the compacted lists;
-// else one launch per domain (per pass) over that domain's items.
-int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, bool batched) {
+// else one launch per domain (per pass) over that domain's items. cfl_dt: the time
+// step is computed here from the speeds of U^n (written to cfl_dt, then used).
+int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, bool batched,
+                 double* cfl_dt = nullptr, double t = 0.0, double t_end = 0.0) {
   const int ph = h->cfg.physics, nv = h->nv;
   CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
   CK(cudaMemsetAsync(h->d_tlow, 0, sizeof(unsigned) * h->ns * h->ndom * 4, s));
   if (batched) CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
   const int cgrid = 8 * h->nsm;
   const std::vector<int> live = batched ? std::vector<int>() : live_domains(h);
-  // speeds of U^n
+  // speeds of U^n (with the CFL rate when the step computes its own dt)
   {
-    int rc = speeds_from_scratch(h, U, 0, 0, batched, live, s);
+    int rc = speeds_from_scratch(h, U, 0, cfl_dt ? 1 : 0, batched, live, s);
     if (rc) return rc;
+    if (cfl_dt) {
+      rc = launch_dt_from(h, slot(h, 0), cfl_dt, t, t_end, s);
+      if (rc) return rc;
+      dt = cfl_dt;
+    }
   }
   for (int i = 1; i <= h->ns; i++) {
     const double* Uk = (i == 1) ? U : h->d_stage[i - 1];
@@ -682,23 +708,14 @@ int amrfd_get_active(amrfd_handle* h, uint8_t* active_dev, void* stream) {
 int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double t_end, void* stream) {
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
-  unsigned long long* sl = slot(h, kSlotDt);
   int rc = speeds_from_scratch(h, U, kSlotDt, 1, true, std::vector<int>(), s);
   if (rc) return rc;
-  DtParams q{};
-  q.doms = h->d_dom;
-  q.slot = sl;
-  q.dt_out = dt_dev;
-  q.ndom = h->ndom;
-  q.cfl = h->cfg.cfl;
-  q.t = t;
-  q.t_end = t_end;
-  q.glm = h->cfg.physics == AMRFD_MHD_GLM;
-  q.ndim = h->cfg.ndim;
-  q.global_min = h->cfg.dt_scope == AMRFD_DT_GLOBAL;
-  Tick tk(h, K_DT, s);
-  CK(launch_dt(q, s));
-  return AMRFD_OK;
+  return launch_dt_from(h, slot(h, kSlotDt), dt_dev, t, t_end, s);
+}
+
+int amrfd_step_cfl(amrfd_handle* h, double* U, double* dt_dev, double t, double t_end, void* stream) {
+  if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
+  return enqueue_step(h, U, dt_dev, (cudaStream_t)stream, true, dt_dev, t, t_end);
 }
 
 int amrfd_step(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {

@@ -589,3 +589,23 @@ def test_limo3_tiles_and_adjoint_unsupported():
     with pytest.raises(A().AmrfdError) as e:
         s.adjoint(U, dt, g, torch.empty_like(U))
     assert e.value.code == A().ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("scope", [0, 1])
+def test_step_cfl_equals_dt_then_step(scope):
+    """amrfd_step_cfl = amrfd_dt + amrfd_step_batched, bitwise (time steps and states),
+    on uneven batched blocks with passive ones, per-domain and global dt, to t_end."""
+    w = W.batched(nblocks=30, sizes=(8, 12, 16))
+    A_ = A()
+    s1 = A_.Solver.from_workload(w, dt_scope=scope)
+    s2 = A_.Solver.from_workload(w, dt_scope=scope)
+    U1, U2 = dev(w.U.copy()), dev(w.U.copy())
+    t, t_end = 0.0, 3e-3
+    for _ in range(6):
+        d1 = s1.dt(U1, t, t_end)
+        s1.step_batched(U1, d1)
+        d2 = s2.step_cfl(U2, t, t_end)
+        assert torch.equal(d1, d2)
+        t += float(d1.min().item())
+    assert s1.error() == A_.OK and s2.error() == A_.OK
+    assert torch.equal(U1, U2)
