@@ -609,3 +609,57 @@ def test_step_cfl_equals_dt_then_step(scope):
         t += float(d1.min().item())
     assert s1.error() == A_.OK and s2.error() == A_.OK
     assert torch.equal(U1, U2)
+
+
+# ------------------------------------------ full sizes, in the bench's launch configuration
+def test_blast_full_size_one_step_elementwise():
+    """The bench's workload and launches (256^3 in 16^3 blocks, autotuned tile,
+    amrfd_step_cfl): the whole first step against the oracle element by element (about
+    half a minute of oracle time), dt bitwise, relative L1 <= 1e-10 and relative L-inf
+    <= 1e-9 per variable group."""
+    w = W.blast3d(256, 16)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel().copy())
+    dt = s.dt(U)
+    s.autotune(U, dt)
+    dt = s.step_cfl(U)
+    assert s.error() == A().OK
+    c, d = ocfg(w), odom(w.domains[0])
+    h, _ = O.dt(c, d, w.U, w.cfl)
+    assert float(dt[0].item()) == h
+    ref, fl, _, ch = O.step(c, d, w.U, h)
+    assert fl == 0
+    got = host(U, ref.shape)
+    assert rel_l1(got, ref, ch) <= 1e-10
+    assert rel_linf(got, ref, ch) <= 1e-9
+
+
+def test_batched_20000_blocks_sampled_against_oracle():
+    """The batched workload at its full size (20000 uneven blocks, 30% passive) through
+    the persistent work list: 60 sampled domains recomputed by the oracle one by one
+    (dt bitwise, one step to 1e-12), and every passive domain untouched."""
+    w = W.batched(20000)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U)
+    dt = s.step_cfl(U)
+    assert s.error() == A().OK
+    got, dth = U.cpu().numpy(), dt.cpu().numpy()
+    c = ocfg(w)
+    rng = np.random.default_rng(12)
+    for i in rng.choice(len(w.domains), 60, replace=False):
+        dd = w.domains[i]
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        shape = (9,) + tuple(dd.n[::-1])
+        if not w.active[i]:
+            assert np.array_equal(got[sl], w.U[sl])
+            continue
+        od = odom(dd)
+        h, _ = O.dt(c, od, w.U[sl].reshape(shape), w.cfl)
+        assert h == dth[i]
+        ref, fl, _, ch = O.step(c, od, w.U[sl].reshape(shape), h)
+        assert rel_linf(got[sl].reshape(shape), ref, ch) <= 1e-12, i
+    passive = np.flatnonzero(w.active == 0)
+    for i in passive[:: max(1, len(passive) // 200)]:
+        dd = w.domains[i]
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        assert np.array_equal(got[sl], w.U[sl])
