@@ -247,8 +247,8 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 
 // Sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of the
 // line's extended index (cell j = k-1 left of face k), then the flux difference
-// Fsum_{k-1} - Fsum_k of cells j = 3..slen+2 written back over the consumed part of
-// the G^+ line (the factor 1/(2 dx) is applied by the stage combination).
+// Fsum_{k-1} - Fsum_k of the segment's cell k-4 stored to out[(k-4) ostr] where
+// wmask has its bit (the factor 1/(2 dx) is applied by the stage combination).
 // REC additionally records, per face and bias, which linear piece the limiter took
 // (3 bits) and the pieces of the two curvature limiters it read (3 bits each):
 // tp/tm point at the line's records, face k goes to index f0 + k - 3 if below fend.
