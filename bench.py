@@ -177,10 +177,30 @@ def adjoint_extra(torch, A, W, reps=3):
     e1.record()
     torch.cuda.synchronize()
     adj = e0.elapsed_time(e1) / reps
+    # the full gradient: 200 steps with checkpoints every 20 (forward, recomputation and
+    # adjoints) against 200 forward steps
+    from paper_1407_2052_gb300 import autodiff
+    area = w.domains[0].dx[0] * w.domains[0].dx[1]
+    e0.record()
+    V.copy_(U)
+    for _ in range(200):
+        s.step_batched(V, dt)
+    e1.record()
+    torch.cuda.synchronize()
+    fwd200 = e0.elapsed_time(e1)
+    U0r = U.clone().requires_grad_(True)
+    e0.record()
+    Uf = autodiff.rollout(s, U0r, dt, 200, 20)
+    B = Uf.view(9, -1)[5:8]
+    (0.5 * (B * B).sum() * area).backward()
+    e1.record()
+    torch.cuda.synchronize()
+    grad200 = e0.elapsed_time(e1)
     assert s.error() == A.OK
     s.close()
     return {"workload": "adjoint2d: 2D MHD+GLM 512^2, SSPRK3, dt 1e-3", "forward_ms": fwd, "adjoint_ms": adj,
-            "ratio": adj / fwd}
+            "ratio": adj / fwd, "rollout_200_steps_every_20": {"forward_ms": fwd200, "gradient_ms": grad200,
+                                                                 "ratio": grad200 / fwd200}}
 
 
 def _time_steps(torch, fn, steps):

@@ -241,9 +241,9 @@ def test_adjoint_matches_autograd_at_128():
 
 def test_rollout_gradient_against_oracle_central_differences():
     """dJ/dU^0 of J = sum |B|^2/2 dx dy after 10 steps (checkpoints every 4) at 128^2,
-    against central differences (h = 1e-6) of the oracle's frozen-speed steps along five
+    against central differences (h = 1e-6) of the oracle's frozen-speed steps along
     random unit directions, each step with the speeds of the oracle's own trajectory:
-    agreement to 1e-6 of the gradient's norm."""
+    agreement to 1e-6 of the gradient's norm, on 20 seeded directions."""
     from paper_1407_2052_gb300 import autodiff
     A = _A()
     w = W.adjoint2d(128)
@@ -271,7 +271,7 @@ def test_rollout_gradient_against_oracle_central_differences():
     rng = np.random.default_rng(23)
     h = 1e-6
     gnorm = float(np.linalg.norm(grad))
-    for _ in range(5):
+    for _ in range(20):
         v = rng.standard_normal(w.U.shape)
         v /= np.linalg.norm(v)
         Bp, Bm = final(w.U + h * v)[5:8], final(w.U - h * v)[5:8]
@@ -300,3 +300,38 @@ def test_adjoint_independent_of_flux_tile():
         assert s.error() == A.OK
         outs.append(out.cpu())
     assert all(torch.equal(o, outs[0]) for o in outs[1:])
+
+
+def test_rollout_200_steps_checkpoint_20_at_512():
+    """The adjoint workload's full length: 512^2, 200 fixed-dt steps, checkpoints every 20,
+    J = sum |B|^2/2 dx dy; the rollout gradient equals (bitwise) the chain of single-step
+    adjoints over the stored trajectory, and is finite."""
+    from paper_1407_2052_gb300 import autodiff
+    A = _A()
+    w = W.adjoint2d(512)
+    area = w.domains[0].dx[0] * w.domains[0].dx[1]
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel().copy()).cuda()
+    dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    nsteps = 200
+    U0r = U0.clone().requires_grad_(True)
+    Uf = autodiff.rollout(s, U0r, dt, nsteps, 20)
+    B = Uf.view(9, -1)[5:8]
+    (0.5 * (B * B).sum() * area).backward()
+    grad = U0r.grad.clone()
+    assert bool(torch.isfinite(grad).all())
+    states = [U0.clone()]
+    for _ in range(nsteps):
+        nxt = states[-1].clone()
+        s.step_batched(nxt, dt)
+        states.append(nxt)
+    assert torch.equal(states[-1], Uf.detach())
+    gB = torch.zeros_like(U0).view(9, -1)
+    gB[5:8] = states[-1].view(9, -1)[5:8] * area
+    g = gB.view(-1).clone()
+    out = torch.empty_like(g)
+    for j in reversed(range(nsteps)):
+        s.adjoint(states[j], dt, g, out)
+        g, out = out, g
+    assert s.error() == A.OK
+    assert torch.equal(g, grad)

@@ -663,3 +663,64 @@ def test_batched_20000_blocks_sampled_against_oracle():
         dd = w.domains[i]
         sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
         assert np.array_equal(got[sl], w.U[sl])
+
+
+# ------------------------------------------------------- full-length runs at reduced size
+def test_blast_64_for_200_steps_vs_oracle():
+    """The blast's full length (200 CFL steps) at 64^3 in 16^3 blocks against the oracle
+    run step by step (about two minutes of oracle time): the same time steps (the first
+    bitwise, then to rounding) and relative L1 <= 1e-10 at the end."""
+    w = W.blast3d(64, 16)
+    s, U, dts = run_gpu(w, 200)
+    ref, odts = run_oracle(w, 200)
+    got = [float(x[0].item()) for x in dts]
+    assert got[0] == odts[0]
+    assert np.allclose(got, odts, rtol=1e-12, atol=0.0)
+    assert rel_l1(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-10
+
+
+def test_batched_blocks_20_steps_vs_oracle():
+    """100 uneven batched blocks (30% passive), 20 steps with per-block CFL dt, against
+    the oracle block by block."""
+    w = W.batched(nblocks=100)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.copy())
+    dts = []
+    for _ in range(20):
+        dts.append(s.step_cfl(U).cpu().numpy())
+    assert s.error() == A().OK
+    got = U.cpu().numpy()
+    c = ocfg(w)
+    for i, dd in enumerate(w.domains):
+        sl = slice(dd.offset, dd.offset + 9 * dd.ncell)
+        if not w.active[i]:
+            assert np.array_equal(got[sl], w.U[sl])
+            continue
+        shape = (9,) + tuple(dd.n[::-1])
+        od = odom(dd)
+        Uo = w.U[sl].reshape(shape).copy()
+        for k in range(20):
+            h, _ = O.dt(c, od, Uo, w.cfl)
+            assert h == dts[k][i] if k == 0 else abs(h - dts[k][i]) <= 1e-12 * h, (i, k)
+            Uo, fl, _, ch = O.step(c, od, Uo, h)
+            assert fl == 0
+        assert rel_linf(got[sl].reshape(shape), Uo, ch) <= 1e-10, i
+
+
+def test_blast_full_size_200_steps_physical_and_conservative():
+    """The bench workload for its full 200 steps (GPU only): no non-physical state, totals
+    of rho, m, E, B conserved to rounding, c_max still from a finite state."""
+    w = W.blast3d(256, 16)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel().copy())
+    del w
+    V = U.view(9, -1)
+    tot0 = V[:8].sum(dim=1)
+    scale = V[:8].abs().sum(dim=1).max()
+    dt = torch.empty(1, dtype=torch.float64, device="cuda")
+    for _ in range(200):
+        s.step_cfl(U, out=dt)
+    assert s.error() == A().OK
+    assert bool(torch.isfinite(U).all())
+    assert torch.all((V[:8].sum(dim=1) - tot0).abs() <= 1e-11 * scale)
+    assert 0.0 < float(dt[0].item()) < 1.0
