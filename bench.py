@@ -453,7 +453,8 @@ def run_ours(args, rank, world, local_rank):
                          "achieved_step": value / world * BYTES_PER_CELL_UPDATE / 1e9,
                          "achieved_flux": flux_gbs, "peak": hbm_peak,
                          "frac_step": value / world * BYTES_PER_CELL_UPDATE / 1e9 / hbm_peak,
-                         "frac_flux": flux_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs"},
+                         "frac_flux": flux_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                         "frac_step_of_nominal_7900": value / world * BYTES_PER_CELL_UPDATE / 1e9 / 7900.0},
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "clocks": clocks,
