@@ -58,6 +58,8 @@ extern "C" {
 #define AMRFD_ERR_CUDA 2
 #define AMRFD_ERR_UNSUPPORTED 3
 #define AMRFD_ERR_NONPHYSICAL 4 /* device found rho <= 0, p <= 0 or a non-finite value */
+#define AMRFD_ERR_CHECK 5       /* checked build (-DAMRFD_CHECKS): a work descriptor or index
+                                   check failed in a kernel; the access was skipped */
 
 typedef struct amrfd_config {
   int physics;    /* AMRFD_EULER | AMRFD_MHD_GLM */
@@ -196,8 +198,8 @@ int amrfd_timing_end(amrfd_handle *h, double ms[4], int counts[4], void *stream)
    out[stage][domain][3], host memory, `nstage` = stages to copy. Synchronises. */
 int amrfd_get_alpha(amrfd_handle *h, double *out, int nstage, void *stream);
 
-/* Synchronise `stream`, return the latched device condition (AMRFD_OK or
-   AMRFD_ERR_NONPHYSICAL) and clear it. */
+/* Synchronise `stream`, return the latched device condition (AMRFD_OK,
+   AMRFD_ERR_CHECK in a checked build, else AMRFD_ERR_NONPHYSICAL) and clear it. */
 int amrfd_get_error(amrfd_handle *h, void *stream);
 
 /* Free the handle and its workspace (synchronises the device first). */

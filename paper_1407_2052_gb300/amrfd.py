@@ -12,13 +12,14 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libamrfd.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libamrfd_checked.so")
 
 EULER, MHD_GLM = 0, 1
 SSPRK3, SSPRK54, SSPRK43 = 0, 1, 2
 PERIODIC, OUTFLOW, SYMMETRIC = 0, 1, 2
 MP5, LIMO3 = 0, 1
 DT_PER_DOMAIN, DT_GLOBAL = 0, 1
-OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL = 0, 1, 2, 3, 4
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_UNSUPPORTED, ERR_NONPHYSICAL, ERR_CHECK = 0, 1, 2, 3, 4, 5
 
 EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_step_batched",
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
@@ -45,17 +46,19 @@ class AmrfdError(RuntimeError):
         super().__init__("%s: %s (code %d)" % (what, _strerror(code), code))
 
 
-_lib = None
+_libs = {}
 
 
-def load():
-    """Load libamrfd.so (built by paper_1407_2052_gb300.build); raise if absent."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libamrfd.so is not built; run `python -c 'import __graft_entry__ as g; g.build()'`")
-    L = ctypes.CDLL(LIB_PATH)
+def load(checked=False):
+    """Load libamrfd.so (checked: libamrfd_checked.so, the build with kernel index
+    checks), built by paper_1407_2052_gb300.build; raise if absent."""
+    if checked in _libs:
+        return _libs[checked]
+    path = LIB_CHECKED_PATH if checked else LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built; run `python -c 'import __graft_entry__ as g; g.build()'`"
+                           % os.path.basename(path))
+    L = ctypes.CDLL(path)
     vp, dp, i = ctypes.c_void_p, ctypes.c_double, ctypes.c_int
     L.amrfd_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Config), ctypes.POINTER(DomainC), i, vp, vp]
     L.amrfd_set_active.argtypes = [vp, vp, vp]
@@ -82,7 +85,7 @@ def load():
     for name in EXPORTS:
         if name not in ("amrfd_destroy", "amrfd_strerror"):
             getattr(L, name).restype = i
-    _lib = L
+    _libs[checked] = L
     return L
 
 
@@ -145,8 +148,8 @@ class Solver:
     """One amrfd handle: a set of domains advanced together on the current GPU."""
 
     def __init__(self, physics, ndim, integrator, gamma, cfl, domains, active=None, glm_cr=0.18,
-                 dt_scope=DT_PER_DOMAIN, stream=None, recon=MP5, limo3_r=1.0):
-        L = load()
+                 dt_scope=DT_PER_DOMAIN, stream=None, recon=MP5, limo3_r=1.0, checked=False):
+        L = self._L = load(checked)
         self.cfg = Config(physics, ndim, integrator, dt_scope, gamma, cfl, glm_cr, recon, 0, limo3_r)
         self.domains = list(domains)
         self.ndom = len(self.domains)
@@ -174,7 +177,7 @@ class Solver:
 
     def close(self):
         if getattr(self, "_h", None):
-            load().amrfd_destroy(self._h)
+            self._L.amrfd_destroy(self._h)
             self._h = None
 
     def __del__(self):
@@ -187,7 +190,7 @@ class Solver:
         import torch
         if active_dev.dtype != torch.uint8 or not active_dev.is_cuda or active_dev.numel() != self.nblocks:
             raise TypeError("expected a CUDA uint8 tensor with one flag per block")
-        _check(load().amrfd_set_active(self._h, ctypes.c_void_p(active_dev.data_ptr()), _stream(stream)),
+        _check(self._L.amrfd_set_active(self._h, ctypes.c_void_p(active_dev.data_ptr()), _stream(stream)),
                "amrfd_set_active")
 
     def _flags(self, t):
@@ -201,34 +204,34 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty(self.nblocks, dtype=torch.uint8, device=U.device)
-        _check(load().amrfd_flag_steady(self._h, _ptr(U), _ptr(U_ref), float(tol), self._flags(out),
+        _check(self._L.amrfd_flag_steady(self._h, _ptr(U), _ptr(U_ref), float(tol), self._flags(out),
                                         _stream(stream)), "amrfd_flag_steady")
         return out
 
     def activate(self, flag, belt=1, stream=None):
         """amrfd_activate: passive candidates `flag`, `belt` safety layers, device work lists rebuilt."""
-        _check(load().amrfd_activate(self._h, self._flags(flag), int(belt), _stream(stream)), "amrfd_activate")
+        _check(self._L.amrfd_activate(self._h, self._flags(flag), int(belt), _stream(stream)), "amrfd_activate")
 
     def active(self, stream=None):
         """Current per-block active flags (CUDA uint8 tensor)."""
         import torch
         out = torch.empty(self.nblocks, dtype=torch.uint8, device="cuda")
-        _check(load().amrfd_get_active(self._h, self._flags(out), _stream(stream)), "amrfd_get_active")
+        _check(self._L.amrfd_get_active(self._h, self._flags(out), _stream(stream)), "amrfd_get_active")
         return out
 
     def dt(self, U, t=0.0, t_end=float("inf"), out=None, stream=None):
         import torch
         if out is None:
             out = torch.empty(self.ndom, dtype=torch.float64, device=U.device)
-        _check(load().amrfd_dt(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)), "amrfd_dt")
+        _check(self._L.amrfd_dt(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)), "amrfd_dt")
         return out
 
     def step(self, U, dt, stream=None):
-        _check(load().amrfd_step(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step")
+        _check(self._L.amrfd_step(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step")
         return U
 
     def step_batched(self, U, dt, stream=None):
-        _check(load().amrfd_step_batched(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step_batched")
+        _check(self._L.amrfd_step_batched(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_step_batched")
         return U
 
     def step_cfl(self, U, t=0.0, t_end=float("inf"), out=None, stream=None):
@@ -236,47 +239,47 @@ class Solver:
         import torch
         if out is None:
             out = torch.empty(self.ndom, dtype=torch.float64, device=U.device)
-        _check(load().amrfd_step_cfl(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)),
+        _check(self._L.amrfd_step_cfl(self._h, _ptr(U), _ptr(out), float(t), float(t_end), _stream(stream)),
                "amrfd_step_cfl")
         return out
 
     def adjoint(self, U_n, dt, gU_np1, gU_n, stream=None):
-        _check(load().amrfd_adjoint(self._h, _ptr(U_n), _ptr(dt), _ptr(gU_np1), _ptr(gU_n), _stream(stream)),
+        _check(self._L.amrfd_adjoint(self._h, _ptr(U_n), _ptr(dt), _ptr(gU_np1), _ptr(gU_n), _stream(stream)),
                "amrfd_adjoint")
         return gU_n
 
     def autotune(self, U, dt, stream=None):
-        _check(load().amrfd_autotune(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_autotune")
+        _check(self._L.amrfd_autotune(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_autotune")
         return self.get_tile()
 
     def set_tile(self, seg, lines, threads):
-        _check(load().amrfd_set_tile(self._h, seg, lines, threads), "amrfd_set_tile")
+        _check(self._L.amrfd_set_tile(self._h, seg, lines, threads), "amrfd_set_tile")
 
     def get_tile(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(load().amrfd_get_tile(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "amrfd_get_tile")
+        _check(self._L.amrfd_get_tile(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "amrfd_get_tile")
         return a.value, b.value, c.value
 
     def alpha(self, nstage=None, stream=None):
         """Raw per-stage splitting speeds of the last step, shape (nstage, ndom, 3)."""
         nstage = self.nstages if nstage is None else nstage
         out = np.zeros((nstage, self.ndom, 3))
-        _check(load().amrfd_get_alpha(self._h, out.ctypes.data_as(ctypes.c_void_p), nstage, _stream(stream)),
+        _check(self._L.amrfd_get_alpha(self._h, out.ctypes.data_as(ctypes.c_void_p), nstage, _stream(stream)),
                "amrfd_get_alpha")
         return out
 
     KINDS = ("speeds", "flux", "combine", "dt")
 
     def timing_begin(self, capacity):
-        _check(load().amrfd_timing_begin(self._h, int(capacity)), "amrfd_timing_begin")
+        _check(self._L.amrfd_timing_begin(self._h, int(capacity)), "amrfd_timing_begin")
 
     def timing_end(self, stream=None):
         """{kind: (total_ms, launches)} for the launches since timing_begin."""
         ms = np.zeros(4)
         cnt = np.zeros(4, dtype=np.int32)
-        _check(load().amrfd_timing_end(self._h, ms.ctypes.data_as(ctypes.c_void_p),
+        _check(self._L.amrfd_timing_end(self._h, ms.ctypes.data_as(ctypes.c_void_p),
                                        cnt.ctypes.data_as(ctypes.c_void_p), _stream(stream)), "amrfd_timing_end")
         return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(self.KINDS)}
 
     def error(self, stream=None):
-        return load().amrfd_get_error(self._h, _stream(stream))
+        return self._L.amrfd_get_error(self._h, _stream(stream))

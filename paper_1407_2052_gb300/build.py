@@ -14,6 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libamrfd.so")
+LIB_CHECKED = os.path.join(HERE, "libamrfd_checked.so")  # -DAMRFD_CHECKS: kernel index checks
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["amrfd_kernels.cu", "amrfd_adjoint.cu", "amrfd_api.cu", "amrfd_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -33,14 +34,21 @@ def _deps():
     return max(os.path.getmtime(f) for f in files)
 
 
-def build(force=False, verbose=False, extra=()):
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _deps() and not extra:
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra=(), checked=False):
+    """Build libamrfd.so, or with checked=True libamrfd_checked.so: the same library
+    compiled with -DAMRFD_CHECKS (descriptor and index checks in the kernels that record
+    AMRFD_ERR_CHECK and skip the access)."""
+    lib = LIB_CHECKED if checked else LIB
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _deps() and not extra:
+        return lib
+    bdir = BUILD + ("_checked" if checked else "")
+    os.makedirs(bdir, exist_ok=True)
     nvcc = _nvcc()
+    if checked:
+        extra = list(extra) + ["-DAMRFD_CHECKS"]
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [nvcc] + ARCH + FLAGS + list(extra) + ["-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
@@ -54,13 +62,13 @@ def build(force=False, verbose=False, extra=()):
     if verbose:
         for _, err in outs:
             sys.stderr.write(err)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in outs] + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

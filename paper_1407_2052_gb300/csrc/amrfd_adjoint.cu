@@ -308,6 +308,7 @@ __global__ void __launch_bounds__(256) adj_flux_kernel(AdjFluxParams p) {
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const FluxItem item = p.items[p.item0 + it];
+    AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.P, p.SSg, item), continue)
     if (!p.active[p.doms[item.dom].block0 + item.blk]) continue;
     if (item.d == 0) adj_item<PHYS, NV, 0>(p, item, sm);
     if constexpr (maxd > 1) { if (item.d == 1) adj_item<PHYS, NV, 1>(p, item, sm); }
@@ -320,6 +321,7 @@ template <int NV>
 __global__ void __launch_bounds__(256) adj_combine_kernel(AdjCombParams p) {
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
+    AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = p.doms[ci.dom];
     if (!p.active[dm.block0 + ci.blk]) continue;
     int o[3];
@@ -351,6 +353,7 @@ __global__ void __launch_bounds__(256) adj_combine_kernel(AdjCombParams p) {
 __global__ void __launch_bounds__(256) adj_passive_kernel(AdjCombParams p) {
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
+    AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = p.doms[ci.dom];
     if (p.active[dm.block0 + ci.blk]) continue;
     int o[3];

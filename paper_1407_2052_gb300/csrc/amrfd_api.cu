@@ -332,6 +332,8 @@ FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int 
   p.SS = SS;
   p.glm = h->cfg.physics == AMRFD_MHD_GLM;
   p.W = h->d_W;
+  p.err = h->d_err;
+  p.ndom = h->ndom;
   return p;
 }
 
@@ -355,6 +357,7 @@ CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
   p.final_stage = (i == h->ns);
   p.W = (i < h->ns) ? h->d_W : nullptr;  // the next flux pass reads them
   p.gm1 = h->cfg.gamma - 1.0;
+  p.ndom = h->ndom;
   return p;
 }
 
@@ -370,6 +373,7 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   p.ndim = h->cfg.ndim;
   p.want_rate = want_rate;
   p.gm1 = h->cfg.gamma - 1.0;
+  p.ndom = h->ndom;
   return p;
 }
 
@@ -557,6 +561,7 @@ const char* amrfd_strerror(int code) {
     case AMRFD_ERR_CUDA: return "CUDA runtime error";
     case AMRFD_ERR_UNSUPPORTED: return "unsupported";
     case AMRFD_ERR_NONPHYSICAL: return "non-physical state (rho <= 0, p <= 0 or non-finite)";
+    case AMRFD_ERR_CHECK: return "descriptor or index check failed (checked build)";
     default: return "unknown error";
   }
 }
@@ -664,6 +669,8 @@ int amrfd_flag_steady(amrfd_handle* h, const double* U, const double* U_ref, dou
   cudaStream_t s = (cudaStream_t)stream;
   CK(cudaMemsetAsync(flag_dev, 1, h->nblocks, s));
   FlagParams p{};
+  p.err = h->d_err;
+  p.ndom = h->ndom;
   p.doms = h->d_dom;
   p.items = h->d_call;
   p.nitems = h->nci;
@@ -883,6 +890,8 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     ap.SSg = h->adj_SSg;
     ap.glm = h->cfg.physics == AMRFD_MHD_GLM;
     ap.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
+    ap.err = h->d_err;
+    ap.ndom = h->ndom;
     {
       Tick tk(h, K_FLUX, s);
       CK(launch_adj_flux(ph, nv, ap, std::min(ap.nitems, 16 * h->nsm), h->adj_threads, h->adj_smem, s));
@@ -901,6 +910,8 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     cq.kin = i - 1;
     cq.ndim = h->cfg.ndim;
     cq.nv = nv;
+    cq.err = h->d_err;
+    cq.ndom = h->ndom;
     {
       Tick tk(h, K_COMBINE, s);
       CK(launch_adj_combine(nv, cq, std::min(h->nci, cgrid), 256, s));
@@ -1037,6 +1048,7 @@ int amrfd_get_error(amrfd_handle* h, void* stream) {
   CK(cudaMemcpyAsync(&e, h->d_err, sizeof e, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   CK(cudaMemsetAsync(h->d_err, 0, sizeof(unsigned), (cudaStream_t)stream));
   CK(cudaStreamSynchronize((cudaStream_t)stream));
+  if (e & kErrCheck) return AMRFD_ERR_CHECK;
   return (e & kErrNonphysical) ? AMRFD_ERR_NONPHYSICAL : AMRFD_OK;
 }
 

@@ -13,6 +13,28 @@ namespace amrfd {
 
 enum { PH_EULER = 0, PH_MHD = 1 };
 
+// Descriptor checks of the checked builds: a flux item lies inside its domain and its
+// tile fits the shared-memory layout (P lines, SS doubles per line); a cell item lies
+// inside its block.
+__device__ __forceinline__ bool flux_item_ok(const DomDev* doms, int ndom, int ndim, int P, int SS,
+                                             const FluxItem& it) {
+  if (it.dom < 0 || it.dom >= ndom) return false;
+  const DomDev& dm = doms[it.dom];
+  const int d = it.d;
+  if (d >= ndim || it.blk < 0 || it.blk >= dm.nb[0] * dm.nb[1] * dm.nb[2]) return false;
+  const int od1 = d == 0 ? 1 : 0, od2 = d == 2 ? 1 : 2;
+  const int bd = (d == 0 ? it.blk % dm.nb[0] : (d == 1 ? (it.blk / dm.nb[0]) % dm.nb[1] : it.blk / (dm.nb[0] * dm.nb[1])));
+  return it.nl >= 1 && it.nl <= P && it.l0 >= 0 && it.l0 + it.nl <= dm.be[od1] * dm.be[od2] && it.s0 >= 0 &&
+         it.slen >= 1 && it.slen + 2 * kGhost <= SS && bd * dm.be[d] + it.s0 + it.slen <= dm.n[d];
+}
+
+__device__ __forceinline__ bool cell_item_ok(const DomDev* doms, int ndom, const CellItem& ci) {
+  if (ci.dom < 0 || ci.dom >= ndom) return false;
+  const DomDev& dm = doms[ci.dom];
+  return ci.blk >= 0 && ci.blk < dm.nb[0] * dm.nb[1] * dm.nb[2] && ci.c0 >= 0 && ci.cnt >= 0 &&
+         ci.c0 + ci.cnt <= dm.be[0] * dm.be[1] * dm.be[2];
+}
+
 // ---------------------------------------------------------------- exact helpers
 __device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }

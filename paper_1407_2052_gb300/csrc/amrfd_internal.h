@@ -9,6 +9,21 @@ constexpr int kMaxStages = 5;
 constexpr int kSlotDt = 5;      // speed slot used by amrfd_dt (slots 0..4: RK stage inputs)
 constexpr int kNumSlots = 6;
 constexpr unsigned kErrNonphysical = 1u;
+constexpr unsigned kErrCheck = 2u;  // checked builds: a descriptor or index check failed
+
+// Checked builds (-DAMRFD_CHECKS): descriptor and index checks in the kernels. A failed
+// check records kErrCheck in the error word and skips the access (`skip` is a
+// statement such as continue or return) instead of letting it fault; the normal build
+// compiles them away.
+#ifdef AMRFD_CHECKS
+#define AMRFD_GUARD(err, cond, skip) \
+  if (!(cond)) {                     \
+    atomicOr((err), kErrCheck);      \
+    skip;                            \
+  }
+#else
+#define AMRFD_GUARD(err, cond, skip)
+#endif
 
 // One domain as the kernels see it.
 struct DomDev {

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
   const bool want_rate = p.want_rate != 0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
+    AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = load_dom(p.doms + ci.dom);
     if (!p.active[dm.block0 + ci.blk]) continue;
     int o[3];
@@ -213,6 +214,8 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
       g = b == 0 ? g - dm.n[D] : (b == 1 ? dm.n[D] - 1 : 2 * dm.n[D] - 1 - g);
     }
     x[D] = g;
+    AMRFD_GUARD(p.err, g >= 0 && g < dm.n[D] && x[od1] < dm.n[od1] && x[od2] < dm.n[od2] && pl < P && j < SS,
+                continue)
     const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
     const bool act = p.active[nbk] != 0;
     const double* base = act ? p.Uk : p.Un;
@@ -475,8 +478,10 @@ __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
   while (it < nitems) {
     const FluxItem item = p.items[p.item0 + it];
-    bool all_live;
-    const bool live = item_live(p, item, all_live);
+    bool all_live = false;
+    bool live = true;
+    AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.P, p.SS, item), live = false)
+    live = live && item_live(p, item, all_live);
     if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live);
     if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live); }
     if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live); }
@@ -501,6 +506,7 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
   const float gam = (float)p.gamma;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
+    AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = load_dom(p.doms + ci.dom);
     if (!p.active[dm.block0 + ci.blk]) continue;
     int o[3];
@@ -771,6 +777,7 @@ __global__ void activate_kernel(ActParams p) {
 __global__ void __launch_bounds__(256) flag_steady_kernel(FlagParams p) {
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const CellItem ci = p.items[it];
+    AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = load_dom(p.doms + ci.dom);
     int o[3];
     block_coords(dm, ci.blk, o);

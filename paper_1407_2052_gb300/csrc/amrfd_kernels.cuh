@@ -25,6 +25,7 @@ struct SpeedParams {
   int exact;                    // 0: publish lower bounds only; 1: exact maxima of the candidates
   double* W;                    // bounds pass: also write the derived quantities of U (or nullptr)
   double gm1;
+  int ndom;
 };
 
 // One flux pass: L_d(U^(k)) for the items' lines.
@@ -50,6 +51,8 @@ struct FluxParams {
   int limo3;                    // reconstruction: 0 MP5, 1 LIMO3
   double limo3_r;               // LIMO3 radius of the asymptotic region
   const double* W;              // derived quantities of Uk in active blocks (nullptr: compute)
+  unsigned* err;                // error word (checked builds)
+  int ndom;
 };
 
 // One stage combination, optionally with the speeds of the new state.
@@ -75,6 +78,7 @@ struct CombParams {
   int final_stage;
   double* W;                    // derived quantities of the output state (or nullptr)
   double gm1;
+  int ndom;
 };
 
 struct DtParams {
@@ -126,6 +130,8 @@ struct AdjFluxParams {
   int P, SSa, SSg;
   int glm;
   const unsigned short* tape;   // limiter pieces recorded by the forward pass of this stage
+  unsigned* err;                // error word (checked builds)
+  int ndom;
 };
 
 // Transposed stage combination.
@@ -143,6 +149,8 @@ struct AdjCombParams {
   int kin;                      // index of the stage input U^(i-1)
   int ndim;
   int nv;
+  unsigned* err;                // error word (checked builds)
+  int ndom;
 };
 
 // Dynamic activation (App. C): one pass of the safety belt over all blocks.
@@ -157,6 +165,8 @@ struct ActParams {
 
 // Steady-state criterion: clears flag[b] when a cell of block b is farther than tol from R.
 struct FlagParams {
+  unsigned* err;                // error word (checked builds)
+  int ndom;
   const DomDev* doms;
   const CellItem* items;         // every block's cell items
   int nitems;
