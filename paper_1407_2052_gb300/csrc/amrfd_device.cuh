@@ -141,7 +141,13 @@ __device__ __forceinline__ double dscale(double x) {
   return r;
 }
 
-__device__ __forceinline__ double dneg(double x) { return bitsd(dbits(x) ^ (long long)0x8000000000000000ULL); }
+// -x by flipping the sign bit (in PTX: the compiler would otherwise emit an FP64 add)
+__device__ __forceinline__ double dneg(double x) {
+  double r;
+  asm("{\n\t.reg .b64 t;\n\tmov.b64 t, %1;\n\txor.b64 t, t, 0x8000000000000000;\n\tmov.b64 %0, t;\n\t}"
+      : "=d"(r) : "d"(x));
+  return r;
+}
 
 // |x| rounded toward zero to FP32, from the bits of |x| whose exponent lies in
 // [2^-60, 2^61) (caller checks): the mantissa's top 23 bits and a rebiased exponent.

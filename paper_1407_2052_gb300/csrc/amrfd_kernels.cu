@@ -228,7 +228,7 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
     if (odd) {
 #pragma unroll
       for (int v = 0; v < NV; v++)
-        if ((odd >> v) & 1u) u[v] = -u[v];
+        if ((odd >> v) & 1u) u[v] = dneg(u[v]);
     }
     // derived quantities: stored by the pass that produced U^(k) for active cells;
     // recomputed for passive neighbours (U^n) and mirror images
