@@ -44,6 +44,14 @@ __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_doub
 // doubles back into FP64 compares, negations or multiplies.
 
 // Monotone signed-integer key of a double (total order; -0 sorts before +0).
+// Bit pattern of |x| (in PTX: masking the sign of a double's bits in C++ is turned by
+// the compiler into an FP64 add with an absolute-value operand).
+__device__ __forceinline__ long long abits(double x) {
+  long long r;
+  asm("{\n\t.reg .b64 t;\n\tmov.b64 t, %1;\n\tand.b64 %0, t, 0x7fffffffffffffff;\n\t}" : "=l"(r) : "d"(x));
+  return r;
+}
+
 __device__ __forceinline__ long long okey(double x) {
   long long b = dbits(x);
   return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
@@ -171,13 +179,20 @@ static __device__ __noinline__ bool mp_accept_slow(double X, double mp, double e
 // truncated to 23 bits, three FP32 roundings, the two FP64 roundings), and only
 // an estimate within the bound of eps falls back to the FP64 evaluation.
 __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
-  const long long bx = dbits(X), bm = dbits(mp);
-  const long long M = 0x7fffffffffffffffLL;
-  const long long ax = bx & M, am = bm & M;
-  if (ax == 0) return true;                       // X = +-0: product +-0
-  const long long kx = okey(X), km = okey(mp);
-  if (kx == km) return true;                      // X == mp: zero difference
-  if ((kx > km) != (bx >= 0)) return true;        // X and X - mp of opposite sign: product <= 0
+  long long ax, am;
+  unsigned quick, opp;
+  // sign analysis on the bit patterns: X = +-0 (product +-0), X == mp (zero
+  // difference), or X and X - mp of opposite sign (product <= 0) accept at once
+  asm("{\n\t.reg .b64 bx, bm, kx, km;\n\t.reg .pred p, q, r;\n\t"
+      "mov.b64 bx, %4;\n\tmov.b64 bm, %5;\n\t"
+      "and.b64 %0, bx, 0x7fffffffffffffff;\n\tand.b64 %1, bm, 0x7fffffffffffffff;\n\t"
+      AMRFD_OKEY("kx", "bx") AMRFD_OKEY("km", "bm")
+      "setp.eq.s64 p, %0, 0;\n\tsetp.eq.s64 q, kx, km;\n\tor.pred p, p, q;\n\t"
+      "setp.gt.s64 q, kx, km;\n\tsetp.ge.s64 r, bx, 0;\n\txor.pred q, q, r;\n\tor.pred p, p, q;\n\t"
+      "selp.u32 %2, 1, 0, p;\n\t"
+      "xor.b64 kx, bx, bm;\n\tsetp.lt.s64 q, kx, 0;\n\tselp.u32 %3, 1, 0, q;\n\t}"
+      : "=l"(ax), "=l"(am), "=r"(quick), "=r"(opp) : "d"(X), "d"(mp));
+  if (quick) return true;
   const int ex = (int)(ax >> 52), em = (int)(am >> 52);
   const bool in_range = ex >= 963 && ex <= 1083 && (am == 0 || (em >= 963 && em <= 1083));
   if (in_range) {
@@ -185,7 +200,7 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
     const float fm0 = am == 0 ? 0.0f : f32_trunc_abs(am);
     // |X - mp| = |X| - s mp with s = sign(X): the subtrahend keeps its magnitude, its
     // sign is flipped when mp and X have opposite signs
-    const float fm = ((bx ^ bm) < 0) ? -fm0 : fm0;
+    const float fm = opp ? -fm0 : fm0;
     const float df = fx - fm;
     const float pe = fx * df;
     const float bound = 9.5367431640625e-07f * fmaf(fx, fx + fabsf(fm), fabsf(pe));  // 2^-20 (...)
@@ -428,13 +443,12 @@ __device__ __forceinline__ double char_speed_exact(const Prim& w, double gamma, 
 // FP32 conversion of x (truncation, relative error < 2^-23) when |x| lies in
 // [2^-100, 2^100] or x is zero; ok = false otherwise.
 __device__ __forceinline__ float f32_of(double x, bool& ok) {
-  const long long b = dbits(x);
-  const long long ax = b & 0x7fffffffffffffffLL;
+  const long long ax = abits(x);
   if (ax == 0) return 0.0f;
   const int e = (int)(ax >> 52);
   if (e < 923 || e > 1123) { ok = false; return 0.0f; }
   const float f = f32_trunc_abs(ax);
-  return b < 0 ? -f : f;
+  return ax != dbits(x) ? -f : f;
 }
 
 // Bounds lo <= c_d <= up of the exact characteristic speeds of a cell (d < ndim), and
