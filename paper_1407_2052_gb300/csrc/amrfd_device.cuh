@@ -36,7 +36,14 @@ __device__ __forceinline__ bool cell_item_ok(const DomDev* doms, int ndom, const
 }
 
 // ---------------------------------------------------------------- exact helpers
-__device__ __forceinline__ long long dbits(double x) { return __double_as_longlong(x); }
+// Bit pattern of x through an opaque PTX move, so that integer tests on it stay on the
+// integer pipe (from a plain reinterpretation the compiler rebuilds FP64 compares,
+// absolute values and negations).
+__device__ __forceinline__ long long dbits(double x) {
+  long long r;
+  asm("mov.b64 %0, %1;" : "=l"(r) : "d"(x));
+  return r;
+}
 __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_double(b); }
 
 // The helpers below are written in inline PTX so that they stay on the integer
@@ -49,6 +56,13 @@ __device__ __forceinline__ double bitsd(long long b) { return __longlong_as_doub
 __device__ __forceinline__ long long abits(double x) {
   long long r;
   asm("{\n\t.reg .b64 t;\n\tmov.b64 t, %1;\n\tand.b64 %0, t, 0x7fffffffffffffff;\n\t}" : "=l"(r) : "d"(x));
+  return r;
+}
+
+// Sign bit of x as 0/1 (in PTX, for the same reason).
+__device__ __forceinline__ unsigned sbit(double x) {
+  unsigned r;
+  asm("{\n\t.reg .b64 t;\n\tmov.b64 t, %1;\n\tshr.u64 t, t, 63;\n\tcvt.u32.u64 %0, t;\n\t}" : "=r"(r) : "d"(x));
   return r;
 }
 

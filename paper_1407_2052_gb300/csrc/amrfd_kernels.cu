@@ -327,9 +327,9 @@ __device__ __forceinline__ void flux_sweep(const double* g, const double* h, int
 __device__ __forceinline__ double limo3_y(double a, double b, double esc) {
   const double eta = fma(a, a, b * b) * esc;  // >= 0: its bit pattern orders like its value
   const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
-  const long long lo = dbits(1.0 - 1e-12), hi = dbits(1.0 + 1e-12), be = dbits(eta);
+  const long long lo = __double_as_longlong(1.0 - 1e-12), hi = __double_as_longlong(1.0 + 1e-12), be = abits(eta);
   if (be <= lo) return y3;
-  const bool neg = dbits(b) < 0;
+  const bool neg = sbit(b) != 0;
   const double ap = neg ? dneg(a) : a;
   const double y3p = neg ? dneg(y3) : y3;
   const double bp = neg ? dneg(b) : b;
