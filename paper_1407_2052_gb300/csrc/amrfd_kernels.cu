@@ -324,11 +324,10 @@ __device__ __forceinline__ void flux_sweep(const double* g, const double* h, int
 // switch eta = (a^2 + b^2) / (4 (r dx)^2) (G = 2 F^{+-}) picks the unlimited value
 // inside the asymptotic region, the limited one outside, and blends linearly over
 // |eta - 1| < 1e-12.
-__device__ __forceinline__ double limo3_y(double a, double b, double esc) {
-  const double eta = fma(a, a, b * b) * esc;  // >= 0: its bit pattern orders like its value
+__device__ __forceinline__ double limo3_y(double a, double b, double s2, long long tlo, long long thi, double esc) {
   const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
-  const long long lo = __double_as_longlong(1.0 - 1e-12), hi = __double_as_longlong(1.0 + 1e-12), be = abits(eta);
-  if (be <= lo) return y3;
+  const long long bs = abits(s2);  // s2 = a^2 + b^2 >= 0: its bit pattern orders like its value
+  if (bs <= tlo) return y3;
   const bool neg = sbit(b) != 0;
   const double ap = neg ? dneg(a) : a;
   const double y3p = neg ? dneg(y3) : y3;
@@ -338,28 +337,32 @@ __device__ __forceinline__ double limo3_y(double a, double b, double esc) {
   t = imin(y3p, t);
   t = imax(0.0, t);
   const double yl = neg ? dneg(t) : t;
-  if (be >= hi) return yl;
-  const double z = (eta - 1.0) * 1e12;
+  if (bs >= thi) return yl;
+  const double z = fma(s2, esc, -1.0) * 1e12;
   return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
 }
 
 // LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep; G^+ from
-// cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k).
+// cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k). The squares of
+// the differences are carried along the line (each enters two faces' switch), and the
+// switch compares a^2 + b^2 with (1 -+ 1e-12)/esc.
 __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, int slen, double esc, double* out,
                                             long long ostr, unsigned long long wmask) {
+  const long long tlo = __double_as_longlong((1.0 - 1e-12) / esc), thi = __double_as_longlong((1.0 + 1e-12) / esc);
   double Pa = g[2] - g[1], Pb = g[3] - g[2];   // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
   double Mb = h[3] - h[2], Ma = h[4] - h[3];   // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
+  double Pa2 = Pa * Pa, Pb2 = Pb * Pb, Ma2 = Ma * Ma, Mb2 = Mb * Mb;
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
-    const double Yp = limo3_y(Pa, Pb, esc);
-    const double Ym = -limo3_y(Ma, Mb, esc);
-    const double F = fma(0.5, Yp + Ym, g[k - 1] + h[k]);
+    const double Yp = limo3_y(Pa, Pb, Pa2 + Pb2, tlo, thi, esc);
+    const double Ym = limo3_y(Ma, Mb, Ma2 + Mb2, tlo, thi, esc);
+    const double F = fma(0.5, Yp - Ym, g[k - 1] + h[k]);
     if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
     Fprev = F;
     if (k < kend) {
-      Pa = Pb; Pb = g[k + 1] - g[k];
-      Mb = Ma; Ma = h[k + 2] - h[k + 1];
+      Pa = Pb; Pa2 = Pb2; Pb = g[k + 1] - g[k]; Pb2 = Pb * Pb;
+      Mb = Ma; Mb2 = Ma2; Ma = h[k + 2] - h[k + 1]; Ma2 = Ma * Ma;
     }
   }
 }
