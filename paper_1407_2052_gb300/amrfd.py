@@ -248,9 +248,44 @@ class Solver:
                "amrfd_adjoint")
         return gU_n
 
-    def autotune(self, U, dt, stream=None):
+    def tile_key(self):
+        """Key of the autotuner cache: physics, dimensions, reconstruction, the multiset of
+        (cells, blocks) shapes and the device's SM count."""
+        import hashlib
+        import torch
+        shapes = sorted((tuple(int(x) for x in d.n), tuple(int(x) for x in d.nb)) for d in self.domains)
+        h = hashlib.sha1(repr(shapes).encode()).hexdigest()[:16]
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        return "p%d-d%d-r%d-%s-sm%d" % (self.cfg.physics, self.cfg.ndim, self.cfg.recon, h, sms)
+
+    def autotune(self, U, dt, stream=None, cache=None):
+        """amrfd_autotune; with `cache` (a JSON file path) a tile chosen before for the same
+        key (tile_key) is reused instead of timing the candidates again."""
+        import json
+        key = self.tile_key() if cache else None
+        if cache and os.path.exists(cache):
+            try:
+                known = json.load(open(cache)).get(key)
+            except (OSError, ValueError):
+                known = None
+            if known:
+                self.set_tile(*known)
+                return self.get_tile()
         _check(self._L.amrfd_autotune(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_autotune")
-        return self.get_tile()
+        tile = self.get_tile()
+        if cache:
+            data = {}
+            if os.path.exists(cache):
+                try:
+                    data = json.load(open(cache))
+                except (OSError, ValueError):
+                    data = {}
+            data[key] = list(tile)
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as fh:
+                json.dump(data, fh, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return tile
 
     def set_tile(self, seg, lines, threads):
         _check(self._L.amrfd_set_tile(self._h, seg, lines, threads), "amrfd_set_tile")

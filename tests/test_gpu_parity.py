@@ -724,3 +724,18 @@ def test_blast_full_size_200_steps_physical_and_conservative():
     assert bool(torch.isfinite(U).all())
     assert torch.all((V[:8].sum(dim=1) - tot0).abs() <= 1e-11 * scale)
     assert 0.0 < float(dt[0].item()) < 1.0
+
+
+def test_autotune_cache_reuses_the_tile(tmp_path):
+    """Solver.autotune(cache=...) times the candidates once per key and reuses the choice."""
+    w = W.blast3d(32, 8)
+    cache = str(tmp_path / "tiles.json")
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel().copy())
+    dt = s.dt(U)
+    tile = s.autotune(U, dt, cache=cache)
+    import json
+    assert json.load(open(cache)) == {s.tile_key(): list(tile)}
+    s2 = A().Solver.from_workload(w)
+    s2.set_tile(8, 1, 32)
+    assert s2.autotune(U, dt, cache=cache) == tile
