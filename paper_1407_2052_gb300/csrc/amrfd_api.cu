@@ -2,6 +2,7 @@
 // lists, per-domain (plain) and persistent (batched, graph-replayed) steps,
 // time step, tile autotuner, error latch.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -23,6 +24,15 @@ namespace {
 struct Graph {
   cudaGraphExec_t exec = nullptr;
 };
+
+// NVTX range around a host-side phase (steps, stages, time step, adjoint, activation,
+// autotuning); a no-op unless a profiler is attached.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+const char* const kStageName[kMaxStages] = {"amrfd stage 1", "amrfd stage 2", "amrfd stage 3", "amrfd stage 4",
+                                             "amrfd stage 5"};
 
 // SSPRK tables of Sec. 2.3 in Shu-Osher form, one StageCoef per stage.
 // SSPRK3 is the third-order TVD Runge-Kutta scheme of Gottlieb & Shu (1998) cited there.
@@ -455,6 +465,7 @@ int launch_dt_from(amrfd_handle* h, const unsigned long long* sl, double* dt_dev
 // step is computed here from the speeds of U^n (written to cfl_dt, then used).
 int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, bool batched,
                  double* cfl_dt = nullptr, double t = 0.0, double t_end = 0.0) {
+  Range rg("amrfd step");
   const int ph = h->cfg.physics, nv = h->nv;
   CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
   CK(cudaMemsetAsync(h->d_tlow, 0, sizeof(unsigned) * h->ns * h->ndom * 4, s));
@@ -472,6 +483,7 @@ int enqueue_step(amrfd_handle* h, double* U, const double* dt, cudaStream_t s, b
     }
   }
   for (int i = 1; i <= h->ns; i++) {
+    Range rs(kStageName[i - 1]);
     const double* Uk = (i == 1) ? U : h->d_stage[i - 1];
     FluxParams fp = flux_params(h, Uk, U, i - 1);
     CombParams cp = comb_params(h, U, dt, i);
@@ -685,6 +697,7 @@ int amrfd_flag_steady(amrfd_handle* h, const double* U, const double* U_ref, dou
 
 int amrfd_activate(amrfd_handle* h, const uint8_t* flag_dev, int belt, void* stream) {
   if (!h || !flag_dev || belt < 0) return AMRFD_ERR_INVALID_ARG;
+  Range rg("amrfd activate");
   cudaStream_t s = (cudaStream_t)stream;
   ActParams p{};
   p.doms = h->d_dom;
@@ -715,6 +728,7 @@ int amrfd_get_active(amrfd_handle* h, uint8_t* active_dev, void* stream) {
 int amrfd_dt(amrfd_handle* h, const double* U, double* dt_dev, double t, double t_end, void* stream) {
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
   cudaStream_t s = (cudaStream_t)stream;
+  Range rg("amrfd dt");
   int rc = speeds_from_scratch(h, U, kSlotDt, 1, true, std::vector<int>(), s);
   if (rc) return rc;
   return launch_dt_from(h, slot(h, kSlotDt), dt_dev, t, t_end, s);
@@ -805,6 +819,7 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
                   void* stream) {
   if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
   if (h->cfg.recon != AMRFD_MP5) return AMRFD_ERR_UNSUPPORTED;
+  Range rg("amrfd adjoint");
   cudaStream_t s = (cudaStream_t)stream;
   {
     int rc = refresh_active_host(h, s);
@@ -947,6 +962,7 @@ int amrfd_get_tile(const amrfd_handle* h, int* seg, int* lines, int* threads) {
 int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* stream) {
   if (!h || !U || !dt_dev) return AMRFD_ERR_INVALID_ARG;
   (void)dt_dev;
+  Range rg("amrfd autotune");
   cudaStream_t s = (cudaStream_t)stream;
   // sample state speeds (slot 0) so that the flux pass sees realistic c_max
   {
