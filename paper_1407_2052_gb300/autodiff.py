@@ -67,3 +67,8 @@ class _Rollout(torch.autograd.Function):
 def rollout(solver, U0, dt, nsteps, every):
     """U after `nsteps` fixed-dt steps, differentiable w.r.t. U0 (checkpoint every `every` steps)."""
     return _Rollout.apply(U0, dt, solver, nsteps, every)
+
+
+def checkpointed_rollout(solver, U0, dt, nsteps, k):
+    """Alias of rollout: nsteps fixed-dt steps with checkpoints every k steps."""
+    return rollout(solver, U0, dt, nsteps, k)

@@ -739,3 +739,44 @@ def test_autotune_cache_reuses_the_tile(tmp_path):
     s2 = A().Solver.from_workload(w)
     s2.set_tile(8, 1, 32)
     assert s2.autotune(U, dt, cache=cache) == tile
+
+
+# ------------------------------------------------------------------ degenerate cases
+def test_all_passive_is_a_no_op():
+    """Every block passive: the step leaves the state bitwise unchanged on both paths and
+    through amrfd_step_cfl, and the time step is t_end - t (no active cell limits it)."""
+    w = W.blast3d(32, 8)
+    w.active = np.zeros(64, np.uint8)
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel().copy())
+    dt = s.dt(U, 0.25, 1.0)
+    assert float(dt[0].item()) == 0.75
+    s.step_batched(U, dt)
+    s.step(U, dt)
+    s.step_cfl(U, 0.5, 1.0)
+    assert s.error() == A().OK
+    assert np.array_equal(U.cpu().numpy(), w.U.ravel())
+
+
+@pytest.mark.parametrize("physics,ndim,n", [(O.EULER, 3, (3, 3, 3)), (O.EULER, 2, (3, 5, 1)),
+                                            (O.MHD_GLM, 3, (3, 4, 3)), (O.MHD_GLM, 1, (3, 1, 1))])
+def test_smallest_periodic_boxes(physics, ndim, n):
+    """Periodic directions of three cells, the smallest allowed: the halo wraps more than
+    once around the box (ghost -3 is cell 0 of the same line)."""
+    bc = ((O.PERIODIC, O.PERIODIC),) * 3
+    w = _smooth_domain(physics, ndim, n, bc, seed=70 + ndim)
+    for batched in (True, False):
+        s, U, dts = run_gpu(w, 2, batched=batched)
+        ref, odts = run_oracle(w, 2)
+        assert float(dts[0][0].item()) == odts[0]
+        assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+def test_single_cell_lines_with_outflow_and_mirror():
+    """Outflow and mirror faces on lines of three cells along every direction of a 3D box."""
+    w = _smooth_domain(O.MHD_GLM, 3, (3, 3, 3), ((1, 2), (2, 1), (1, 1)), seed=77)
+    w.domains[0].asym = ((0, 0x1A2), (0x1A4, 0), (0, 0))
+    s, U, dts = run_gpu(w, 2)
+    ref, odts = run_oracle(w, 2)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
