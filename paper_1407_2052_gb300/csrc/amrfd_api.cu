@@ -178,7 +178,12 @@ int build_items(amrfd_handle* h) {
   std::vector<int> c_owner, c_one, c_beg, c_cnt;
   h->dom_fbeg.assign(h->ndom, -1); h->dom_fend.assign(h->ndom, -1);
   h->dom_cbeg.assign(h->ndom, -1); h->dom_cend.assign(h->ndom, -1);
-  const int cell_chunk = 4096;
+  // cell items of at most 4096 cells, smaller when the domains are few and large so that
+  // the cell-wise passes still get about eight items per SM
+  long long total_cells = 0;
+  for (int g = 0; g < h->nblocks; g++) total_cells += bsize[g];
+  const long long want = (total_cells + 8LL * h->nsm - 1) / (8LL * h->nsm);
+  const int cell_chunk = (int)std::max<long long>(256, std::min<long long>(4096, (want + 255) / 256 * 256));
   for (int pos = 0; pos < h->nblocks; pos++) {
     const int g = ord[pos], d = bdom[g], b = bloc[g];
     const DomDev& dm = h->hdom[d];
