@@ -780,3 +780,16 @@ def test_single_cell_lines_with_outflow_and_mirror():
     ref, odts = run_oracle(w, 2)
     assert float(dts[0][0].item()) == odts[0]
     assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+@pytest.mark.parametrize("n,nb", [((32760, 1, 1), (1, 1, 1)), ((4096, 4096, 1), (1, 1, 1))])
+def test_longest_blocks_one_step(n, nb):
+    """Blocks at the longest edges the work items address (32760 cells in one 1D block;
+    one 4096^2 block): one step against the oracle element by element."""
+    ndim = 1 if n[1] == 1 else 2
+    bc = ((O.OUTFLOW, O.OUTFLOW), (O.PERIODIC, O.PERIODIC), (0, 0))
+    w = _smooth_domain(O.EULER, ndim, n, bc, seed=90 + ndim, nb=nb)
+    s, U, dts = run_gpu(w, 1)
+    ref, odts = run_oracle(w, 1)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
