@@ -396,22 +396,43 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     graph_ms = e0.elapsed_time(e1) / args.steps
 
-    # ---- end to end through the public API with host buffers (pinned)
+    # ---- end to end through the public API with host buffers (pinned): every step copies
+    # its input state host -> device and its result device -> host. Two device buffers and
+    # a copy stream let step i's copies overlap the neighbouring steps' compute.
     hU = U0.cpu().pin_memory()
-    hout = torch.empty_like(hU).pin_memory()
+    houts = [torch.empty_like(hU).pin_memory() for _ in range(2)]
     nbytes = hU.numel() * 8
-    for _ in range(2):
-        U.copy_(hU, non_blocking=True)
-        one_step()
-        hout.copy_(U, non_blocking=True)
+    bufs = [U, torch.empty_like(U)]
+    cstream = torch.cuda.Stream()
+    dts = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in range(2)]
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+    ev_free = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_steps(k):
+        for i in range(k):
+            b = i & 1
+            with torch.cuda.stream(cstream):
+                if i >= 2:
+                    cstream.wait_event(ev_free[b])
+                bufs[b].copy_(hU, non_blocking=True)
+                ev_in[b].record(cstream)
+            stream.wait_event(ev_in[b])
+            s.step_cfl(bufs[b], out=dts[b])
+            ev_out[b].record(stream)
+            with torch.cuda.stream(cstream):
+                cstream.wait_event(ev_out[b])
+                houts[b].copy_(bufs[b], non_blocking=True)
+                ev_free[b].record(cstream)
+        stream.wait_stream(cstream)
+
+    e2e_steps(2)
     barrier()
     e0.record(stream)
-    for _ in range(args.steps):
-        U.copy_(hU, non_blocking=True)
-        one_step()
-        hout.copy_(U, non_blocking=True)
+    e2e_steps(args.steps)
     e1.record(stream)
     barrier()
+    assert torch.equal(houts[(args.steps - 1) & 1], bufs[(args.steps - 1) & 1].cpu())
     e2e_ms = e0.elapsed_time(e1)
     _, e2e_value = aggregate(e2e_ms, ncell, args.steps, world, dist, "cuda")
 
@@ -456,12 +477,14 @@ def run_ours(args, rank, world, local_rank):
                          "frac_flux": flux_gbs / hbm_peak, "peak_source": "MEASURED_PEAKS.json hbm_gbs",
                          "frac_step_of_nominal_7900": value / world * BYTES_PER_CELL_UPDATE / 1e9 / 7900.0},
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+                "d2h_bytes_per_step": nbytes,
+                "note": "pinned host buffers; each step's H2D and D2H copies run on a copy stream "
+                        "overlapping the neighbouring steps' compute (two device buffers)"},
         "clocks": clocks,
     }
     tile = list(s.get_tile())
     s.close()
-    del U, U0
+    del U, U0, bufs, houts, hU
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
         out["batched"] = batched_extra(torch, A, W)
