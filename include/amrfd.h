@@ -150,7 +150,8 @@ int amrfd_step(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
 /* Same update as amrfd_step, bitwise identical, issued as one persistent launch
    per pass over a device-side work list of active (block, tile) items sorted
    largest first; the whole step is replayed from a CUDA graph captured on the
-   first call for a given (U, dt_dev) pair. */
+   first call for a given (U, dt_dev) pair (the 16 most recently used pairs are
+   kept; evicting one synchronises `stream` once). */
 int amrfd_step_batched(amrfd_handle *h, double *U, const double *dt_dev, void *stream);
 
 /* One CFL-limited step: writes dt_dev[ndomain] (device) exactly as

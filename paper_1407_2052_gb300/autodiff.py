@@ -14,9 +14,13 @@ class AmrfdStep(torch.autograd.Function):
     def forward(ctx, U, dt, solver):
         ctx.solver = solver
         ctx.save_for_backward(U, dt)
-        out = U.detach().clone()
-        solver.step_batched(out, dt)
-        return out
+        # step a buffer kept on the solver, so that repeated calls replay one captured graph
+        buf = getattr(solver, "_step_buf", None)
+        if buf is None or buf.shape != U.shape or buf.device != U.device:
+            buf = solver._step_buf = torch.empty_like(U)
+        buf.copy_(U.detach())
+        solver.step_batched(buf, dt)
+        return buf.clone()
 
     @staticmethod
     def backward(ctx, g):
@@ -50,14 +54,16 @@ class _Rollout(torch.autograd.Function):
         solver, nsteps, every = ctx.solver, ctx.nsteps, ctx.every
         g = g.contiguous().clone()
         gn = torch.empty_like(g)
+        # one set of state buffers for every segment: the recomputation steps run on the
+        # same addresses each time, so their captured graphs are replayed
+        states = [torch.empty_like(g) for _ in range(min(every, nsteps))]
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
             count = min(every, nsteps - start)
-            states = [ctx.ckpts[seg].clone()]
-            for _ in range(count - 1):
-                nxt = states[-1].clone()
-                solver.step_batched(nxt, dt)
-                states.append(nxt)
+            states[0].copy_(ctx.ckpts[seg])
+            for j in range(1, count):
+                states[j].copy_(states[j - 1])
+                solver.step_batched(states[j], dt)
             for j in reversed(range(count)):
                 solver.adjoint(states[j], dt, g, gn)
                 g, gn = gn, g

@@ -23,7 +23,9 @@ namespace {
 
 struct Graph {
   cudaGraphExec_t exec = nullptr;
+  unsigned long long used = 0;      // last use (LRU eviction)
 };
+constexpr size_t kMaxGraphs = 16;   // captured steps kept per handle
 
 // NVTX range around a host-side phase (steps, stages, time step, adjoint, activation,
 // autotuning); a no-op unless a profiler is attached.
@@ -132,6 +134,7 @@ struct amrfd_handle {
   std::vector<int> tkind;
   int tused = 0;
   std::map<std::pair<const void*, const void*>, Graph> graphs;
+  unsigned long long graph_clock = 0;
 };
 
 namespace {
@@ -758,6 +761,15 @@ int amrfd_step_batched(amrfd_handle* h, double* U, const double* dt_dev, void* s
   auto key = std::make_pair((const void*)U, (const void*)dt_dev);
   auto itg = h->graphs.find(key);
   if (itg == h->graphs.end()) {
+    if (h->graphs.size() >= kMaxGraphs) {
+      // evict the least recently used capture (after the work queued so far)
+      auto lru = h->graphs.begin();
+      for (auto it = h->graphs.begin(); it != h->graphs.end(); ++it)
+        if (it->second.used < lru->second.used) lru = it;
+      CK(cudaStreamSynchronize(s));
+      cudaGraphExecDestroy(lru->second.exec);
+      h->graphs.erase(lru);
+    }
     // capture on a private stream, ordered after the caller's work through events
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
@@ -771,6 +783,7 @@ int amrfd_step_batched(amrfd_handle* h, double* U, const double* dt_dev, void* s
     CK(e);
     itg = h->graphs.emplace(key, gr).first;
   }
+  itg->second.used = ++h->graph_clock;
   CK(cudaGraphLaunch(itg->second.exec, s));
   return AMRFD_OK;
 }
