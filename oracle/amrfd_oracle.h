@@ -9,6 +9,12 @@
  * CPU-baseline leg and the smoke check may call it. It shares no code, header,
  * table or constant with the CUDA library under paper_1407_2052_gb300/.
  *
+ * Parity unpinned (these follow stated readings of the paper; no check against
+ * anything but this code fixes them): the value eps = 1e-10 of the MP5 acceptance
+ * test, the scope of the splitting speed (per direction, per RK stage, over active
+ * cells), the unsplit multi-D time step, the GLM damping length c_r = 0.18 and the
+ * GLM speed frozen over a step, and LIMO3's switch radius r and blend width.
+ *
  * State layout: one domain is an interior-only array U[v][z][y][x], x fastest,
  * with n[0]*n[1]*n[2] cells per variable (unused dimensions have n = 1).
  *   Euler  (nv = 2 + ndim): rho, m_1..m_ndim, E
