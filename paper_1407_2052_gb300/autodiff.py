@@ -54,16 +54,20 @@ class _Rollout(torch.autograd.Function):
         solver, nsteps, every = ctx.solver, ctx.nsteps, ctx.every
         g = g.contiguous().clone()
         gn = torch.empty_like(g)
-        # one set of state buffers for every segment: the recomputation steps run on the
-        # same addresses each time, so their captured graphs are replayed
+        # the recomputation steps one work buffer (one captured graph, replayed) and keeps
+        # a copy of every state of the segment for the reverse sweep
         states = [torch.empty_like(g) for _ in range(min(every, nsteps))]
+        wb = getattr(solver, "_step_buf", None)
+        if wb is None or wb.shape != g.shape or wb.device != g.device:
+            wb = solver._step_buf = torch.empty_like(g)
         for seg in reversed(range(len(ctx.ckpts))):
             start = seg * every
             count = min(every, nsteps - start)
-            states[0].copy_(ctx.ckpts[seg])
-            for j in range(1, count):
-                states[j].copy_(states[j - 1])
-                solver.step_batched(states[j], dt)
+            wb.copy_(ctx.ckpts[seg])
+            for j in range(count):
+                states[j].copy_(wb)
+                if j + 1 < count:
+                    solver.step_batched(wb, dt)
             for j in reversed(range(count)):
                 solver.adjoint(states[j], dt, g, gn)
                 g, gn = gn, g
