@@ -106,18 +106,6 @@ __device__ __forceinline__ double iminmod(double a, double b) {
   return r;
 }
 
-// minmod of four arguments: signed smallest magnitude if all share a sign, else 0.
-__device__ __forceinline__ double iminmod4(double w, double x, double y, double z) {
-  long long bw = dbits(w), bx = dbits(x), by = dbits(y), bz = dbits(z);
-  const long long M = 0x7fffffffffffffffLL;
-  long long m = bw & M, t;
-  t = bx & M; m = t < m ? t : m;
-  t = by & M; m = t < m ? t : m;
-  t = bz & M; m = t < m ? t : m;
-  bool mixed = ((bw ^ bx) | (bw ^ by) | (bw ^ bz)) < 0;
-  return mixed ? 0.0 : bitsd(m | (bw & ~M));
-}
-
 // median(x, y, z) -- one of its arguments, no rounding
 __device__ __forceinline__ double imedian(double x, double y, double z) {
   return imax(imin(x, y), imin(imax(x, y), z));
@@ -589,14 +577,6 @@ __device__ __forceinline__ void split_flux_w(const double* u, const double* w, d
     gp[v] = fma(alpha, u[v], f[v]);
     gm[v] = fma(-alpha, u[v], f[v]);
   }
-}
-
-template <int PHYS, int NV, int D>
-__device__ __forceinline__ void split_flux(const double* u, double gm1, double alpha, double ch2,
-                                           double* gp, double* gm) {
-  double w[NumW<PHYS, NV>::value];
-  prim_w<PHYS, NV>(u, gm1, w);
-  split_flux_w<PHYS, NV, D>(u, w, alpha, ch2, gp, gm);
 }
 
 // ------------------------------------------------------------- block reductions
