@@ -318,6 +318,25 @@ def brio_wu(n=512):
                     extra={"x": x})
 
 
+def brio_wu2d(n=128):
+    """The Brio-Wu states (Sec. 4.5.2) in bands along the diagonal of the periodic box
+    [-1,1]^2: left state where (x + y) mod 2 < 1, else right (two tubes per period, one of
+    them mirrored), B_parallel = 0.75 along (1,1)/sqrt(2), B_perp = +-1 along
+    (-1,1)/sqrt(2), gamma 5/3, SSPRK(5,4), CFL 0.4."""
+    x, dx = centres(n, -1.0, 1.0)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    left = np.mod(X + Y + 2.0, 2.0) < 1.0
+    rho = np.where(left, 1.0, 0.125)
+    p = np.where(left, 1.0, 0.1)
+    bt = np.where(left, 1.0, -1.0)
+    r2 = 1.0 / np.sqrt(2.0)
+    zero = np.zeros_like(X)
+    B = [0.75 * r2 - bt * r2, 0.75 * r2 + bt * r2, zero]
+    U = conserved_mhd(rho, [zero, zero, zero], p, B, 5.0 / 3.0).reshape(9, 1, n, n)
+    dom = Domain((n, n, 1), (dx, dx, 1.0))
+    return Workload("briowu2d", MHD_GLM, 2, SSPRK54, 5.0 / 3.0, 0.4, [dom], U)
+
+
 def random_states(rng, n, physics, ndim, gamma, beta_min=0.05):
     """n random physical cell states (for point-wise tests), shape (nv, n)."""
     rho = rng.uniform(0.2, 3.0, n)

@@ -793,3 +793,14 @@ def test_longest_blocks_one_step(n, nb):
     ref, odts = run_oracle(w, 1)
     assert float(dts[0][0].item()) == odts[0]
     assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
+
+
+def test_brio_wu_rotated_2d():
+    """The Brio-Wu states in diagonal bands of a periodic 2D box (MHD shocks, compound
+    waves and contacts across both directions at once), 128^2, 60 SSPRK(5,4) steps: first
+    dt bitwise, relative L1 <= 1e-10."""
+    w = W.brio_wu2d(128)
+    s, U, dts = run_gpu(w, 60)
+    ref, odts = run_oracle(w, 60)
+    assert float(dts[0][0].item()) == odts[0]
+    assert rel_l1(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-10
