@@ -386,8 +386,9 @@ def run_ours(args, rank, world, local_rank):
             gpu_index = int(vis.split(",")[local_rank])
     except ValueError:
         pass
-    clk_path = os.path.join(ROOT, "gpurun_out", "clocks_bench_rank%d.csv" % rank) if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else "/tmp/amrfd_clocks_rank%d.csv" % rank
+    import tempfile
+    clk_dir = args.clocks_dir or tempfile.gettempdir()
+    clk_path = os.path.join(clk_dir, "clocks_bench_rank%d.csv" % rank)
     proc, fh = clocks_sampler(clk_path)
     s.timing_begin(16 * args.steps + 16)
     barrier()
@@ -536,6 +537,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default flux-pass tile")
     ap.add_argument("--tile", default="", help="seg,lines,threads of the flux pass (skips autotuning)")
     ap.add_argument("--n", type=int, default=N_BLAST, help="cells per side of the blast (profiling of small cases)")
+    ap.add_argument("--clocks-dir", default="", help="where to keep the nvidia-smi clock samples (default: temp dir)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
