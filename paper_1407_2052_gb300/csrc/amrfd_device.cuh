@@ -196,6 +196,8 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
       : "=l"(ax), "=l"(am), "=r"(quick), "=r"(opp) : "d"(X), "d"(mp));
   if (quick) return true;
   const int ex = (int)(ax >> 52), em = (int)(am >> 52);
+  // |X|, |mp| < 2^-60: fl(X - mp) <= 2^-59 and the product is at most 2^-119
+  if (ex < 963 && em < 963 && dbits(eps) >= (904LL << 52)) return true;
   const bool in_range = ex >= 963 && ex <= 1083 && (am == 0 || (em >= 963 && em <= 1083));
   if (in_range) {
     const float fx = f32_trunc_abs(ax);
@@ -277,6 +279,45 @@ __device__ __forceinline__ double dm4(double ka, double kb) {
       "selp.b64 x, 0, x, q;\n\tmov.b64 %0, x;\n\t}"
       : "=d"(r) : "d"(sm), "d"(t));
   return r;
+}
+
+// mp5_rel2 that also reports whether the acceptance test failed (rej). CARRY takes
+// the curvature-limited second differences Mp, Mm from the caller (carried along the
+// line); otherwise they are formed here, only when the test fails, from the curvatures
+// of cells i-1, i, i+1 with the operands and order of the carried ones (for NEG, of
+// the mirrored stencil), so both forms give the same result.
+template <bool NEG, bool CARRY>
+__device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
+                                             double eps16, bool& rej) {
+  constexpr double sg = NEG ? -1.0 : 1.0;
+  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
+                   c6 = sg * (6.0 / 60.0);
+  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));  // 2 (f_or - f_i)
+  X = fma(-c6, Dp, X);
+  const double d0 = NEG ? dneg(D0) : D0;
+  const double d1 = NEG ? dneg(D1) : D1;
+  const double ul = dscale<3>(d0);     // 2 (f_ul - f_i)
+  const double d1x2 = dscale<1>(d1);   // 2 (f_{i+1} - f_i)
+  const double mp = iminmod(d1x2, ul);  // 2 (f_mp - f_i)
+  rej = false;
+  if (mp_accept(X, mp, eps16)) return X;
+  rej = true;
+  if (!CARRY) {
+    if (!NEG) {
+      const double k0 = D1 - D0;
+      Mp = dm4(k0, Dp - D1);
+      Mm = dm4(D0 - Dm, k0);
+    } else {
+      const double k0 = D0 - D1;
+      Mp = dm4(D1 - Dp, k0);
+      Mm = dm4(k0, Dm - D0);
+    }
+  }
+  const double md = d1 - Mp;                  // 2 (f_md - f_i)
+  const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
+  const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
+  const double fmax = imin(imax(imax(0.0, d1x2), md), imax(imax(0.0, ul), lc));
+  return imedian(X, fmin, fmax);
 }
 
 // ------------------------------------------------ selection-tracking variants
@@ -453,6 +494,18 @@ __device__ __forceinline__ float f32_of(double x, bool& ok) {
   return ax != dbits(x) ? -f : f;
 }
 
+// As f32_of for a momentum or field component, except that a nonzero |x| < 2^-100
+// gives 0 and sets flushed (the caller bounds the effect of the change).
+__device__ __forceinline__ float f32_of_flush(double x, bool& ok, bool& flushed) {
+  const long long ax = abits(x);
+  if (ax == 0) return 0.0f;
+  const int e = (int)(ax >> 52);
+  if (e < 923) { flushed = true; return 0.0f; }
+  if (e > 1123) { ok = false; return 0.0f; }
+  const float f = f32_trunc_abs(ax);
+  return ax != dbits(x) ? -f : f;
+}
+
 // Bounds lo <= c_d <= up of the exact characteristic speeds of a cell (d < ndim), and
 // of its CFL rate sum_d c_d/dx_d (index 3), from an FP32 evaluation. The relative
 // error of every FP32 quantity is bounded by the input truncation (2^-23 each), the
@@ -461,21 +514,30 @@ __device__ __forceinline__ float f32_of(double x, bool& ok) {
 // the discriminant of the fast speed is formed as (a^2 - b_d^2)^2 + b_t^2 (b_t^2 +
 // 2 (a^2 + b_d^2)) (b_t the transverse Alfven speed), a sum of non-negative terms,
 // so the square roots do not amplify it. The bound used, 2^-17 (T/S + 1), holds with
-// a margin of four. force = true when no bound is claimed (non-physical or out of
-// FP32 range): the caller then evaluates the cell exactly.
+// a margin of four. Momentum and field components below 2^-100 in magnitude (the
+// exactly-zero components of a uniform state pick up such values ahead of a wave)
+// enter as 0. Each such change moves c_d = |v_d| + c_f by at most 2^-100 (1.5 +
+// gamma) (1/rho + 1/sqrt(rho)): c_f is 1-Lipschitz in the sound speed a and in
+// b_d = |B_d|/sqrt(rho), 1.5-Lipschitz in the transverse b_t, and a moves by at most
+// the square root of the change of a^2. With at most six such components, with
+// T/S < 2^10 (FP32 a^2 then within 2^-10 of its value) and with
+// (1.5 + gamma)(1/rho + 1/sqrt(rho))/a <= 2^76, the total is below 2^-21 c_d, and
+// the bounds widen by 2^-20 relative; otherwise the cell is evaluated exactly.
+// force = true when no bound is claimed (non-physical or out of FP32 range): the
+// caller then evaluates the cell exactly.
 template <int PHYS, int NV>
 __device__ __forceinline__ void speed_bounds(const double* u, float gam, int ndim, const float* rdx, bool want_rate,
                                              float up[4], float lo[4], bool& force) {
-  bool ok = true;
+  bool ok = true, fl = false;
   const float rho = f32_of(u[0], ok);
   constexpr int nm = PHYS == PH_EULER ? NV - 2 : 3;
   float m[3] = {0.f, 0.f, 0.f}, B[3] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int k = 0; k < nm; k++) m[k] = f32_of(u[1 + k], ok);
+  for (int k = 0; k < nm; k++) m[k] = f32_of_flush(u[1 + k], ok, fl);
   const float E = f32_of(u[PHYS == PH_EULER ? NV - 1 : 4], ok);
   if (PHYS == PH_MHD) {
 #pragma unroll
-    for (int k = 0; k < 3; k++) B[k] = f32_of(u[5 + k], ok);
+    for (int k = 0; k < 3; k++) B[k] = f32_of_flush(u[5 + k], ok, fl);
   }
   if (PHYS == PH_MHD && ((dbits(u[8]) >> 52) & 0x7ff) == 0x7ff) ok = false;  // psi not finite
   force = !ok || !(rho > 0.0f) || !(E > 0.0f);
@@ -488,8 +550,13 @@ __device__ __forceinline__ void speed_bounds(const double* u, float gam, int ndi
   const float half = 0.5f * (ke2 + b2);
   const float T = E + half, S = E - half;
   if (!(S > 1.9073486e-6f * T)) { force = true; return; }  // S <= 2^-19 T: too uncertain
-  const float rel = 7.6293945e-6f * fmaf(T, __frcp_rn(S), 1.0f);  // 2^-17 (T/S + 1)
-  const float a2 = gam * (gam - 1.0f) * S * ir;                   // gamma p / rho
+  float rel = 7.6293945e-6f * fmaf(T, __frcp_rn(S), 1.0f);  // 2^-17 (T/S + 1)
+  const float a2 = gam * (gam - 1.0f) * S * ir;             // gamma p / rho
+  if (fl) {
+    const float q = (1.5f + gam) * (ir + sqrtf(ir)) / sqrtf(a2);
+    if (!(S > 9.765625e-4f * T) || !(q <= 7.5557864e22f)) { force = true; return; }  // 2^-10, 2^76
+    rel += 9.5367431640625e-07f;                                                   // 2^-20
+  }
   float rate_up = 0.0f, rate_lo = 0.0f;
 #pragma unroll
   for (int d = 0; d < 3; d++) {

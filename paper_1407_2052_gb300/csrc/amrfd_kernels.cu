@@ -252,13 +252,14 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 // line's extended index (cell j = k-1 left of face k), then the flux difference
 // Fsum_{k-1} - Fsum_k of the segment's cell k-4 stored to out[(k-4) ostr] where
 // wmask has its bit (the factor 1/(2 dx) is applied by the stage combination).
-// REC additionally records, per face and bias, which linear piece the limiter took
+// The curvature-limited second differences are carried along the line. REC
+// additionally records, per face and bias, which linear piece the limiter took
 // (3 bits) and the pieces of the two curvature limiters it read (3 bits each):
 // tp/tm point at the line's records, face k goes to index f0 + k - 3 if below fend.
 template <bool REC>
-__device__ __forceinline__ void flux_sweep(const double* g, const double* h, int slen, double eps16, unsigned short* tp,
-                                           unsigned short* tm, int f0, int fend, double* out, long long ostr,
-                                           unsigned long long wmask) {
+__device__ __forceinline__ void flux_sweep_carry(const double* g, const double* h, int slen, double eps16,
+                                                 unsigned short* tp, unsigned short* tm, int f0, int fend,
+                                                 double* out, long long ostr, unsigned long long wmask) {
   int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
   double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
@@ -315,6 +316,66 @@ __device__ __forceinline__ void flux_sweep(const double* g, const double* h, int
   (void)Mk3;
 }
 
+// Plain MP5 sweep, same fluxes as flux_sweep_carry. The curvature-limited second
+// differences serve only faces that fail the acceptance test, so a warp (32 lines of
+// one variable) carries them along the line only while some lane keeps failing: after
+// a face where one did, it forms them from the current differences (the operands of
+// the carried ones) and carries them; after a face where none did, it drops them and
+// forms them per face at failing faces only (mp5_rel2_r without CARRY).
+__device__ __forceinline__ void flux_sweep_adaptive(const double* g, const double* h, int slen, double eps16,
+                                                    double* out, long long ostr, unsigned long long wmask) {
+  const unsigned lanes = __activemask();
+  double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
+  double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
+  double Pk3 = 0.0, Mk4 = 0.0, PM2 = 0.0, PM3 = 0.0, MM3 = 0.0, MM4 = 0.0;
+  bool carry = false;
+  double cp = g[2], cm = h[3];
+  double Fprev = 0.0;
+  const int kend = slen + 3;
+  for (int k = 3; k <= kend; ++k) {
+    // left-biased reconstruction of G^+ centred on cell k-1, right-biased of G^-
+    // centred on cell k (mirror image)
+    double Yp, Ym;
+    bool rp, rm;
+    if (carry) {
+      Yp = mp5_rel2_r<false, true>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16, rp);
+      Ym = mp5_rel2_r<true, true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, rm);
+    } else {
+      Yp = mp5_rel2_r<false, false>(Pd1, Pd2, Pd3, Pd4, 0.0, 0.0, eps16, rp);
+      Ym = mp5_rel2_r<true, false>(Md5, Md4, Md3, Md2, 0.0, 0.0, eps16, rm);
+    }
+    const double F = fma(0.5, Yp + Ym, cp + cm);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    Fprev = F;
+    if (k < kend) {
+      const bool want = __any_sync(lanes, rp || rm);
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
+      cp = g[k];
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
+      cm = h[k + 1];
+      if (want && carry) {
+        const double pk = Pd4 - Pd3;
+        PM2 = PM3;
+        PM3 = dm4(Pk3, pk);
+        Pk3 = pk;
+        const double mk = Md5 - Md4;
+        MM3 = MM4;
+        MM4 = dm4(Mk4, mk);
+        Mk4 = mk;
+      } else if (want) {
+        const double Pk2 = Pd3 - Pd2, Mk3 = Md4 - Md3;
+        Pk3 = Pd4 - Pd3;
+        Mk4 = Md5 - Md4;
+        PM2 = dm4(Pd2 - Pd1, Pk2);
+        PM3 = dm4(Pk2, Pk3);
+        MM3 = dm4(Md3 - Md2, Mk3);
+        MM4 = dm4(Mk3, Mk4);
+      }
+      carry = want;
+    }
+  }
+}
+
 // LIMO3 (Cada & Torrilhon 2009) in product form: with a = delta_{i-1/2} and
 // b = delta_{i+1/2} (G units), the correction b phi(theta) of u_i + b phi / 2 is
 //   unlimited  b phi_3 = (2 b + a) / 3,
@@ -342,7 +403,7 @@ __device__ __forceinline__ double limo3_y(double a, double b, double s2, long lo
   return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
 }
 
-// LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep; G^+ from
+// LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep_carry; G^+ from
 // cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k). The squares of
 // the differences are carried along the line (each enters two faces' switch), and the
 // switch compares a^2 + b^2 with (1 -+ 1e-12)/esc.
@@ -445,7 +506,8 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
       const double rdx = p.limo3_r * dm.dx[D];
       limo3_sweep(g, h, slen, 0.25 / (rdx * rdx), out, ostr, wmask);
     } else {
-      flux_sweep<REC>(g, h, slen, eps16, tp, tm, f0, fend, out, ostr, wmask);
+      if constexpr (REC) flux_sweep_carry<true>(g, h, slen, eps16, tp, tm, f0, fend, out, ostr, wmask);
+      else flux_sweep_adaptive(g, h, slen, eps16, out, ostr, wmask);
     }
   }
 }
@@ -500,6 +562,69 @@ __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
 }
 
 // ----------------------------------------------------------------- combine
+// The cells of one item. Every load of a cell is issued before its stores (the output
+// may be the U^n buffer, so loads cannot move past a store); A0ONE skips the product
+// with a first coefficient of 1. Per variable the operations and their order are
+// a_0 U^(k_0), then a_t U^(k_t) and w_d L_d by FMA, then the psi damping.
+template <int PHYS, int NV, bool A0ONE>
+__device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev& dm, const CellItem& ci,
+                                              const int o[3], double w0, double w1, double w2, double fac,
+                                              float gam, float lom[4]) {
+  const float rdx[3] = {0.f, 0.f, 0.f};
+  const long long nc = dm.ncell;
+  for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+    const int l = ci.c0 + c;
+    const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+    const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+    double u[NV];
+    {
+      const double* b0 = p.buf[p.co.k[0]] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = A0ONE ? b0[v * nc] : p.co.a[0] * b0[v * nc];
+    }
+    for (int t = 1; t < p.co.nterm; t++) {
+      const double* bt = p.buf[p.co.k[t]] + idx;
+      const double at = p.co.a[t];
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(at, bt[v * nc], u[v]);
+    }
+    {
+      const double* L0 = p.L[0] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w0, L0[v * nc], u[v]);
+    }
+    if (p.ndim > 1) {
+      const double* L1 = p.L[1] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w1, L1[v * nc], u[v]);
+    }
+    if (p.ndim > 2) {
+      const double* L2 = p.L[2] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w2, L2[v * nc], u[v]);
+    }
+    if constexpr (PHYS == PH_MHD) u[NV - 1] *= fac;  // psi
+#pragma unroll
+    for (int v = 0; v < NV; v++) p.out[idx + v * nc] = u[v];
+    if (p.W) {
+      constexpr int NW = NumW<PHYS, NV>::value;
+      double w[NW];
+      prim_w<PHYS, NV>(u, p.gm1, w);
+      const long long wi = dm.woff + (idx - dm.off);
+#pragma unroll
+      for (int q = 0; q < NW; q++) p.W[wi + (long long)q * nc] = w[q];
+    }
+    if (p.tlow_out) {
+      float up[4], lo[4];
+      bool force;
+      speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
+      if (!force)
+#pragma unroll
+        for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
+    }
+  }
+}
+
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
   __shared__ float redf[4][32];
@@ -507,6 +632,7 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
   __shared__ double s_fac;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
   const float gam = (float)p.gamma;
+  const bool a0_one = p.co.a[0] == 1.0;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
     AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
@@ -529,42 +655,9 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
       __syncthreads();
     }
     const double fac = damp ? s_fac : 1.0;
-    const float rdx[3] = {0.f, 0.f, 0.f};
     float lom[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
-      const int l = ci.c0 + c;
-      const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
-      const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-      double u[NV];
-#pragma unroll
-      for (int v = 0; v < NV; v++) {
-        const long long e = idx + (long long)v * dm.ncell;
-        double acc = p.co.a[0] * p.buf[p.co.k[0]][e];
-        for (int t = 1; t < p.co.nterm; t++) acc = fma(p.co.a[t], p.buf[p.co.k[t]][e], acc);
-        acc = fma(w0, p.L[0][e], acc);
-        if (p.ndim > 1) acc = fma(w1, p.L[1][e], acc);
-        if (p.ndim > 2) acc = fma(w2, p.L[2][e], acc);
-        if (PHYS == PH_MHD && v == 8) acc *= fac;
-        u[v] = acc;
-        p.out[e] = acc;
-      }
-      if (p.W) {
-        constexpr int NW = NumW<PHYS, NV>::value;
-        double w[NW];
-        prim_w<PHYS, NV>(u, p.gm1, w);
-        const long long wi = dm.woff + (idx - dm.off);
-#pragma unroll
-        for (int q = 0; q < NW; q++) p.W[wi + (long long)q * dm.ncell] = w[q];
-      }
-      if (p.tlow_out) {
-        float up[4], lo[4];
-        bool force;
-        speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
-        if (!force)
-#pragma unroll
-          for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
-      }
-    }
+    if (a0_one) combine_cells<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom);
+    else combine_cells<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom);
     if (p.tlow_out) {
       block_max4f_bcast(lom, redf, thr);
       if (threadIdx.x == 0)

@@ -611,6 +611,67 @@ def test_step_cfl_equals_dt_then_step(scope):
     assert torch.equal(U1, U2)
 
 
+# ------------------------------------------------- speed maxima with components below 2^-100
+def _tiny_components_workload(adversarial, n=32):
+    """3D MHD+GLM periodic state whose momenta and B_z hold values of 1e-320 .. 1e-31 in
+    about half of the cells (the exactly-zero components of a uniform background pick
+    up such values ahead of a wave), with a hot sphere that sets the speed maxima.
+    adversarial adds a cell A (rho = 2^-95, B = 0, sound speed 5) whose momenta of a
+    few 2^-101 add 2/64 .. 4/64 to its speeds, and a cell B (rho = 1) whose speeds lie
+    between A's with and without those momenta: A's true speeds are the maxima."""
+    rng = np.random.default_rng(W.SEED0 + 101)
+    g = 5.0 / 3.0
+    x, dx = W.centres(n, -0.5, 0.5)
+    Z, Y, X = np.meshgrid(x, x, x, indexing="ij")
+    rho = 1.0 + 1e-3 * (2.0 * rng.random(X.shape) - 1.0)
+    p = np.where(X * X + Y * Y + Z * Z < 0.04, 10.0, 0.1)
+    zero = np.zeros_like(rho)
+    U = W.conserved_mhd(rho, [zero, zero, zero], p, [zero + 0.5, zero + 0.5, zero], g)
+    for v in (1, 2, 3, 7):
+        mag = 10.0 ** rng.uniform(-320.0, -31.0, X.shape)
+        sgn = np.where(rng.random(X.shape) < 0.5, -1.0, 1.0)
+        U[v] = np.where(rng.random(X.shape) < 0.5, sgn * mag, 0.0)
+    if adversarial:
+        ra = 2.0 ** -95
+        ma = np.array([4.0, 3.0, -2.0]) * 2.0 ** -101
+        pa = 25.0 * ra / g
+        U[:, 3, 20, 27] = [ra, *ma, pa / (g - 1.0) + 0.5 * float(ma @ ma) / ra, 0.0, 0.0, 0.0, 0.0]
+        vb = np.array([2.0, 1.5, 1.0]) / 64.0
+        U[:, 12, 5, 9] = [1.0, *vb, (25.0 / g) / (g - 1.0) + 0.5 * float(vb @ vb), 0.0, 0.0, 0.0, 0.0]
+    dom = W.Domain((n, n, n), (dx, dx, dx), nb=(2, 2, 2))
+    return W.Workload("tiny", W.MHD_GLM, 3, W.SSPRK3, g, 0.3, [dom], U, active=np.ones(8, np.uint8))
+
+
+@pytest.mark.parametrize("adversarial", [False, True])
+def test_speed_maxima_with_tiny_components_bitwise(adversarial):
+    """CFL time step and the splitting speeds of every stage, bit-identical to the oracle
+    on states whose momenta and fields carry components below 2^-100 (left out of the
+    FP32 bounds with a widened margin, or evaluated exactly where that margin is not
+    enough). With dt = 0 the stage states are U^n, up to the rounding of the Shu-Osher
+    combination (3/4 U + 1/4 U), so later stages match to 1e-14: a maximum left out
+    would be off by 6e-3 in the adversarial case."""
+    w = _tiny_components_workload(adversarial)
+    c, d = ocfg(w), odom(w.domains[0])
+    al, rate, fl = O.speeds(c, d, w.U)
+    assert fl == 0
+    if adversarial:
+        assert al[0] == 5.0625 and al[1] == 5.046875 and al[2] == 5.03125
+    s = A().Solver.from_workload(w)
+    U = dev(w.U.ravel())
+    h, _ = O.dt(c, d, w.U, w.cfl)
+    assert float(s.dt(U)[0].item()) == h
+    s.step_batched(U, torch.zeros(1, dtype=torch.float64, device="cuda"))
+    assert s.error() == A().OK
+    got = s.alpha()
+    assert np.array_equal(got[0, 0], al), (got[0, 0], al)
+    for k in range(1, got.shape[0]):
+        assert np.allclose(got[k, 0], al, rtol=1e-14, atol=0.0), (k, got[k, 0], al)
+    s2 = A().Solver.from_workload(w)
+    U2 = dev(w.U.ravel())
+    assert float(s2.step_cfl(U2)[0].item()) == h
+    assert np.array_equal(s2.alpha(1)[0, 0], al)
+
+
 # ------------------------------------------ full sizes, in the bench's launch configuration
 def test_blast_full_size_one_step_elementwise():
     """The bench's workload and launches (256^3 in 16^3 blocks, autotuned tile,
