@@ -107,6 +107,7 @@ struct amrfd_handle {
   bool active_h_stale = false;          // device flags changed by amrfd_activate
   FluxItem *d_fall = nullptr, *d_fact = nullptr;
   CellItem *d_call = nullptr, *d_cact = nullptr;
+  float* d_item_up = nullptr;       // per cell item x 4: largest FP32 upper bound of the speeds
   int* d_counts = nullptr;          // counts[0] = flux items, [1] = cell items
   int* d_counters = nullptr;        // one per persistent launch
   double* d_stage[kMaxStages] = {};
@@ -232,8 +233,9 @@ int build_items(amrfd_handle* h) {
   h->nci = (int)ci.size();
   h->nfgroups = (int)g_owner.size();
   // (re)allocate and upload
-  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
+  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact); cudaFree(h->d_item_up);
   for (int k = 0; k < 12; k++) cudaFree(h->d_grp[k]);
+  CK(cudaMalloc(&h->d_item_up, sizeof(float) * 4 * std::max(1, h->nci)));
   CK(cudaMalloc(&h->d_fall, sizeof(FluxItem) * std::max(1, h->nfi)));
   CK(cudaMalloc(&h->d_fact, sizeof(FluxItem) * std::max(1, h->nfi)));
   CK(cudaMalloc(&h->d_call, sizeof(CellItem) * std::max(1, h->nci)));
@@ -367,6 +369,7 @@ CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
   p.co = h->co[i - 1];
   p.slot_out = (i < h->ns) ? slot(h, i) : nullptr;
   p.tlow_out = (i < h->ns) ? tlow(h, i) : nullptr;
+  p.item_up = (i < h->ns) ? h->d_item_up : nullptr;  // read by the exact pass over U^(i)
   p.araw0 = slot(h, 0);
   p.err = h->d_err;
   p.gamma = h->cfg.gamma;
@@ -392,6 +395,9 @@ SpeedParams speed_params(amrfd_handle* h, const double* U, int k, int want_rate)
   p.want_rate = want_rate;
   p.gm1 = h->cfg.gamma - 1.0;
   p.ndom = h->ndom;
+  // every exact pass follows, on the same stream and item list, a bounds pass or a
+  // stage combination that wrote the per-item upper bounds of the same state
+  p.item_up = h->d_item_up;
   return p;
 }
 
@@ -1092,7 +1098,7 @@ void amrfd_destroy(amrfd_handle* h) {
   free_graphs(h);
   cudaFree(h->d_dom); cudaFree(h->d_active); cudaFree(h->d_bdom);
   cudaFree(h->d_act_tmp[0]); cudaFree(h->d_act_tmp[1]);
-  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact);
+  cudaFree(h->d_fall); cudaFree(h->d_fact); cudaFree(h->d_call); cudaFree(h->d_cact); cudaFree(h->d_item_up);
   for (int k = 0; k < 12; k++) cudaFree(h->d_grp[k]);
   cudaFree(h->d_counts); cudaFree(h->d_counters);
   for (int k = 0; k < kMaxStages; k++) cudaFree(h->d_stage[k]);

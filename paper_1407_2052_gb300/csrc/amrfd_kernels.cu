@@ -99,19 +99,25 @@ __device__ __forceinline__ bool exact_speeds(const double* u, double gamma, int 
 // ------------------------------------------------------------------ speeds
 // Exact per-domain maxima in two launches. The bounds launch (exact = 0) evaluates
 // FP32 bounds of every active cell's speeds and publishes, per domain, the largest
-// lower bound T (an integer max of the FP32 bits). The exact launch (exact = 1)
-// re-evaluates the bounds and computes the exact IEEE speeds only of the cells whose
-// upper bound reaches T, or that carry no bound. The maxima are exact: a cell left
-// out lies below T, and T is below the speed of the cell that set it.
+// lower bound T (an integer max of the FP32 bits), and per item the largest upper bound
+// (+inf when a cell carries none). The exact launch (exact = 1) skips the items whose
+// upper bounds stay below T, re-evaluates the bounds of the other items' cells and
+// computes the exact IEEE speeds only of the cells whose upper bound reaches T, or that
+// carry no bound. The maxima are exact: a cell left out lies below T, and T is below the
+// speed of the cell that set it. Only the directions d < ndim (and the CFL rate when
+// asked for) take part.
 
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
   __shared__ unsigned long long red[4][32];
   __shared__ float redf[4][32];
-  __shared__ float thr[4];
+  __shared__ float thr[4], thr_up[4];
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
   const float gam = (float)p.gamma;
   const bool want_rate = p.want_rate != 0;
+  bool on[4];
+#pragma unroll
+  for (int q = 0; q < 4; q++) on[q] = q < 3 ? q < p.ndim : want_rate;
   for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
     AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
@@ -121,12 +127,21 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
     block_coords(dm, ci.blk, o);
     const float rdx[3] = {(float)(1.0 / dm.dx[0]), (float)(1.0 / dm.dx[1]), (float)(1.0 / dm.dx[2])};
     unsigned* tl = p.tlow + (size_t)ci.dom * 4;
+    float* iu = p.item_up ? p.item_up + (size_t)(p.item0 + it) * 4 : nullptr;
     float T[4] = {0.f, 0.f, 0.f, 0.f};
-    if (p.exact)
+    if (p.exact) {
 #pragma unroll
       for (int q = 0; q < 4; q++) T[q] = __uint_as_float(tl[q]);
+      if (iu) {  // the same decision in every thread of the block
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; q++) any |= on[q] && iu[q] >= T[q];
+        if (!any) continue;
+      }
+    }
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
     float lom[4] = {0.f, 0.f, 0.f, 0.f};
+    float upm[4] = {0.f, 0.f, 0.f, 0.f};
     for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
       const int l = ci.c0 + c;
       const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
@@ -146,14 +161,21 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
       bool force;
       speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, want_rate, up, lo, force);
       if (!p.exact) {
-        if (!force)
+        if (!force) {
 #pragma unroll
-          for (int q = 0; q < 4; q++) lom[q] = fmaxf(lom[q], lo[q]);
+          for (int q = 0; q < 4; q++) {
+            lom[q] = fmaxf(lom[q], lo[q]);
+            upm[q] = fmaxf(upm[q], up[q]);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; q++) upm[q] = __int_as_float(0x7f800000);  // +inf
+        }
         continue;
       }
       bool cand = force;
 #pragma unroll
-      for (int q = 0; q < 4; q++) cand |= (q < 3 || want_rate) && up[q] >= T[q];
+      for (int q = 0; q < 4; q++) cand |= on[q] && up[q] >= T[q];
       if (!cand) continue;
       if (!exact_speeds<PHYS, NV>(u, p.gamma, p.ndim, dm.dx, want_rate, mx)) atomicOr(p.err, kErrNonphysical);
     }
@@ -163,6 +185,12 @@ __global__ void __launch_bounds__(256) speeds_kernel(SpeedParams p) {
 #pragma unroll
         for (int q = 0; q < 4; q++)
           if (thr[q] > 0.f) atomicMax(tl + q, __float_as_uint(thr[q]));
+      if (iu) {
+        block_max4f_bcast(upm, redf, thr_up);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int q = 0; q < 4; q++) iu[q] = thr_up[q];
+      }
       continue;
     }
     block_max4(mx, red);
@@ -569,7 +597,7 @@ __global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
 template <int PHYS, int NV, bool A0ONE>
 __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev& dm, const CellItem& ci,
                                               const int o[3], double w0, double w1, double w2, double fac,
-                                              float gam, float lom[4]) {
+                                              float gam, float lom[4], float upm[4]) {
   const float rdx[3] = {0.f, 0.f, 0.f};
   const long long nc = dm.ncell;
   for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
@@ -618,9 +646,16 @@ __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev&
       float up[4], lo[4];
       bool force;
       speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
-      if (!force)
+      if (!force) {
 #pragma unroll
-        for (int q = 0; q < 3; q++) lom[q] = fmaxf(lom[q], lo[q]);
+        for (int q = 0; q < 3; q++) {
+          lom[q] = fmaxf(lom[q], lo[q]);
+          upm[q] = fmaxf(upm[q], up[q]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 3; q++) upm[q] = __int_as_float(0x7f800000);  // +inf
+      }
     }
   }
 }
@@ -628,7 +663,7 @@ __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev&
 template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
   __shared__ float redf[4][32];
-  __shared__ float thr[4];
+  __shared__ float thr[4], thr_up[4];
   __shared__ double s_fac;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
   const float gam = (float)p.gamma;
@@ -656,14 +691,21 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
     }
     const double fac = damp ? s_fac : 1.0;
     float lom[4] = {0.f, 0.f, 0.f, 0.f};
-    if (a0_one) combine_cells<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom);
-    else combine_cells<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom);
+    float upm[4] = {0.f, 0.f, 0.f, 0.f};
+    if (a0_one) combine_cells<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+    else combine_cells<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
     if (p.tlow_out) {
       block_max4f_bcast(lom, redf, thr);
       if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 3; q++)
           if (thr[q] > 0.f) atomicMax(p.tlow_out + (size_t)ci.dom * 4 + q, __float_as_uint(thr[q]));
+      if (p.item_up) {
+        block_max4f_bcast(upm, redf, thr_up);
+        if (threadIdx.x == 0)
+#pragma unroll
+          for (int q = 0; q < 4; q++) p.item_up[(size_t)(p.item0 + it) * 4 + q] = thr_up[q];
+      }
     } else if (damp) {
       __syncthreads();  // s_fac is rewritten by the next item
     }

@@ -26,6 +26,9 @@ struct SpeedParams {
   double* W;                    // bounds pass: also write the derived quantities of U (or nullptr)
   double gm1;
   int ndom;
+  float* item_up;               // per item (index item0 + it) x 4: largest FP32 upper bound, +inf
+                                // when a cell has none; bounds pass writes, exact pass skips items
+                                // below the thresholds (nullptr: none)
 };
 
 // One flux pass: L_d(U^(k)) for the items' lines.
@@ -79,6 +82,7 @@ struct CombParams {
   double* W;                    // derived quantities of the output state (or nullptr)
   double gm1;
   int ndom;
+  float* item_up;               // with tlow_out: per item upper bounds, as SpeedParams::item_up
 };
 
 struct DtParams {
