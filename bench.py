@@ -37,14 +37,14 @@ FLUX_BYTES_PER_CELL = 4 * NV * 8
 # (profiles/flux_kernel_blast3d.md): DADD + DMUL + 2 DFMA thread instructions = flop,
 # and DADD + DMUL + DFMA = FP64 pipe instructions. The curvature limiters are formed
 # only where warps need them, so the count depends on the data (first timed step).
-FLUX_FLOPS_PER_CELL_DIR = 292.1
-FLUX_FP64_INST_PER_CELL_DIR = 189.7
+FLUX_FLOPS_PER_CELL_DIR = 292.0
+FLUX_FP64_INST_PER_CELL_DIR = 189.5
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64 (profiling recipe table)
 # FP64 pipe: 2 thread instructions / clock / SM (ncu peak_sustained) x 152 SMs x 2.07 GHz
 FP64_PEAK_GINST = 2 * 152 * 2.07
 # DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write, 128^3 capture,
 # scaled by cells): traffic grows with the cells processed
-FLUX_TRAFFIC_BYTES_PER_CELL = (316.482816 + 413.723392) * 1e6 / 128 ** 3
+FLUX_TRAFFIC_BYTES_PER_CELL = (313.990144 + 410.184704) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):

@@ -304,7 +304,7 @@ int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
 
 int default_threads(int nv, int lines) {
   int t = ((nv * lines + 31) / 32) * 32;
-  return std::max(64, std::min(t, 384));
+  return std::max(64, std::min(t, kFluxMaxThreads));
 }
 
 unsigned long long* slot(amrfd_handle* h, int k) { return h->d_slot + (size_t)k * h->ndom * 4; }
@@ -965,7 +965,7 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
 }
 
 int amrfd_set_tile(amrfd_handle* h, int seg, int lines, int threads) {
-  if (!h || seg < 8 || seg > 64 || lines < 1 || lines > 32 || threads < 32 || threads > 384 || threads % 32)
+  if (!h || seg < 8 || seg > 64 || lines < 1 || lines > 32 || threads < 32 || threads > kFluxMaxThreads || threads % 32)
     return AMRFD_ERR_INVALID_ARG;
   int rc = configure_tile(h, seg, lines, threads);
   if (rc) return rc;
@@ -1004,7 +1004,7 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
     for (int ln : lines_c) {
       if (h->cfg.ndim == 1 && ln != 1) continue;
       for (int mul = 1; mul <= 2; mul++) {
-        const int thr = std::min(384, default_threads(h->nv, ln) * mul);
+        const int thr = std::min(kFluxMaxThreads, default_threads(h->nv, ln) * mul);
         if (mul == 2 && thr == default_threads(h->nv, ln)) continue;
         if (configure_tile(h, sg, h->cfg.ndim == 1 ? 1 : ln, thr)) continue;
         if (compact(h, s)) continue;

@@ -555,7 +555,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
 }
 
 template <int PHYS, int NV, int MODE>
-__global__ void __launch_bounds__(384, 2) flux_kernel(FluxParams p) {
+__global__ void __launch_bounds__(kFluxMaxThreads, 2) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
   __shared__ int s_it;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
