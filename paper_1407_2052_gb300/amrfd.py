@@ -269,8 +269,9 @@ class Solver:
             except (OSError, ValueError):
                 known = None
             if known:
-                self.set_tile(*known)
-                return self.get_tile()
+                # a tile the library no longer accepts (another version's limits) is tuned again
+                if self._L.amrfd_set_tile(self._h, *(int(x) for x in known)) == OK:
+                    return self.get_tile()
         _check(self._L.amrfd_autotune(self._h, _ptr(U), _ptr(dt), _stream(stream)), "amrfd_autotune")
         tile = self.get_tile()
         if cache:

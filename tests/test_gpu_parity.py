@@ -800,6 +800,12 @@ def test_autotune_cache_reuses_the_tile(tmp_path):
     s2 = A().Solver.from_workload(w)
     s2.set_tile(8, 1, 32)
     assert s2.autotune(U, dt, cache=cache) == tile
+    # a cached tile the library rejects (more threads than a flux CTA takes) is tuned again
+    json.dump({s.tile_key(): [16, 32, 384]}, open(cache, "w"))
+    with pytest.raises(A().AmrfdError):
+        s2.set_tile(16, 32, 384)
+    again = s2.autotune(U, dt, cache=cache)
+    assert again[2] <= 288 and json.load(open(cache)) == {s.tile_key(): list(again)}
 
 
 # ------------------------------------------------------------------ degenerate cases
