@@ -801,7 +801,8 @@ def test_autotune_cache_reuses_the_tile(tmp_path):
     s2.set_tile(8, 1, 32)
     assert s2.autotune(U, dt, cache=cache) == tile
     # a cached tile the library rejects (more threads than a flux CTA takes) is tuned again
-    json.dump({s.tile_key(): [16, 32, 384]}, open(cache, "w"))
+    with open(cache, "w") as fh:
+        json.dump({s.tile_key(): [16, 32, 384]}, fh)
     with pytest.raises(A().AmrfdError):
         s2.set_tile(16, 32, 384)
     again = s2.autotune(U, dt, cache=cache)
