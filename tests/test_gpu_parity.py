@@ -487,6 +487,29 @@ def test_mirror_faces_smooth_one_step(case, batched):
     assert rel_linf(host(U, ref.shape), ref, LAST_CH[0]) <= 1e-12
 
 
+@pytest.mark.parametrize("case", ["sod1d", "mhd2d"])
+def test_long_uneven_segments_tile_invariance(case):
+    """Segments up to 64 cells whose length does not divide evenly (Sod's 200 cells give
+    segments of 50; a 100 x 36 MHD box segments of 50 and 36): the same bits under every
+    tile, after two steps."""
+    if case == "sod1d":
+        w = W.sod(200)
+        tiles = [(8, 1, 32), (16, 1, 32), (32, 1, 64), (50, 1, 32), (64, 1, 64), (64, 1, 96)]
+    else:
+        w = _smooth_domain(O.MHD_GLM, 2, (100, 36, 1), ((O.PERIODIC, O.PERIODIC), (O.OUTFLOW, O.OUTFLOW), (0, 0)),
+                           seed=77, nb=(4, 2, 1))
+        tiles = [(16, 32, 288), (64, 8, 288), (50, 4, 160), (36, 16, 288), (8, 1, 32)]
+    base = None
+    for tile in tiles:
+        s = A().Solver.from_workload(w)
+        s.set_tile(*tile)
+        _, U, _ = run_gpu(w, 2, solver=s)
+        out = U.cpu()
+        if base is None:
+            base = out
+        assert torch.equal(out, base), tile
+
+
 def test_mirror_faces_tile_invariance():
     """Segments that end on a mirror face give the same bits under every tile."""
     w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((2, 2), (2, 1), (0, 0)), seed=41, nb=(5, 3, 2))
