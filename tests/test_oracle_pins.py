@@ -433,6 +433,74 @@ def test_dt_closed_form_uniform():
     assert O.dt(cm, d, Um, 0.4)[0] == pytest.approx(0.4 / (chh / 0.1 + chh / 0.3), rel=1e-14)
 
 
+# ------------------------------------------------------------- GLM psi damping
+def _uniform_mhd(rho, v, p, B, psi, n, g):
+    u = W.conserved_mhd(np.array(rho), [np.array(x) for x in v], np.array(p), [np.array(x) for x in B], g,
+                        np.array(psi))
+    shape = (9,) + tuple(n[::-1])
+    return u, np.broadcast_to(u.reshape(-1, 1, 1, 1), shape).copy()
+
+
+@pytest.mark.parametrize("integrator", [O.SSPRK3, O.SSPRK54])
+def test_psi_damping_closed_form_on_uniform_state(integrator):
+    """Sec. 4.2: the GLM source -(c_h^2/c_p^2) psi, integrated exactly after the step with
+    c_p^2/c_h = c_r, multiplies psi by exp(-dt c_h/c_r) once per step. A uniform state has
+    L(U) = 0, so only the damping moves it. With B along x and v along z, c_h has a closed
+    form: the z fast speed is the perpendicular one, sqrt(a^2 + b^2), and it is the largest
+    of the three: c_h = |v_z| + sqrt(gamma p/rho + B_x^2/rho)."""
+    g = 5.0 / 3.0
+    rho, vz, p, bx, psi0, dt, cr = 1.25, -0.375, 0.5, 0.75, 0.125, 0.01, 0.18
+    c = O.cfg(O.MHD_GLM, 3, integrator=integrator, gamma=g, glm_cr=cr)
+    n = [4, 5, 6]
+    d = O.dom(n, [0.1, 0.2, 0.3])
+    u, U = _uniform_mhd(rho, (0.0, 0.0, vz), p, (bx, 0.0, 0.0), psi0, n, g)
+    ch = abs(vz) + math.sqrt(g * p / rho + bx * bx / rho)
+    Un, fl, _, ch_or = O.step(c, d, U, dt)
+    assert fl == 0
+    assert ch_or == pytest.approx(ch, rel=1e-15)
+    want = psi0 * math.exp(-dt * ch / cr)
+    np.testing.assert_allclose(Un[8], want, rtol=1e-14, atol=0)
+    # a damping with the wrong exponent, once per stage, or not at all lies far outside
+    assert abs(want - psi0 * math.exp(-dt * ch * cr)) > 1e-4 * psi0
+    assert abs(want - psi0 * math.exp(-3 * dt * ch / cr)) > 1e-4 * psi0
+    for v in range(8):
+        np.testing.assert_allclose(Un[v], u[v], rtol=1e-14, atol=1e-15)
+    # c_r <= 0 switches the damping off: psi stays (up to the stage sums' rounding)
+    c0 = O.cfg(O.MHD_GLM, 3, integrator=integrator, gamma=g, glm_cr=0.0)
+    U0, fl0, _, _ = O.step(c0, d, U, dt)
+    assert fl0 == 0
+    np.testing.assert_allclose(U0[8], psi0, rtol=1e-14, atol=0)
+
+
+def test_psi_damping_uses_speed_of_step_start_once():
+    """On non-uniform data the damping is the only difference between c_r > 0 and c_r <= 0:
+    every other variable is bitwise the same, and psi differs by one factor
+    exp(-dt c_h/c_r) with c_h the largest splitting speed of U^n (not of a later stage),
+    applied once after the last stage."""
+    w = W.vortex2d(32)
+    c = _ocfg(w)
+    d = _odom(w.domains[0])
+    U = w.U.reshape(9, 1, 32, 32).copy()
+    U[8] = 0.05 * np.sin(np.linspace(0.0, 7.0, 32 * 32)).reshape(1, 32, 32)
+    h = 0.5 * O.dt(c, d, U, w.cfl)[0]
+    cd = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, 0.18)
+    cz = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, 0.0)
+    Ud, fl1, _, ch = O.step(cd, d, U, h)
+    Uz, fl2, _, _ = O.step(cz, d, U, h)
+    assert fl1 == 0 and fl2 == 0
+    assert np.array_equal(Ud[:8], Uz[:8])
+    araw0, _, _ = O.speeds(cd, d, U)
+    assert ch == max(araw0[:2])
+    fac = math.exp(-h * ch / 0.18)
+    nz = np.abs(Uz[8]) > 1e-6
+    np.testing.assert_allclose(Ud[8][nz] / Uz[8][nz], fac, rtol=2e-16 * 4, atol=0)
+    # the speeds of the step's end state differ from U^n's by far more than the tolerance
+    # resolves, so a damping taken with a later state's c_h would fail the ratio above
+    araw1, _, _ = O.speeds(cd, d, Ud)
+    fac1 = math.exp(-h * max(araw1[:2]) / 0.18)
+    assert abs(fac1 - fac) > 1e3 * 2e-16 * fac
+
+
 def _mirror_double(U, axis, sgn):
     """Periodic data of twice the length: U followed by its mirror image times sgn."""
     return np.concatenate([U, sgn * np.flip(U, axis=axis)], axis=axis)
