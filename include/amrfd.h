@@ -195,6 +195,15 @@ int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);
 int amrfd_timing_begin(amrfd_handle *h, int capacity);
 int amrfd_timing_end(amrfd_handle *h, double ms[4], int counts[4], void *stream);
 
+/* FP64 throughput of this GPU, the denominator of the flux pass's roofline (the
+   paper has no counterpart: a measurement utility). Runs a kernel of independent
+   FP64 fused multiply-adds on `stream`: five single launches after a warm-up
+   (burst: the best) and then back-to-back launches for about `seconds` (0..60;
+   sustained). out[0] = burst TFLOP/s, out[1] = sustained TFLOP/s (2 flop per
+   FMA), out[2] = milliseconds of the best launch, out[3] = FMAs per launch.
+   Synchronises `stream`; AMRFD_ERR_INVALID_ARG for a bad `seconds` or NULL out. */
+int amrfd_fp64_peak(double seconds, double out[4], void *stream);
+
 /* Per-stage splitting speeds of the last step, raw (before raising to c_h):
    out[stage][domain][3], host memory, `nstage` = stages to copy. Synchronises. */
 int amrfd_get_alpha(amrfd_handle *h, double *out, int nstage, void *stream);
@@ -211,13 +220,18 @@ void amrfd_destroy(amrfd_handle *h);
    a deployment variant of amrfd_dt. Inputs as for amrfd_create plus amrfd_dt:
    `domains[ndomain]` (host), optional per-block `active_dev` (device, NULL = all
    active), state `U` and output `dt_dev[ndomain]` (device). Scratch is a fixed
-   ~190 KB __device__ array inside the library, held by every GPU that loads it
+   ~116 KB __device__ array inside the library, held by every GPU that loads it
    until the process exits; ndomain is limited to 1024 (AMRFD_ERR_INVALID_ARG,
-   with a message on stderr, beyond). The first call on a device looks up the
-   array's device address and should come before any stream capture. All calls
+   with a message on stderr, beyond). The descriptors travel as kernel arguments:
+   the call neither copies from host memory nor waits for the GPU. The first call
+   on a device looks up the array's device address and should come before any
+   stream capture; that address is kept for the life of the process, so the
+   library must not outlive a reset of the device's primary context. All calls
    share the one array and each leaves its contents behind: calls whose work
    overlaps on the GPU (other streams, other host threads) race; serialise them.
-   Non-physical cells are skipped without setting an error latch. */
+   A domain holding a non-physical cell (rho <= 0, p <= 0 or a non-finite value,
+   among its active cells) gets dt = NaN, and with AMRFD_DT_GLOBAL every domain
+   does; amrfd_dt instead leaves such cells out and latches AMRFD_ERR_NONPHYSICAL. */
 int amrfd_dt_noalloc(const amrfd_config *cfg, const amrfd_domain *domains, int ndomain,
                      const uint8_t *active_dev, const double *U, double *dt_dev, double t, double t_end,
                      void *stream);

@@ -25,7 +25,7 @@ EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
            "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
            "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active",
-           "amrfd_step_cfl")
+           "amrfd_step_cfl", "amrfd_fp64_peak")
 
 
 class Config(ctypes.Structure):
@@ -78,6 +78,7 @@ def load(checked=False):
     L.amrfd_timing_begin.argtypes = [vp, i]
     L.amrfd_timing_end.argtypes = [vp, vp, vp, vp]
     L.amrfd_dt_noalloc.argtypes = [ctypes.POINTER(Config), ctypes.POINTER(DomainC), i, vp, vp, vp, dp, dp, vp]
+    L.amrfd_fp64_peak.argtypes = [dp, vp, vp]
     L.amrfd_destroy.argtypes = [vp]
     L.amrfd_destroy.restype = None
     L.amrfd_strerror.argtypes = [i]
@@ -135,13 +136,43 @@ def domains_c(domains):
 def dt_noalloc(physics, ndim, gamma, cfl, domains, U, out, active=None, t=0.0, t_end=float("inf"),
                dt_scope=DT_PER_DOMAIN, stream=None):
     """amrfd_dt_noalloc: the CFL time step without a handle or any device allocation
-    (for callers that cannot allocate; `out` is a caller-owned float64 CUDA tensor)."""
+    (for callers that cannot allocate; `out` is a caller-owned float64 CUDA tensor).
+    The tensors are checked here, before the call, because the kernels trust their sizes:
+    `active` a contiguous CUDA uint8 tensor with one flag per block, `out` a float64 CUDA
+    tensor of at least len(domains) values, `U` large enough for every domain."""
+    import torch
+    nv = 2 + ndim if physics == EULER else 9
+    nblocks = sum(int(d.nb[0]) * int(d.nb[1]) * int(d.nb[2]) for d in domains)
+    need = max((int(d.offset) + nv * int(d.n[0]) * int(d.n[1]) * int(d.n[2]) for d in domains), default=0)
+    if active is not None:
+        if not isinstance(active, torch.Tensor) or active.dtype != torch.uint8 or not active.is_contiguous():
+            raise TypeError("active: expected a contiguous uint8 tensor")
+        if active.numel() != nblocks:
+            raise ValueError("active: %d flags for %d blocks" % (active.numel(), nblocks))
+        if not active.is_cuda:
+            raise TypeError("active: expected a CUDA tensor")
+    if not isinstance(out, torch.Tensor) or out.dtype != torch.float64 or not out.is_contiguous():
+        raise TypeError("out: expected a contiguous float64 tensor")
+    if out.numel() < len(domains):
+        raise ValueError("out: %d values for %d domains" % (out.numel(), len(domains)))
+    if not isinstance(U, torch.Tensor) or U.numel() < need:
+        raise ValueError("U: the domains need %d elements" % need)
     cfg = Config(physics, ndim, SSPRK3, dt_scope, gamma, cfl, 0.0)
     doms = domains_c(domains)
     act = ctypes.c_void_p(active.data_ptr()) if active is not None else None
     _check(load().amrfd_dt_noalloc(ctypes.byref(cfg), doms, len(domains), act, _ptr(U), _ptr(out), float(t),
                                    float(t_end), _stream(stream)), "amrfd_dt_noalloc")
     return out
+
+
+def fp64_peak(seconds=2.0, stream=None):
+    """amrfd_fp64_peak: measured FP64 throughput of the current GPU,
+    {"burst_tflops", "sustained_tflops", "launch_ms", "fma_per_launch"}."""
+    out = np.zeros(4)
+    _check(load().amrfd_fp64_peak(float(seconds), out.ctypes.data_as(ctypes.c_void_p), _stream(stream)),
+           "amrfd_fp64_peak")
+    return {"burst_tflops": float(out[0]), "sustained_tflops": float(out[1]), "launch_ms": float(out[2]),
+            "fma_per_launch": float(out[3])}
 
 
 class Solver:

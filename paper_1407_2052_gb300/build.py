@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libamrfd.so")
 LIB_CHECKED = os.path.join(HERE, "libamrfd_checked.so")  # -DAMRFD_CHECKS: kernel index checks
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["amrfd_kernels.cu", "amrfd_adjoint.cu", "amrfd_api.cu", "amrfd_noalloc.cu"]
+SOURCES = ["amrfd_kernels.cu", "amrfd_adjoint.cu", "amrfd_api.cu", "amrfd_noalloc.cu", "amrfd_measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I" + os.path.join(ROOT, "include")]

@@ -6,9 +6,12 @@
 // locks or implicit device synchronisation on a hot path, or a host that
 // forbids the library from growing its device footprint after start-up. For
 // them, amrfd_dt_noalloc computes the same per-domain time step as amrfd_dt
-// without a handle: its scratch (domain descriptors, work partition and the
-// per-domain speed maxima) lives in one file-scope __device__ array of fixed
-// size, so the call allocates nothing on the device or the host heap.
+// without a handle: its scratch (domain descriptors, work partition, the
+// per-domain speed maxima and failure flags) lives in one file-scope __device__
+// array of fixed size, so the call allocates nothing on the device or the host
+// heap. The descriptors reach the scratch as kernel arguments (copied by the
+// launch itself), so no host buffer is read after the call returns and no
+// host-to-device copy stalls the calling thread.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -23,24 +26,54 @@ namespace {
 
 constexpr int kNaMaxDomains = 1024;    // largest ndomain accepted
 constexpr int kNaChunk = 4096;         // cells per thread block item
+constexpr int kNaBatch = 256;          // descriptors per upload launch (kernel arguments < 32 KB)
+
+// What the time step needs of one domain.
+struct NaDesc {
+  int n[3], be[3], nb[3];
+  int block0;        // global index of the domain's first block
+  int ncell;
+  int chunk0;        // first work chunk of the domain
+  long long off;     // element offset of the domain in U
+  double dx[3];
+};
 
 struct NaLayout {
-  DomDev dom[kNaMaxDomains];
-  int chunk0[kNaMaxDomains + 1];      // prefix sum of per-domain chunk counts
+  NaDesc dom[kNaMaxDomains];
+  int nchunks;                              // chunks of all domains
+  unsigned bad[kNaMaxDomains];              // a non-physical cell was met
   unsigned long long slot[kNaMaxDomains][4];
 };
 
 // The scratch. Every GPU that loads the library holds it until the process exits.
 static __device__ __align__(256) unsigned char g_na_scratch[sizeof(NaLayout)];
 
-// Host staging of the descriptors (no heap use on the call path).
-static NaLayout g_na_host;
+// One upload launch: descriptors first..first+count-1 by value.
+struct NaUpload {
+  NaLayout* lay;
+  int first, count, nchunks;
+  NaDesc d[kNaBatch];
+};
+static_assert(sizeof(NaUpload) < 32000, "kernel argument block too large");
+
+static NaUpload g_na_up;                  // host staging of the arguments (no heap use)
 static std::mutex g_na_mutex;
-static void* g_na_dev_ptr[64];         // device address of g_na_scratch, per device
+static void* g_na_dev_ptr[64];            // device address of g_na_scratch, per device
+
+// Copies the descriptors into the scratch and clears their maxima and flags.
+__global__ void __launch_bounds__(256) na_upload_kernel(const __grid_constant__ NaUpload u) {
+  for (int i = threadIdx.x; i < u.count; i += blockDim.x) {
+    const int k = u.first + i;
+    u.lay->dom[k] = u.d[i];
+    u.lay->bad[k] = 0u;
+#pragma unroll
+    for (int q = 0; q < 4; q++) u.lay->slot[k][q] = 0ull;
+  }
+  if (threadIdx.x == 0) u.lay->nchunks = u.nchunks;
+}
 
 struct NaParams {
-  const NaLayout* lay;
-  NaLayout* lay_w;
+  NaLayout* lay;
   int ndom;
   const unsigned char* active;  // per global block or nullptr
   const double* U;
@@ -52,21 +85,22 @@ template <int PHYS, int NV>
 __global__ void __launch_bounds__(256) na_speeds_kernel(NaParams p) {
   __shared__ unsigned long long red[4][32];
   __shared__ int s_dom;
-  const int nchunks = p.lay->chunk0[p.ndom];
+  __shared__ int s_bad;
+  const int nchunks = p.lay->nchunks;
   for (int it = blockIdx.x; it < nchunks; it += gridDim.x) {
     if (threadIdx.x == 0) {
-      int lo = 0, hi = p.ndom - 1;  // last domain with chunk0 <= it
+      int lo = 0, hi = p.ndom - 1;  // last domain whose first chunk is <= it
       while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (p.lay->chunk0[mid] <= it) lo = mid; else hi = mid - 1;
+        if (p.lay->dom[mid].chunk0 <= it) lo = mid; else hi = mid - 1;
       }
       s_dom = lo;
+      s_bad = 0;
     }
     __syncthreads();
     const int dmi = s_dom;
-    __syncthreads();
-    const DomDev dm = p.lay->dom[dmi];
-    const long long c0 = (long long)(it - p.lay->chunk0[dmi]) * kNaChunk;
+    const NaDesc dm = p.lay->dom[dmi];
+    const long long c0 = (long long)(it - dm.chunk0) * kNaChunk;
     unsigned long long mx[4] = {0ull, 0ull, 0ull, 0ull};
     for (int c = threadIdx.x; c < kNaChunk; c += blockDim.x) {
       const long long idx = c0 + c;
@@ -83,7 +117,10 @@ __global__ void __launch_bounds__(256) na_speeds_kernel(NaParams p) {
 #pragma unroll
       for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
       Prim w;
-      if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) continue;
+      if (!cons2prim_exact<PHYS, NV>(u, p.gamma, p.ndim, w)) {
+        s_bad = 1;  // benign race: every writer stores 1
+        continue;
+      }
       double rate = 0.0;
 #pragma unroll
       for (int d = 0; d < 3; d++) {
@@ -108,8 +145,9 @@ __global__ void __launch_bounds__(256) na_speeds_kernel(NaParams p) {
 #pragma unroll
       for (int q = 0; q < 4; q++) {
         const unsigned long long xw = warp_max_u64(lane < nw ? red[q][lane] : 0ull);
-        if (lane == 0 && xw) atomicMax(&p.lay_w->slot[dmi][q], xw);
+        if (lane == 0 && xw) atomicMax(&p.lay->slot[dmi][q], xw);
       }
+      if (lane == 0 && s_bad) atomicOr(&p.lay->bad[dmi], 1u);
     }
     __syncthreads();
   }
@@ -123,11 +161,17 @@ struct NaDtParams {
   int glm, ndim, global_min;
 };
 
+// dt per domain as amrfd_dt computes it; NaN for a domain that holds a non-physical
+// cell (with the global scope: for every domain, when any holds one).
 __global__ void __launch_bounds__(1024) na_dt_kernel(NaDtParams p) {
   __shared__ long long red[32];
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  const double qnan = __longlong_as_double(0x7ff8000000000000LL);
   long long best = 0x7fffffffffffffffLL;
   for (int dmi = threadIdx.x; dmi < p.ndom; dmi += blockDim.x) {
-    const DomDev& dm = p.lay->dom[dmi];
+    const NaDesc& dm = p.lay->dom[dmi];
     const unsigned long long* s = p.lay->slot[dmi];
     double rate;
     if (p.glm) {
@@ -140,6 +184,10 @@ __global__ void __launch_bounds__(1024) na_dt_kernel(NaDtParams p) {
     }
     double dt = rate > 0.0 ? __ddiv_rn(p.cfl, rate) : __longlong_as_double(0x7ff0000000000000LL);
     dt = imin(dt, __dsub_rn(p.t_end, p.t));
+    if (p.lay->bad[dmi]) {
+      dt = qnan;
+      s_bad = 1;
+    }
     p.dt_out[dmi] = dt;
     const long long k = okey(dt);
     best = k < best ? k : best;
@@ -161,7 +209,7 @@ __global__ void __launch_bounds__(1024) na_dt_kernel(NaDtParams p) {
   }
   __syncthreads();
   const long long kb = red[0];
-  const double dmin = bitsd(kb ^ ((kb >> 63) & 0x7fffffffffffffffLL));
+  const double dmin = s_bad ? qnan : bitsd(kb ^ ((kb >> 63) & 0x7fffffffffffffffLL));
   for (int dmi = threadIdx.x; dmi < p.ndom; dmi += blockDim.x) p.dt_out[dmi] = dmin;
 }
 
@@ -184,6 +232,21 @@ extern "C" int amrfd_dt_noalloc(const amrfd_config* cfg, const amrfd_domain* dom
   if (cfg->ndim < 1 || cfg->ndim > 3) return na_fail("ndim must be 1, 2 or 3");
   if (cfg->dt_scope != AMRFD_DT_PER_DOMAIN && cfg->dt_scope != AMRFD_DT_GLOBAL) return na_fail("bad dt_scope");
   if (!(cfg->gamma > 1.0) || !(cfg->cfl > 0.0)) return na_fail("gamma must exceed 1 and cfl be positive");
+  // every descriptor is checked before anything is enqueued
+  long long nch = 0;
+  for (int i = 0; i < ndomain; i++) {
+    const amrfd_domain& d = domains[i];
+    for (int k = 0; k < 3; k++) {
+      if (d.n[k] < 1 || d.nb[k] < 1 || d.n[k] % d.nb[k]) return na_fail("bad n or nb");
+      if (k >= cfg->ndim && d.n[k] != 1) return na_fail("n must be 1 beyond ndim");
+      if (k < cfg->ndim && !(d.dx[k] > 0.0)) return na_fail("dx must be positive");
+    }
+    if (d.offset < 0) return na_fail("negative offset");
+    const long long nc = (long long)d.n[0] * d.n[1] * d.n[2];
+    if (nc > 0x7fffffffLL) return na_fail("domain too large");
+    nch += (nc + kNaChunk - 1) / kNaChunk;
+    if (nch > 0x7fffffffLL) return na_fail("too many cells");
+  }
   const int nv = cfg->physics == AMRFD_EULER ? 2 + cfg->ndim : 9;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return AMRFD_ERR_CUDA;
@@ -200,45 +263,38 @@ extern "C" int amrfd_dt_noalloc(const amrfd_config* cfg, const amrfd_domain* dom
     g_na_dev_ptr[dev] = ptr;
   }
   NaLayout* lay = (NaLayout*)g_na_dev_ptr[dev];
-  int nblk = 0, nch = 0;
-  for (int i = 0; i < ndomain; i++) {
-    const amrfd_domain& d = domains[i];
-    DomDev& dm = g_na_host.dom[i];
-    std::memset(&dm, 0, sizeof dm);
-    for (int k = 0; k < 3; k++) {
-      if (d.n[k] < 1 || d.nb[k] < 1 || d.n[k] % d.nb[k]) return na_fail("bad n or nb");
-      if (k >= cfg->ndim && d.n[k] != 1) return na_fail("n must be 1 beyond ndim");
-      if (k < cfg->ndim && !(d.dx[k] > 0.0)) return na_fail("dx must be positive");
-      dm.n[k] = d.n[k];
-      dm.nb[k] = d.nb[k];
-      dm.be[k] = d.n[k] / d.nb[k];
-      dm.bc[k][0] = d.bc[k][0];
-      dm.bc[k][1] = d.bc[k][1];
-      dm.dx[k] = d.dx[k];
+  // descriptors and work partition into the scratch, maxima and flags cleared, as
+  // kernel arguments in batches of kNaBatch domains
+  int nblk = 0, ch = 0;
+  for (int first = 0; first < ndomain; first += kNaBatch) {
+    const int count = ndomain - first < kNaBatch ? ndomain - first : kNaBatch;
+    g_na_up.lay = lay;
+    g_na_up.first = first;
+    g_na_up.count = count;
+    g_na_up.nchunks = (int)nch;
+    for (int i = 0; i < count; i++) {
+      const amrfd_domain& d = domains[first + i];
+      NaDesc& dm = g_na_up.d[i];
+      std::memset(&dm, 0, sizeof dm);
+      for (int k = 0; k < 3; k++) {
+        dm.n[k] = d.n[k];
+        dm.nb[k] = d.nb[k];
+        dm.be[k] = d.n[k] / d.nb[k];
+        dm.dx[k] = d.dx[k];
+      }
+      const long long nc = (long long)d.n[0] * d.n[1] * d.n[2];
+      dm.ncell = (int)nc;
+      dm.off = d.offset;
+      dm.block0 = nblk;
+      dm.chunk0 = ch;
+      nblk += d.nb[0] * d.nb[1] * d.nb[2];
+      ch += (int)((nc + kNaChunk - 1) / kNaChunk);
     }
-    if (d.offset < 0) return na_fail("negative offset");
-    const long long nc = (long long)d.n[0] * d.n[1] * d.n[2];
-    if (nc > 0x7fffffffLL) return na_fail("domain too large");
-    dm.ncell = (int)nc;
-    dm.off = d.offset;
-    dm.block0 = nblk;
-    nblk += d.nb[0] * d.nb[1] * d.nb[2];
-    g_na_host.chunk0[i] = nch;
-    const long long add = (nc + kNaChunk - 1) / kNaChunk;
-    if ((long long)nch + add > 0x7fffffffLL) return na_fail("too many cells");
-    nch += (int)add;
+    na_upload_kernel<<<1, 256, 0, s>>>(g_na_up);
+    if (cudaGetLastError() != cudaSuccess) return AMRFD_ERR_CUDA;
   }
-  g_na_host.chunk0[ndomain] = nch;
-  (void)nv;
-  // descriptors and work partition into the scratch; speed maxima cleared
-  if (cudaMemcpyAsync(lay->dom, g_na_host.dom, sizeof(DomDev) * ndomain, cudaMemcpyHostToDevice, s) != cudaSuccess ||
-      cudaMemcpyAsync(lay->chunk0, g_na_host.chunk0, sizeof(int) * (ndomain + 1), cudaMemcpyHostToDevice, s) !=
-          cudaSuccess ||
-      cudaMemsetAsync(lay->slot, 0, sizeof(unsigned long long) * 4 * ndomain, s) != cudaSuccess)
-    return AMRFD_ERR_CUDA;
   NaParams p{};
   p.lay = lay;
-  p.lay_w = lay;
   p.ndom = ndomain;
   p.active = active_dev;
   p.U = U;
@@ -246,7 +302,7 @@ extern "C" int amrfd_dt_noalloc(const amrfd_config* cfg, const amrfd_domain* dom
   p.ndim = cfg->ndim;
   int nsm = 0;
   if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return AMRFD_ERR_CUDA;
-  const int grid = nch < 8 * nsm ? (nch > 0 ? nch : 1) : 8 * nsm;
+  const int grid = nch < 8 * nsm ? (nch > 0 ? (int)nch : 1) : 8 * nsm;
   if (cfg->physics == AMRFD_MHD_GLM) na_speeds_kernel<PH_MHD, 9><<<grid, 256, 0, s>>>(p);
   else if (nv == 3) na_speeds_kernel<PH_EULER, 3><<<grid, 256, 0, s>>>(p);
   else if (nv == 4) na_speeds_kernel<PH_EULER, 4><<<grid, 256, 0, s>>>(p);

@@ -80,3 +80,36 @@ def test_create_rejects_bad_arguments_on_host(lib, bad):
     rc = lib.amrfd_create(ctypes.byref(h), ctypes.byref(cfg), A.domains_c(doms), len(doms), None, None)
     assert rc == A.ERR_INVALID_ARG
     assert not h.value
+
+
+def test_dt_noalloc_binding_rejects_bad_tensors_before_the_call():
+    """The kernels of amrfd_dt_noalloc trust the sizes they are given, so the binding checks
+    the flags, the output and the state first (no library call, no GPU needed)."""
+    torch = pytest.importorskip("torch")
+    from paper_1407_2052_gb300 import amrfd as A
+    from paper_1407_2052_gb300 import workloads as W
+    doms = [W.Domain((8, 8, 8), (0.1,) * 3), W.Domain((8, 8, 8), (0.1,) * 3, offset=9 * 512)]
+    U = torch.zeros(2 * 9 * 512, dtype=torch.float64)
+    out = torch.zeros(2, dtype=torch.float64)
+
+    def call(**kw):
+        args = dict(U=U, out=out, active=None)
+        args.update(kw)
+        A.dt_noalloc(A.MHD_GLM, 3, 5 / 3, 0.3, doms, args["U"], args["out"], active=args["active"])
+
+    with pytest.raises(TypeError):
+        call(active=torch.ones(2, dtype=torch.bool))
+    with pytest.raises(TypeError):
+        call(active=torch.ones(2, dtype=torch.int64))
+    with pytest.raises(ValueError):
+        call(active=torch.ones(1, dtype=torch.uint8))
+    with pytest.raises(TypeError):
+        call(active=torch.ones(4, dtype=torch.uint8)[::2])
+    with pytest.raises(TypeError):  # right size and type, but host memory
+        call(active=torch.ones(2, dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        call(out=torch.zeros(1, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        call(out=torch.zeros(2, dtype=torch.float32))
+    with pytest.raises(ValueError):
+        call(U=torch.zeros(9 * 512, dtype=torch.float64))

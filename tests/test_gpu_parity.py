@@ -110,6 +110,45 @@ def run_oracle(w, nsteps=1, fixed_dt=None):
     return U, dts
 
 
+def ssp_limit_run(w, cfl, recon, early):
+    """A run at the SSP-limit CFL compared in two ways. The first `early` steps (each side
+    computing its own CFL steps), before rounding has been amplified, are held to the
+    shocked-data tolerance: relative L1 <= 1e-10 with the same time steps bit for bit. The
+    whole run to t_end is held to ten times the oracle's own sensitivity to a 1e-15
+    perturbation of its input (at least 1e-10); that bound is printed (tagged SSP-LIMIT-TOL)."""
+    c, d = ocfg(w), odom(w.domains[0])
+    Ue, t_e, hs = w.U.copy(), 0.0, []
+    for _ in range(early):
+        h, _ = O.dt(c, d, Ue, cfl, t_e, w.t_end)
+        hs.append(h)
+        Ue, fl, _, _ = O.step(c, d, Ue, h)
+        assert fl == 0
+        t_e += h
+    Uo, t, n, fl = O.evolve(c, d, w.U, cfl, w.t_end)
+    Up, _, n2, _ = O.evolve(c, d, w.U * (1 + 1e-15), cfl, w.t_end)
+    assert fl == 0 and n2 == n
+    tol = 10 * rel_l1(Up, Uo, 1.0) + 1e-10
+    s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, cfl, w.domains, glm_cr=w.glm_cr, recon=recon)
+    U = dev(w.U.copy().ravel())
+    tg, ng = 0.0, 0
+    while tg < w.t_end * (1 - 1e-14):
+        dt = s.dt(U, tg, w.t_end)
+        h = float(dt[0].item())
+        s.step_batched(U, dt)
+        tg += h
+        ng += 1
+        if ng <= early:
+            assert h == hs[ng - 1], ng
+        if ng == early:
+            e_early = rel_l1(host(U, Ue.shape), Ue, 1.0)
+            assert e_early <= 1e-10, e_early
+    assert s.error() == A().OK and ng == n
+    e_end = rel_l1(host(U, Uo.shape), Uo, 1.0)
+    print("SSP-LIMIT-TOL cfl=%g recon=%d steps=%d early(%d)=%.3e end=%.3e tol=%.3e"
+          % (cfl, recon, n, early, e_early, e_end, tol))
+    assert e_end <= tol
+
+
 # --------------------------------------------------------------- single domains
 def test_sod_first_step_dt_alpha_bitwise():
     w = W.sod(512)
@@ -153,17 +192,16 @@ def test_brio_wu_shock_tube(cfl):
     """1D MHD Brio-Wu tube (Sec. 4.5.2), SSPRK(5,4)-MP5 to t = 0.2: at CFL 0.4 the same
     number of steps and relative L1 <= 1e-10 against the oracle. At the SSP limit 1.5
     (the paper's maximal-CFL run) the scheme amplifies rounding: the oracle itself moves
-    by ~1e-3 under a 1e-15 perturbation of its input, so there the GPU result must stay
-    within ten times the oracle's own sensitivity (and stay physical)."""
+    by ~1e-3 under a 1e-15 perturbation of its input (1.7e-13 after 10 steps, 1e-10 after
+    20, 3e-8 after 40). There the first 10 steps are held to 1e-10 and the end state to ten
+    times the oracle's own sensitivity (ssp_limit_run)."""
     w = W.brio_wu(512)
+    if cfl > 1.0:
+        ssp_limit_run(w, cfl, O.MP5, early=10)
+        return
     c, d = ocfg(w), odom(w.domains[0])
     Uo, t, n, fl = O.evolve(c, d, w.U, cfl, w.t_end)
     assert fl == 0
-    tol = 1e-10
-    if cfl > 1.0:
-        Up, _, n2, _ = O.evolve(c, d, w.U * (1 + 1e-15), cfl, w.t_end)
-        assert n2 == n
-        tol = 10 * rel_l1(Up, Uo, 1.0) + 1e-10
     s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, cfl, w.domains, glm_cr=w.glm_cr)
     U = dev(w.U.copy().ravel())
     tg, ng = 0.0, 0
@@ -173,7 +211,7 @@ def test_brio_wu_shock_tube(cfl):
         tg += float(dt[0].item())
         ng += 1
     assert s.error() == A().OK and ng == n
-    assert rel_l1(host(U, Uo.shape), Uo, 1.0) <= tol
+    assert rel_l1(host(U, Uo.shape), Uo, 1.0) <= 1e-10
 
 
 def test_vortex_smooth_100_steps():
@@ -575,24 +613,10 @@ def test_limo3_ragged_boxes(case):
 
 def test_limo3_brio_wu_ssprk43_at_cfl_2():
     """SSPRK(4,3)-LIMO3 Brio-Wu at its SSP limit CFL 2.0 (Sec. 4.5.2): same step count as
-    the oracle; the result within ten times the oracle's own sensitivity to a 1e-15
-    perturbation of its input (and at least 1e-10)."""
-    w = _limo(W.brio_wu(512), integrator=O.SSPRK43)
-    c, d = ocfg(w), odom(w.domains[0])
-    Uo, t, n, fl = O.evolve(c, d, w.U, 2.0, w.t_end)
-    Up, _, n2, _ = O.evolve(c, d, w.U * (1 + 1e-15), 2.0, w.t_end)
-    assert fl == 0 and n2 == n
-    tol = 10 * rel_l1(Up, Uo, 1.0) + 1e-10
-    s = A().Solver(w.physics, w.ndim, w.integrator, w.gamma, 2.0, w.domains, glm_cr=w.glm_cr, recon=O.LIMO3)
-    U = dev(w.U.copy().ravel())
-    tg, ng = 0.0, 0
-    while tg < w.t_end * (1 - 1e-14):
-        dt = s.dt(U, tg, w.t_end)
-        s.step_batched(U, dt)
-        tg += float(dt[0].item())
-        ng += 1
-    assert s.error() == A().OK and ng == n
-    assert rel_l1(host(U, Uo.shape), Uo, 1.0) <= tol
+    the oracle; the first 40 steps within 1e-10 (the oracle's own sensitivity to a 1e-15
+    input perturbation stays near 4e-15 there), the end state within ten times that
+    sensitivity at t_end (ssp_limit_run)."""
+    ssp_limit_run(_limo(W.brio_wu(512), integrator=O.SSPRK43), 2.0, O.LIMO3, early=40)
 
 
 def test_limo3_tiles_and_adjoint_unsupported():

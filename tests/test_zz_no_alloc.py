@@ -72,3 +72,83 @@ def test_noalloc_rejects_too_many_domains():
     rc = L.amrfd_dt_noalloc(ctypes.byref(cfg), A.domains_c(w.domains), len(w.domains), None,
                             ctypes.c_void_p(U.data_ptr()), ctypes.c_void_p(out.data_ptr()), 0.0, 1.0, None)
     assert rc == A.ERR_INVALID_ARG
+
+
+def _dt_both(A, w, U, dt_scope=0, t=0.0, t_end=float("inf"), active=None):
+    """(handle amrfd_dt, amrfd_dt_noalloc) on the same inputs, as numpy arrays."""
+    s = A.Solver.from_workload(w, dt_scope=dt_scope)
+    if active is not None:
+        s.set_active(active)
+    want = s.dt(U, t=t, t_end=t_end).cpu().numpy()
+    err = s.error()
+    s.close()
+    got = _via_c_abi(A, w, U, active=active, dt_scope=dt_scope, t=t, t_end=t_end)
+    return want, got, err
+
+
+def test_noalloc_more_shapes_bitwise():
+    """The 3- and 4-variable Euler kernels, the t_end clamp deciding the step, and domains
+    whose cell counts are not multiples of the 4096-cell work chunk beside smaller ones
+    (the chunk-to-domain search), with the global scope."""
+    from paper_1407_2052_gb300 import amrfd as A
+    w = W.sod(512)
+    U = torch.from_numpy(np.ascontiguousarray(w.U.ravel())).cuda()
+    want, got, _ = _dt_both(A, w, U, t=0.1, t_end=0.1 + 1e-7)
+    assert np.array_equal(got, want) and got[0] <= 1.0000001e-7
+    want, got, _ = _dt_both(A, w, U, t=0.0, t_end=0.2)
+    assert np.array_equal(got, want) and got[0] > 1e-7
+    w = W.sine_advection(96, ndim=2)
+    U = torch.from_numpy(np.ascontiguousarray(w.U.ravel())).cuda()
+    want, got, _ = _dt_both(A, w, U)
+    assert np.array_equal(got, want)
+    w = W.batched(nblocks=40, sizes=(8, 24))
+    assert {d.n[0] for d in w.domains} == {8, 24}
+    U = torch.from_numpy(w.U).cuda()
+    for scope in (A.DT_PER_DOMAIN, A.DT_GLOBAL):
+        want, got, _ = _dt_both(A, w, U, dt_scope=scope)
+        assert np.array_equal(got, want)
+
+
+def test_noalloc_flags_a_nonphysical_domain_with_nan():
+    """A domain with a cell of negative pressure gets dt = NaN (the handle's amrfd_dt leaves
+    the cell out and latches AMRFD_ERR_NONPHYSICAL); the other domains keep amrfd_dt's value.
+    With the global scope every domain gets NaN."""
+    from paper_1407_2052_gb300 import amrfd as A
+    w = W.batched(nblocks=12, sizes=(8, 12))
+    bad = 5
+    d = w.domains[bad]
+    w.U[d.offset + 4 * d.ncell + 17] = -1.0  # total energy below the kinetic + magnetic part
+    U = torch.from_numpy(w.U).cuda()
+    want, got, err = _dt_both(A, w, U)
+    assert err == A.ERR_NONPHYSICAL
+    assert np.isnan(got[bad])
+    keep = np.arange(len(w.domains)) != bad
+    assert np.array_equal(got[keep], want[keep])
+    _, got, _ = _dt_both(A, w, U, dt_scope=A.DT_GLOBAL)
+    assert np.all(np.isnan(got))
+    # the next call on physical data is unaffected by the flags the previous one left
+    w2 = W.batched(nblocks=12, sizes=(8, 12))
+    U2 = torch.from_numpy(w2.U).cuda()
+    want, got, err = _dt_both(A, w2, U2)
+    assert err == A.OK and np.array_equal(got, want)
+
+
+def test_noalloc_call_leaves_device_memory_unchanged():
+    """The point of the entry point: after the library is loaded and the first call has
+    looked up the scratch, further calls change neither torch's allocator statistics nor
+    the device's free memory."""
+    from paper_1407_2052_gb300 import amrfd as A
+    w = W.batched(nblocks=64)
+    U = torch.from_numpy(w.U).cuda()
+    act = torch.from_numpy(w.active).cuda()
+    out = torch.empty(len(w.domains), dtype=torch.float64, device="cuda")
+    A.dt_noalloc(w.physics, w.ndim, w.gamma, w.cfl, w.domains, U, out, active=act)
+    first = out.clone()
+    torch.cuda.synchronize()
+    before = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    for _ in range(3):
+        A.dt_noalloc(w.physics, w.ndim, w.gamma, w.cfl, w.domains, U, out, active=act)
+    torch.cuda.synchronize()
+    after = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved(), torch.cuda.mem_get_info()[0])
+    assert after == before
+    assert torch.equal(out, first)
