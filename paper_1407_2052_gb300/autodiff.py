@@ -36,14 +36,20 @@ def step(solver, U, dt):
 
 class _Rollout(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, U0, dt, solver, nsteps, every):
-        ctx.solver, ctx.nsteps, ctx.every = solver, nsteps, every
+    def forward(ctx, U0, dt, solver, nsteps, every, stats):
+        ctx.solver, ctx.nsteps, ctx.every, ctx.stats = solver, nsteps, every, stats
+        ev = _events(stats, 2)
+        if ev:
+            ev[0].record()
         U = U0.detach().clone()
         ckpts = []
         for n in range(nsteps):
             if n % every == 0:
                 ckpts.append(U.clone())
             solver.step_batched(U, dt)
+        if ev:
+            ev[1].record()
+            ctx.fwd_events = ev
         ctx.ckpts = ckpts
         ctx.save_for_backward(dt)
         return U
@@ -51,7 +57,7 @@ class _Rollout(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         (dt,) = ctx.saved_tensors
-        solver, nsteps, every = ctx.solver, ctx.nsteps, ctx.every
+        solver, nsteps, every, stats = ctx.solver, ctx.nsteps, ctx.every, ctx.stats
         g = g.contiguous().clone()
         gn = torch.empty_like(g)
         # the recomputation steps one work buffer (one captured graph, replayed) and keeps
@@ -60,7 +66,10 @@ class _Rollout(torch.autograd.Function):
         wb = getattr(solver, "_step_buf", None)
         if wb is None or wb.shape != g.shape or wb.device != g.device:
             wb = solver._step_buf = torch.empty_like(g)
-        for seg in reversed(range(len(ctx.ckpts))):
+        ev = _events(stats, 3 * len(ctx.ckpts))
+        for i, seg in enumerate(reversed(range(len(ctx.ckpts)))):
+            if ev:
+                ev[3 * i].record()
             start = seg * every
             count = min(every, nsteps - start)
             wb.copy_(ctx.ckpts[seg])
@@ -68,17 +77,39 @@ class _Rollout(torch.autograd.Function):
                 states[j].copy_(wb)
                 if j + 1 < count:
                     solver.step_batched(wb, dt)
+            if ev:
+                ev[3 * i + 1].record()
             for j in reversed(range(count)):
                 solver.adjoint(states[j], dt, g, gn)
                 g, gn = gn, g
-        return g, None, None, None, None
+            if ev:
+                ev[3 * i + 2].record()
+        if ev:
+            ev[-1].synchronize()
+            f0, f1 = ctx.fwd_events
+            stats["forward_ms"] = stats.get("forward_ms", 0.0) + f0.elapsed_time(f1)
+            stats["recompute_ms"] = stats.get("recompute_ms", 0.0) + sum(
+                ev[3 * i].elapsed_time(ev[3 * i + 1]) for i in range(len(ctx.ckpts)))
+            stats["adjoint_ms"] = stats.get("adjoint_ms", 0.0) + sum(
+                ev[3 * i + 1].elapsed_time(ev[3 * i + 2]) for i in range(len(ctx.ckpts)))
+            stats["backward_ms"] = stats.get("backward_ms", 0.0) + ev[0].elapsed_time(ev[-1])
+        return g, None, None, None, None, None
 
 
-def rollout(solver, U0, dt, nsteps, every):
-    """U after `nsteps` fixed-dt steps, differentiable w.r.t. U0 (checkpoint every `every` steps)."""
-    return _Rollout.apply(U0, dt, solver, nsteps, every)
+def _events(stats, n):
+    if stats is None:
+        return None
+    return [torch.cuda.Event(enable_timing=True) for _ in range(n)]
 
 
-def checkpointed_rollout(solver, U0, dt, nsteps, k):
+def rollout(solver, U0, dt, nsteps, every, stats=None):
+    """U after `nsteps` fixed-dt steps, differentiable w.r.t. U0 (checkpoint every `every` steps).
+    With a dict `stats`, the device time of the forward run, of the backward pass's
+    recomputation and of its adjoint steps is added to it (milliseconds, CUDA events on the
+    current stream; the backward pass then waits for its last event)."""
+    return _Rollout.apply(U0, dt, solver, nsteps, every, stats)
+
+
+def checkpointed_rollout(solver, U0, dt, nsteps, k, stats=None):
     """Alias of rollout: nsteps fixed-dt steps with checkpoints every k steps."""
-    return rollout(solver, U0, dt, nsteps, k)
+    return rollout(solver, U0, dt, nsteps, k, stats)

@@ -350,9 +350,10 @@ __device__ __forceinline__ void flux_sweep_carry(const double* g, const double* 
 // a face where one did, it forms them from the current differences (the operands of
 // the carried ones) and carries them; after a face where none did, it drops them and
 // forms them per face at failing faces only (mp5_rel2_r without CARRY).
+// Every lane in `lanes` must call this with the same slen (the face votes pair up).
 __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const double* h, int slen, double eps16,
-                                                    double* out, long long ostr, unsigned long long wmask) {
-  const unsigned lanes = __activemask();
+                                                    double* out, long long ostr, unsigned long long wmask,
+                                                    unsigned lanes) {
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
   double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
   double Pk3 = 0.0, Mk4 = 0.0, PM2 = 0.0, PM3 = 0.0, MM3 = 0.0, MM4 = 0.0;
@@ -485,15 +486,26 @@ __device__ __forceinline__ bool item_live(const FluxParams& p, const FluxItem& i
   return live;
 }
 
-// Phase B of a flux item: one thread per (line, variable) sweeps the faces and stores
-// L_D of the segment's cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
-// 2: LIMO3). Sweeps start, start + stride, ...
+// Parts of a segment's sweep: a segment of 32 cells or more is swept in np parts of
+// at least 16 cells (part q covers cells [q slen/np, (q+1) slen/np)), one thread per
+// (part, line, variable); each part recomputes the face at its left end, as a
+// 16-cell segment does. Longer segments then cost less halo work in phase A (6 cells
+// per segment) without leaving phase-B threads idle.
+constexpr int kPartMin = 16;
+__device__ __forceinline__ int sweep_parts(int slen) { return slen >= 2 * kPartMin ? slen / kPartMin : 1; }
+
+// Phase B of a flux item: one thread per (part, line, variable) sweeps the part's faces
+// and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
+// 2: LIMO3). The loop runs warp by warp: every lane of a warp takes the same number of
+// trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work.
+// A warp whose lanes hold parts of different lengths takes the vote-free carried sweep
+// (same fluxes).
 template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                             const int o[3], bool all_live, const double* sm, int start,
-                                             int stride) {
+                                             const int o[3], bool all_live, const double* sm) {
   constexpr bool REC = MODE == 1;
   const int nl = it.nl, slen = it.slen;
+  const int np = sweep_parts(slen);
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
   // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
   const double eps16 = 16.0 * 1e-10;
@@ -513,29 +525,48 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   }
   const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
   double* Ld = p.L[D] + dm.off;
-  for (int t = start; t < nl * NV; t += stride) {
-    const int v = t / nl, pl = t - v * nl;
-    const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS;
-    const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS;
+  const int total = nl * NV * np;
+  const int lane = threadIdx.x & 31;
+  for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
+    const int t = t0 + lane;
+    const bool valid = t < total;
+    int pl = 0, v = 0, q = 0, p0 = 0, plen = 0;
+    if (valid) {
+      pl = t % nl;
+      const int r = t / nl;
+      v = r % NV;
+      q = r / NV;
+      p0 = q * slen / np;
+      plen = (q + 1) * slen / np - p0;
+    }
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    const int pmin = __reduce_min_sync(0xffffffffu, valid ? plen : 0x7fffffff);
+    const int pmax = __reduce_max_sync(0xffffffffu, valid ? plen : 0);
+    if (!valid) continue;
+    const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS + p0;
+    const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS + p0;
     const int line = it.l0 + pl;
     const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
     int x[3];
     x[od1] = o[od1] + a1;
     x[od2] = o[od2] + a2;
-    x[D] = o[D] + it.s0;
+    x[D] = o[D] + it.s0 + p0;
     double* out = Ld + (long long)v * dm.ncell + ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
-    unsigned short *tp = nullptr, *tm = nullptr;
-    if (REC) {
-      const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
-      tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
-      tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
-    }
+    const unsigned long long pmask = (wmask >> p0) & (plen >= 64 ? ~0ull : ((1ull << plen) - 1ull));
     if constexpr (MODE == 2) {
       const double rdx = p.limo3_r * dm.dx[D];
-      limo3_sweep(g, h, slen, 0.25 / (rdx * rdx), out, ostr, wmask);
+      limo3_sweep(g, h, plen, 0.25 / (rdx * rdx), out, ostr, pmask);
+    } else if constexpr (REC) {
+      const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
+      unsigned short* tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
+      unsigned short* tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
+      // a part records the faces it owns: its left face and interior faces; the
+      // segment's last part also the faces the segment owns at its right end
+      const int fe = q == np - 1 ? fend : f0 + p0 + plen;
+      flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask);
     } else {
-      if constexpr (REC) flux_sweep_carry<true>(g, h, slen, eps16, tp, tm, f0, fend, out, ostr, wmask);
-      else flux_sweep_adaptive(g, h, slen, eps16, out, ostr, wmask);
+      if (pmin == pmax) flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
+      else flux_sweep_carry<false>(g, h, plen, eps16, nullptr, nullptr, 0, 0, out, ostr, pmask);
     }
   }
 }
@@ -550,7 +581,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   const double alpha = item_alpha<D>(p, it, ch2);
   flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch2, sm, threadIdx.x, blockDim.x);
   __syncthreads();
-  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm, threadIdx.x, blockDim.x);
+  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm);
   __syncthreads();
 }
 
