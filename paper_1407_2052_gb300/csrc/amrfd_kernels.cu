@@ -486,20 +486,24 @@ __device__ __forceinline__ bool item_live(const FluxParams& p, const FluxItem& i
   return live;
 }
 
-// Parts of a segment's sweep: a segment of 32 cells or more is swept in np parts of
-// at least 16 cells (part q covers cells [q slen/np, (q+1) slen/np)), one thread per
-// (part, line, variable); each part recomputes the face at its left end, as a
-// 16-cell segment does. Longer segments then cost less halo work in phase A (6 cells
-// per segment) without leaving phase-B threads idle.
+// Parts of a segment's sweep: a segment of 32 cells or more is swept in np equal parts
+// of at least 16 cells (np the largest divisor of slen up to slen/16), one thread per
+// (variable, part, line); each part recomputes the face at its left end, as a 16-cell
+// segment does. Longer segments then cost less halo work in phase A (6 cells per
+// segment) without leaving phase-B threads idle. Equal parts keep every sweep of an
+// item equally long, which the adaptive sweep's per-face votes need.
 constexpr int kPartMin = 16;
-__device__ __forceinline__ int sweep_parts(int slen) { return slen >= 2 * kPartMin ? slen / kPartMin : 1; }
+__device__ __forceinline__ int sweep_parts(int slen) {
+  int np = slen / kPartMin;
+  while (np > 1 && slen % np) np--;
+  return np > 1 ? np : 1;
+}
 
-// Phase B of a flux item: one thread per (part, line, variable) sweeps the part's faces
+// Phase B of a flux item: one thread per (variable, part, line) sweeps the part's faces
 // and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
 // 2: LIMO3). The loop runs warp by warp: every lane of a warp takes the same number of
-// trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work.
-// A warp whose lanes hold parts of different lengths takes the vote-free carried sweep
-// (same fluxes).
+// trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work,
+// all of them sweeping parts of the same length.
 template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
                                              const int o[3], bool all_live, const double* sm) {
@@ -530,18 +534,16 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
     const int t = t0 + lane;
     const bool valid = t < total;
-    int pl = 0, v = 0, q = 0, p0 = 0, plen = 0;
-    if (valid) {
+    const int plen = slen / np;
+    int pl = 0, v = 0, q = 0;
+    if (valid) {  // a warp holds consecutive parts and lines of one variable
       pl = t % nl;
       const int r = t / nl;
-      v = r % NV;
-      q = r / NV;
-      p0 = q * slen / np;
-      plen = (q + 1) * slen / np - p0;
+      q = r % np;
+      v = r / np;
     }
+    const int p0 = q * plen;
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
-    const int pmin = __reduce_min_sync(0xffffffffu, valid ? plen : 0x7fffffff);
-    const int pmax = __reduce_max_sync(0xffffffffu, valid ? plen : 0);
     if (!valid) continue;
     const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS + p0;
     const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS + p0;
@@ -565,8 +567,7 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
       const int fe = q == np - 1 ? fend : f0 + p0 + plen;
       flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask);
     } else {
-      if (pmin == pmax) flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
-      else flux_sweep_carry<false>(g, h, plen, eps16, nullptr, nullptr, 0, 0, out, ostr, pmask);
+      flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
     }
   }
 }

@@ -74,11 +74,11 @@ def test_noalloc_rejects_too_many_domains():
     assert rc == A.ERR_INVALID_ARG
 
 
-def _dt_both(A, w, U, dt_scope=0, t=0.0, t_end=float("inf"), active=None):
-    """(handle amrfd_dt, amrfd_dt_noalloc) on the same inputs, as numpy arrays."""
+def _dt_both(A, w, U, dt_scope=0, t=0.0, t_end=float("inf")):
+    """(handle amrfd_dt, amrfd_dt_noalloc) on the same inputs and the workload's active
+    flags, as numpy arrays, and the handle's error latch."""
     s = A.Solver.from_workload(w, dt_scope=dt_scope)
-    if active is not None:
-        s.set_active(active)
+    active = torch.from_numpy(w.active).cuda() if w.active is not None else None
     want = s.dt(U, t=t, t_end=t_end).cpu().numpy()
     err = s.error()
     s.close()
@@ -107,6 +107,10 @@ def test_noalloc_more_shapes_bitwise():
     for scope in (A.DT_PER_DOMAIN, A.DT_GLOBAL):
         want, got, _ = _dt_both(A, w, U, dt_scope=scope)
         assert np.array_equal(got, want)
+    w.active = None  # every block active
+    for scope in (A.DT_PER_DOMAIN, A.DT_GLOBAL):
+        want, got, _ = _dt_both(A, w, U, dt_scope=scope)
+        assert np.array_equal(got, want) and np.all(np.isfinite(got))
 
 
 def test_noalloc_flags_a_nonphysical_domain_with_nan():
@@ -115,7 +119,7 @@ def test_noalloc_flags_a_nonphysical_domain_with_nan():
     With the global scope every domain gets NaN."""
     from paper_1407_2052_gb300 import amrfd as A
     w = W.batched(nblocks=12, sizes=(8, 12))
-    bad = 5
+    bad = int(np.flatnonzero(w.active)[2])
     d = w.domains[bad]
     w.U[d.offset + 4 * d.ncell + 17] = -1.0  # total energy below the kinetic + magnetic part
     U = torch.from_numpy(w.U).cuda()
