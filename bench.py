@@ -490,28 +490,38 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- end to end through the public API with host buffers (pinned): every step uploads
     # its input state host -> device and downloads its result device -> host, and the next
-    # step of that trajectory uploads the downloaded result. Two trajectories alternate, one
-    # from the timed region's first state and one from its midpoint, so that together they
-    # take exactly the K steps timed above and one's copies overlap the other's compute.
-    ka = (args.steps + 1) // 2
+    # step of that trajectory uploads the downloaded result. NT trajectories take turns, each
+    # starting from the state the timed region had at its first step of that trajectory, so
+    # that together they take exactly the K steps timed above; while one computes, the
+    # others' copies run on an upload and a download stream.
+    NT = min(3, args.steps)
+    starts = [(args.steps * i + NT - 1) // NT for i in range(NT + 1)]   # step index of each start
     U.copy_(UW)
-    for _ in range(ka):
+    first = []
+    for i in range(args.steps):
+        if i in starts[:NT]:
+            first.append(U.clone())
         one_step()
-    UM = U.clone()
-    hst = [torch.empty(U.shape, dtype=U.dtype).pin_memory() for _ in range(2)]
+    hst = [torch.empty(U.shape, dtype=U.dtype).pin_memory() for _ in range(NT)]
     nbytes = hst[0].numel() * 8
-    bufs = [U, torch.empty_like(U)]
+    bufs = [U] + [torch.empty_like(U) for _ in range(NT - 1)]
     up, down = torch.cuda.Stream(), torch.cuda.Stream()   # host->device, device->host
-    dts = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in range(2)]
-    ev_in = [torch.cuda.Event() for _ in range(2)]
-    ev_out = [torch.cuda.Event() for _ in range(2)]
-    ev_free = [torch.cuda.Event() for _ in range(2)]
+    dts = [torch.empty(1, dtype=torch.float64, device="cuda") for _ in range(NT)]
+    ev_in = [torch.cuda.Event() for _ in range(NT)]
+    ev_out = [torch.cuda.Event() for _ in range(NT)]
+    ev_free = [torch.cuda.Event() for _ in range(NT)]
+    lens = [starts[i + 1] - starts[i] for i in range(NT)]
 
-    def e2e_steps(k):
-        for i in range(k):
-            b = i & 1
+    def e2e_steps(lengths):
+        done = [0] * NT
+        i = 0
+        while any(done[b] < lengths[b] for b in range(NT)):
+            b = i % NT
+            i += 1
+            if done[b] >= lengths[b]:
+                continue
             with torch.cuda.stream(up):
-                if i >= 2:
+                if done[b] > 0:
                     up.wait_event(ev_free[b])      # the trajectory's previous result is home
                 bufs[b].copy_(hst[b], non_blocking=True)
                 ev_in[b].record(up)
@@ -522,22 +532,25 @@ def run_ours(args, rank, world, local_rank):
                 down.wait_event(ev_out[b])
                 hst[b].copy_(bufs[b], non_blocking=True)
                 ev_free[b].record(down)
+            done[b] += 1
         stream.wait_stream(up)
         stream.wait_stream(down)
 
-    hst[0].copy_(UW)
-    hst[1].copy_(UM)
-    e2e_steps(2)
+    for b in range(NT):
+        hst[b].copy_(first[b])
+    e2e_steps([1] * NT)
     torch.cuda.synchronize()
-    hst[0].copy_(UW)
-    hst[1].copy_(UM)
+    for b in range(NT):
+        hst[b].copy_(first[b])
     barrier()
     e0.record(stream)
-    e2e_steps(args.steps)
+    e2e_steps(lens)
     e1.record(stream)
     barrier()
-    # trajectory 0 ends where trajectory 1 began, trajectory 1 where the timed region ended
-    assert torch.equal(hst[0], UM.cpu()) and torch.equal(hst[1], Uend.cpu())
+    # each trajectory ends where the next began; the last where the timed region ended
+    for b in range(NT - 1):
+        assert torch.equal(hst[b], first[b + 1].cpu())
+    assert torch.equal(hst[NT - 1], Uend.cpu())
     e2e_ms = e0.elapsed_time(e1)
     _, e2e_value = aggregate(e2e_ms, ncell, args.steps, world, dist, "cuda")
 
@@ -585,14 +598,14 @@ def run_ours(args, rank, world, local_rank):
                          "frac_step_of_nominal_7900": value / world * BYTES_PER_CELL_UPDATE / 1e9 / 7900.0},
         "e2e": {"value": e2e_value, "unit": "cell-updates/s", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes,
-                "note": "pinned host buffers; the K timed steps as two alternating trajectories, each "
+                "note": "pinned host buffers; the K timed steps as three trajectories taking turns, each "
                         "step uploading its trajectory's last downloaded result; copies on two streams "
-                        "overlap the other trajectory's compute"},
+                        "overlap the other trajectories' compute"},
         "clocks": clocks,
     }
     tile = list(s.get_tile())
     s.close()
-    del U, U0, UW, UM, Uend, bufs, hst
+    del U, U0, UW, Uend, bufs, hst, first
     torch.cuda.empty_cache()
     if rank == 0 and world == 1 and not args.no_extras:
         out["batched"] = batched_extra(torch, A, W)
