@@ -275,32 +275,15 @@ int compact(amrfd_handle* h, cudaStream_t s) {
   return AMRFD_OK;
 }
 
-// Parts of a segment's sweep (as the kernels count them): the largest divisor of slen up
-// to slen/16.
-int sweep_parts_host(int slen) {
-  int np = slen / 16;
-  while (np > 1 && slen % np) np--;
-  return np > 1 ? np : 1;
-}
-
-// Shared memory of the flux pass: every warp holds G^{+-} of up to flux_P lines of one
-// variable, at a line stride of flux_SS doubles (the longest segment + 6 halo cells, odd:
-// conflict-free 64-bit lines); flux_P lines at that stride fill the warp's 32 lanes with
-// sweep parts.
-void flux_layout(const amrfd_handle* h, int seg, int lines, int* P, int* SS) {
+int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
   // segments run through blocks, never beyond the domain nor longer than seg
   int maxext = 1;
   for (auto& dm : h->hdom)
     for (int d = 0; d < h->cfg.ndim; d++) maxext = std::max(maxext, dm.n[d]);
   const int S = std::min(seg, maxext);
-  *SS = (S + 2 * kGhost) | 1;
-  *P = std::max(1, std::min(lines, 32 / sweep_parts_host(S)));
-}
-
-int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
-  int P = 0, SS = 0;
-  flux_layout(h, seg, lines, &P, &SS);
-  size_t smem = sizeof(double) * (threads / 32) * 2 * (size_t)P * SS;
+  int SS = S + 2 * kGhost;
+  if (SS % 2 == 0) SS++;  // odd stride in doubles: conflict-free 64-bit lines
+  size_t smem = sizeof(double) * 2 * h->nv * lines * SS;
   if (smem > 227 * 1024) return AMRFD_ERR_INVALID_ARG;
   h->seg = seg;
   h->lines = lines;
@@ -319,12 +302,12 @@ int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
   return AMRFD_OK;
 }
 
-// Threads of a flux CTA: one warp per task of a full item (a variable and a group of
-// lines that fills 32 lanes with sweep parts), at most kFluxMaxThreads.
+// Threads of a flux CTA: one per (sweep part, line, variable) of a full tile; a segment
+// of 32 cells or more is swept in parts of at least 16 cells (sweep_parts in the kernels).
 int default_threads(int nv, int lines, int seg) {
-  const int per_warp = std::max(1, std::min(lines, 32 / sweep_parts_host(seg)));
-  const int warps = nv * ((lines + per_warp - 1) / per_warp);
-  return std::max(64, std::min(32 * warps, kFluxMaxThreads));
+  const int parts = seg >= 32 ? seg / 16 : 1;
+  int t = ((nv * lines * parts + 31) / 32) * 32;
+  return std::max(64, std::min(t, kFluxMaxThreads));
 }
 
 unsigned long long* slot(amrfd_handle* h, int k) { return h->d_slot + (size_t)k * h->ndom * 4; }
@@ -362,8 +345,14 @@ FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int 
   p.araw0 = slot(h, 0);
   p.gm1 = h->cfg.gamma - 1.0;
   p.ndim = h->cfg.ndim;
-  flux_layout(h, h->seg, h->lines, &p.P, &p.SS);
-  p.lines = h->lines;
+  p.P = h->lines;
+  int S = 1;
+  for (auto& dm : h->hdom)
+    for (int d = 0; d < h->cfg.ndim; d++) S = std::max(S, std::min(dm.n[d], h->seg));
+  // segments are balanced, never longer than seg
+  int SS = std::min(S, h->seg) + 2 * kGhost;
+  if (SS % 2 == 0) SS++;
+  p.SS = SS;
   p.glm = h->cfg.physics == AMRFD_MHD_GLM;
   p.W = h->d_W;
   p.err = h->d_err;
@@ -1017,12 +1006,9 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
   for (int sg : segs) {
     for (int ln : lines_c) {
       if (h->cfg.ndim == 1 && ln != 1) continue;
-      // threads: one warp per task of an item, twice that, or seven warps (three CTAs per SM)
-      const int def = default_threads(h->nv, ln, sg);
-      const int cand[3] = {def, std::min(kFluxMaxThreads, 2 * def), 224};
-      for (int ci = 0; ci < 3; ci++) {
-        const int thr = cand[ci];
-        if ((ci == 1 && thr == def) || (ci == 2 && (thr == def || thr == cand[1]))) continue;
+      for (int mul = 1; mul <= 2; mul++) {
+        const int thr = std::min(kFluxMaxThreads, default_threads(h->nv, ln, sg) * mul);
+        if (mul == 2 && thr == default_threads(h->nv, ln, sg)) continue;
         if (configure_tile(h, sg, h->cfg.ndim == 1 ? 1 : ln, thr)) continue;
         if (compact(h, s)) continue;
         FluxParams fp = flux_params(h, U, U, 0);

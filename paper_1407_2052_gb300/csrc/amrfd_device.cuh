@@ -613,58 +613,36 @@ __device__ __forceinline__ void prim_w(const double* u, double gm1, double* w) {
   }
 }
 
-// Physical flux of variable V along D from U and its derived quantities, then the
-// Lax-Friedrichs split in doubled form G^{+-} = F +- alpha U (= 2 F^{+-}); psi's flux
-// is c_h^2 B_D. U(k) returns conserved variable k, W(q) derived quantity q (both may
-// load on demand): only the operands variable V needs are read.
-template <int PHYS, int NV, int D, int V, class UF, class WF>
-__device__ __forceinline__ void split_flux_v(UF&& U, WF&& W, double alpha, double ch2, double& gp, double& gm) {
-  const double uv = U(V);
-  double f;
-  if constexpr (PHYS == PH_EULER) {
+// Physical flux along D from U and its derived quantities, then the Lax-Friedrichs
+// split in doubled form G^{+-} = F +- alpha U (= 2 F^{+-}); psi's flux is c_h^2 B_D.
+template <int PHYS, int NV, int D>
+__device__ __forceinline__ void split_flux_w(const double* u, const double* w, double alpha, double ch2,
+                                             double* gp, double* gm) {
+  double f[NV];
+  if (PHYS == PH_EULER) {
     constexpr int nm = NV - 2;
-    if constexpr (V == 0) f = U(1 + D);
-    else if constexpr (V <= nm) f = (V - 1 == D) ? fma(W(D), uv, W(nm)) : W(D) * uv;
-    else f = W(D) * (uv + W(nm));
+    const double p = w[nm], vd = w[D];
+    f[0] = u[1 + D];
+#pragma unroll
+    for (int k = 0; k < nm; k++) f[1 + k] = (k == D) ? fma(vd, u[1 + k], p) : vd * u[1 + k];
+    f[NV - 1] = vd * (u[NV - 1] + p);
   } else {
-    if constexpr (V == 0) {
-      f = U(1 + D);
-    } else if constexpr (V <= 3) {
-      const double bd = U(5 + D);
-      f = fma(W(D), uv, -bd * U(5 + V - 1));
-      if (V - 1 == D) f += W(3);
-    } else if constexpr (V == 4) {
-      const double bd = U(5 + D);
-      f = fma(W(D), uv + W(3), -bd * W(4));
-    } else if constexpr (V <= 7) {
-      if constexpr (V - 5 == D) {
-        f = U(8);
-      } else {
-        const double bd = U(5 + D);
-        f = fma(W(D), uv, -bd * W(V - 5));
-      }
-    } else {
-      f = ch2 * U(5 + D);
+    const double ptot = w[3], vb = w[4];
+    const double vd = w[D], bd = u[5 + D];
+    f[0] = u[1 + D];
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+      f[1 + k] = fma(vd, u[1 + k], -bd * u[5 + k]);
+      if (k == D) f[1 + k] += ptot;
+      f[5 + k] = (k == D) ? u[8] : fma(vd, u[5 + k], -bd * w[k]);
     }
+    f[4] = fma(vd, u[4] + ptot, -bd * vb);
+    f[8] = ch2 * bd;
   }
-  gp = fma(alpha, uv, f);
-  gm = fma(-alpha, uv, f);
-}
-
-// split_flux_v for a variable v known at run time (the same across a warp, so the
-// branches do not diverge); every operand index stays a compile-time constant.
-template <int PHYS, int NV, int D, class UF, class WF>
-__device__ __forceinline__ void split_flux_var(int v, UF&& U, WF&& W, double alpha, double ch2, double& gp,
-                                               double& gm) {
-  switch (v) {
-#define AMRFD_SFV(K)                                                                  \
-  case K:                                                                             \
-    if constexpr (K < NV) split_flux_v<PHYS, NV, D, (K < NV ? K : 0)>(U, W, alpha, ch2, gp, gm); \
-    break;
-    AMRFD_SFV(0) AMRFD_SFV(1) AMRFD_SFV(2) AMRFD_SFV(3) AMRFD_SFV(4)
-    AMRFD_SFV(5) AMRFD_SFV(6) AMRFD_SFV(7) AMRFD_SFV(8)
-#undef AMRFD_SFV
-    default: gp = gm = 0.0; break;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    gp[v] = fma(alpha, u[v], f[v]);
+    gm[v] = fma(-alpha, u[v], f[v]);
   }
 }
 

@@ -209,27 +209,23 @@ __device__ __forceinline__ double glm_speed(const unsigned long long* s0, int nd
   return ch;
 }
 
-// One warp's task of a flux item: variable v of the item's lines l_beg .. l_beg+ln-1.
-// Phase A puts G^{+-}_v of those lines (segment + halo, ss doubles apart) into the
-// warp's shared memory, cells start at the lane, then every 32nd.
-struct WarpTask {
-  int v, l_beg, ln, np, plen, ss;
-};
-
+// Phase A of a flux item: the tile's G^{+-} (lines x segment + halo) into shared
+// memory, cells start, start + stride, ... of the tile.
 template <int PHYS, int NV, int D>
 __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                             const int o[3], double alpha, double ch2, const WarpTask& tk,
-                                             double* gsm, double* hsm) {
+                                             const int o[3], double alpha, double ch2, double* sm, int start,
+                                             int stride) {
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
   const int W = it.slen + 2 * kGhost;
-  const int ln = tk.ln;
+  const int nl = it.nl;
+  const int P = p.P, SS = p.SS;
   const double gm1 = p.gm1;
-  for (int c = threadIdx.x & 31; c < ln * W; c += 32) {
+  for (int c = start; c < nl * W; c += stride) {
     int pl, j;
     if (D == 0) { pl = c / W; j = c - pl * W; }
-    else { j = c / ln; pl = c - j * ln; }
-    const int line = it.l0 + tk.l_beg + pl;
+    else { j = c / nl; pl = c - j * nl; }
+    const int line = it.l0 + pl;
     const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
     int x[3];
     x[od1] = o[od1] + a1;
@@ -246,35 +242,37 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
       g = b == 0 ? g - dm.n[D] : (b == 1 ? dm.n[D] - 1 : 2 * dm.n[D] - 1 - g);
     }
     x[D] = g;
-    AMRFD_GUARD(p.err, g >= 0 && g < dm.n[D] && x[od1] < dm.n[od1] && x[od2] < dm.n[od2] && pl < tk.ln &&
-                j < tk.ss && (pl + 1) * tk.ss <= p.P * p.SS, continue)
+    AMRFD_GUARD(p.err, g >= 0 && g < dm.n[D] && x[od1] < dm.n[od1] && x[od2] < dm.n[od2] && pl < P && j < SS,
+                continue)
     const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
     const bool act = p.active[nbk] != 0;
     const double* base = act ? p.Uk : p.Un;
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
-    const long long nc = dm.ncell;
     const double* src = base + dm.off + idx;
-    auto U = [&](int k) {
-      const double y = src[(long long)k * nc];
-      return ((odd >> k) & 1u) ? dneg(y) : y;
-    };
-    double gp, gmn;
+    constexpr int NW = NumW<PHYS, NV>::value;
+    double u[NV], w[NW], gp[NV], gmn[NV];
+#pragma unroll
+    for (int v = 0; v < NV; v++) u[v] = src[(long long)v * dm.ncell];
+    if (odd) {
+#pragma unroll
+      for (int v = 0; v < NV; v++)
+        if ((odd >> v) & 1u) u[v] = dneg(u[v]);
+    }
     // derived quantities: stored by the pass that produced U^(k) for active cells;
     // recomputed for passive neighbours (U^n) and mirror images
     if (p.W && act && !odd) {
       const double* ws = p.W + dm.woff + idx;
-      split_flux_var<PHYS, NV, D>(tk.v, U, [&](int q) { return ws[(long long)q * nc]; }, alpha, ch2, gp, gmn);
-    } else {
-      constexpr int NW = NumW<PHYS, NV>::value;
-      double u[NV], w[NW];
 #pragma unroll
-      for (int k = 0; k < NV; k++) u[k] = U(k);
+      for (int q = 0; q < NW; q++) w[q] = ws[(long long)q * dm.ncell];
+    } else {
       prim_w<PHYS, NV>(u, gm1, w);
-      split_flux_var<PHYS, NV, D>(tk.v, [&](int k) { return u[k]; }, [&](int q) { return w[q]; }, alpha, ch2, gp,
-                                  gmn);
     }
-    gsm[pl * tk.ss + j] = gp;
-    hsm[pl * tk.ss + j] = gmn;
+    split_flux_w<PHYS, NV, D>(u, w, alpha, ch2, gp, gmn);
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      sm[((0 * NV + v) * P + pl) * SS + j] = gp[v];
+      sm[((1 * NV + v) * P + pl) * SS + j] = gmn[v];
+    }
   }
 }
 
@@ -489,11 +487,11 @@ __device__ __forceinline__ bool item_live(const FluxParams& p, const FluxItem& i
 }
 
 // Parts of a segment's sweep: a segment of 32 cells or more is swept in np equal parts
-// of at least 16 cells (np the largest divisor of slen up to slen/16); each part
-// recomputes the face at its left end, as a 16-cell segment does. Longer segments then
-// cost less halo work in phase A (6 cells per segment) without leaving lanes idle in
-// phase B. Equal parts keep every sweep of a warp equally long, which the adaptive
-// sweep's per-face votes need.
+// of at least 16 cells (np the largest divisor of slen up to slen/16), one thread per
+// (variable, part, line); each part recomputes the face at its left end, as a 16-cell
+// segment does. Longer segments then cost less halo work in phase A (6 cells per
+// segment) without leaving phase-B threads idle. Equal parts keep every sweep of an
+// item equally long, which the adaptive sweep's per-face votes need.
 constexpr int kPartMin = 16;
 __device__ __forceinline__ int sweep_parts(int slen) {
   int np = slen / kPartMin;
@@ -501,61 +499,27 @@ __device__ __forceinline__ int sweep_parts(int slen) {
   return np > 1 ? np : 1;
 }
 
-// Phase B of a warp's task: lane (part q, line pl), pl fastest, sweeps part q of line pl
-// of variable v and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter
-// pieces; 2: LIMO3).
+// Phase B of a flux item: one thread per (variable, part, line) sweeps the part's faces
+// and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
+// 2: LIMO3). The loop runs warp by warp: every lane of a warp takes the same number of
+// trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work,
+// all of them sweeping parts of the same length.
 template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                             const int o[3], unsigned long long wmask, const WarpTask& tk,
-                                             const double* gsm, const double* hsm) {
+                                             const int o[3], bool all_live, const double* sm) {
   constexpr bool REC = MODE == 1;
+  const int nl = it.nl, slen = it.slen;
+  const int np = sweep_parts(slen);
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
   // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
   const double eps16 = 16.0 * 1e-10;
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
-  const int lane = threadIdx.x & 31;
-  const bool valid = lane < tk.ln * tk.np;
-  const unsigned vm = __ballot_sync(0xffffffffu, valid);
-  if (!valid) return;
-  const int pl = lane % tk.ln, q = lane / tk.ln;
-  const int plen = tk.plen, p0 = q * plen, v = tk.v;
-  const double* g = gsm + pl * tk.ss + p0;
-  const double* h = hsm + pl * tk.ss + p0;
-  const int line = it.l0 + tk.l_beg + pl;
-  const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
-  int x[3];
-  x[od1] = o[od1] + a1;
-  x[od2] = o[od2] + a2;
-  x[D] = o[D] + it.s0 + p0;
-  const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
-  double* out = p.L[D] + dm.off + (long long)v * dm.ncell + ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
-  const unsigned long long pmask = (wmask >> p0) & (plen >= 64 ? ~0ull : ((1ull << plen) - 1ull));
-  if constexpr (MODE == 2) {
-    const double rdx = p.limo3_r * dm.dx[D];
-    limo3_sweep(g, h, plen, 0.25 / (rdx * rdx), out, ostr, pmask);
-  } else if constexpr (REC) {
-    const int f0 = o[D] + it.s0;
-    const int fend = f0 + it.slen + ((dm.bc[D][1] != 0 && f0 + it.slen == dm.n[D]) ? 1 : 0);
-    const long long nlines = (long long)dm.n[od1] * dm.n[od2];
-    const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
-    unsigned short* tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
-    unsigned short* tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
-    // a part records the faces it owns: its left face and interior faces; the
-    // segment's last part also the faces the segment owns at its right end
-    const int fe = q == tk.np - 1 ? fend : f0 + p0 + plen;
-    flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask);
-  } else {
-    flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
-  }
-}
-
-// Cells of the segment inside active blocks (a segment through several blocks may cross
-// a passive one; every line of the item crosses the same blocks).
-template <int D>
-__device__ __forceinline__ unsigned long long segment_mask(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                                           const int o[3], bool all_live) {
-  const int slen = it.slen;
+  const int f0 = o[D] + it.s0;
+  const int fend = f0 + slen + ((dm.bc[D][1] != 0 && f0 + slen == dm.n[D]) ? 1 : 0);
+  const long long nlines = (long long)dm.n[od1] * dm.n[od2];
+  // cells of the segment inside active blocks (a segment through several blocks may
+  // cross a passive one; every line of the item crosses the same blocks)
   unsigned long long wmask = slen >= 64 ? ~0ull : ((1ull << slen) - 1ull);
   if (!all_live) {
     const int bstride = D == 0 ? 1 : (D == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
@@ -563,88 +527,97 @@ __device__ __forceinline__ unsigned long long segment_mask(const FluxParams& p, 
     for (int j = 0; j < slen; j++)
       if (!p.active[dm.block0 + bo + ((o[D] + it.s0 + j) / dm.be[D]) * bstride]) wmask &= ~(1ull << j);
   }
-  return wmask;
+  const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
+  double* Ld = p.L[D] + dm.off;
+  const int total = nl * NV * np;
+  const int lane = threadIdx.x & 31;
+  for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
+    const int t = t0 + lane;
+    const bool valid = t < total;
+    const int plen = slen / np;
+    int pl = 0, v = 0, q = 0;
+    if (valid) {  // a warp holds consecutive parts and lines of one variable
+      pl = t % nl;
+      const int r = t / nl;
+      q = r % np;
+      v = r / np;
+    }
+    const int p0 = q * plen;
+    const unsigned vm = __ballot_sync(0xffffffffu, valid);
+    if (!valid) continue;
+    const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS + p0;
+    const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS + p0;
+    const int line = it.l0 + pl;
+    const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
+    int x[3];
+    x[od1] = o[od1] + a1;
+    x[od2] = o[od2] + a2;
+    x[D] = o[D] + it.s0 + p0;
+    double* out = Ld + (long long)v * dm.ncell + ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
+    const unsigned long long pmask = (wmask >> p0) & (plen >= 64 ? ~0ull : ((1ull << plen) - 1ull));
+    if constexpr (MODE == 2) {
+      const double rdx = p.limo3_r * dm.dx[D];
+      limo3_sweep(g, h, plen, 0.25 / (rdx * rdx), out, ostr, pmask);
+    } else if constexpr (REC) {
+      const long long ld = (long long)(o[od2] + a2) * dm.n[od1] + (o[od1] + a1);
+      unsigned short* tp = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 0) * nlines + ld) * (dm.n[D] + 1);
+      unsigned short* tm = p.tape + dm.tape_off[D] + ((long long)(v * 2 + 1) * nlines + ld) * (dm.n[D] + 1);
+      // a part records the faces it owns: its left face and interior faces; the
+      // segment's last part also the faces the segment owns at its right end
+      const int fe = q == np - 1 ? fend : f0 + p0 + plen;
+      flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask);
+    } else {
+      flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
+    }
+  }
 }
 
-// Lines per warp task of an item: as many as fill 32 lanes with sweep parts and fit the
-// warp's shared memory (P lines at stride SS).
-__device__ __forceinline__ int task_lines(const FluxParams& p, const FluxItem& it) {
-  const int np = sweep_parts(it.slen);
-  const int ss = (it.slen + 2 * kGhost) | 1;
-  return max(1, min(min((int)it.nl, 32 / np), (p.P * p.SS) / ss));
-}
-
-// Task k of item `iti` (variable k % NV of line group k / NV) by one warp: phase A, the
-// warp's own barrier, phase B, the barrier again (the next task reuses the warp's
-// shared memory). The item, its domain and its splitting speed are read per task, so
-// that as little as possible stays live across the sweep.
+// One flux item by the whole CTA: phase A, barrier, phase B, barrier.
 template <int PHYS, int NV, int D, int MODE>
-__device__ __forceinline__ void flux_task(const FluxParams& p, int iti, int k, double* wsm) {
-  const FluxItem it = p.items[p.item0 + iti];
-  bool all_live = false;
-  item_live(p, it, all_live);
+__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
   const DomDev dm = load_dom(p.doms + it.dom);
   int o[3];
   block_coords(dm, it.blk, o);
   double ch2;
   const double alpha = item_alpha<D>(p, it, ch2);
-  const int lw = task_lines(p, it);
-  WarpTask tk;
-  tk.np = sweep_parts(it.slen);
-  tk.plen = it.slen / tk.np;
-  tk.ss = (it.slen + 2 * kGhost) | 1;  // odd stride in doubles: conflict-free 64-bit lines
-  tk.v = k % NV;
-  tk.l_beg = (k / NV) * lw;
-  tk.ln = min(lw, (int)it.nl - tk.l_beg);
-  double* gsm = wsm;
-  double* hsm = wsm + p.P * p.SS;
-  flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch2, tk, gsm, hsm);
-  __syncwarp();
-  const unsigned long long wmask = segment_mask<D>(p, dm, it, o, all_live);
-  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, wmask, tk, gsm, hsm);
-  __syncwarp();
+  flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch2, sm, threadIdx.x, blockDim.x);
+  __syncthreads();
+  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm);
+  __syncthreads();
 }
 
-// Flux pass by independent warps. A CTA walks its items (blockIdx.x, + gridDim.x, ...);
-// an item splits into tasks, one per variable and group of lines (task_lines), and the
-// CTA's warps take the tasks of its item sequence in turn, warp w the tasks whose running
-// index is w modulo the warps. No warp waits for another: each computes the split fluxes
-// of its own variable and lines (phase A) and sweeps them (phase B) in its own shared
-// memory. The warps of a CTA work on the same item at about the same time, so they share
-// its loads in L1.
-// 104 registers: the MP5 sweep with the task loop around it needs them without spilling,
-// and two CTAs of nine warps still fit an SM (2 x 288 x 104 < 65536).
 template <int PHYS, int NV, int MODE>
-__global__ void __maxnreg__(104) flux_kernel(FluxParams p) {
+__global__ void __launch_bounds__(kFluxMaxThreads, 2) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
+  __shared__ int s_it;
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
+  int it;
+  if (p.counter) {
+    if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
+    __syncthreads();
+    it = s_it;
+    __syncthreads();
+  } else {
+    it = blockIdx.x;
+  }
   constexpr int maxd = PHYS == PH_EULER ? NV - 2 : 3;
-  int k = threadIdx.x >> 5;  // this warp's next task, counted from the current item's first
-  for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
-    int ntask = 0, d = 0;
-    {
-      const FluxItem item = p.items[p.item0 + it];
-      bool all_live = false;
-      bool live = true;
-      AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.lines, p.SS, item), live = false)
-      live = live && item_live(p, item, all_live);
-      if (live) {
-        const int lw = task_lines(p, item);
-        ntask = NV * ((item.nl + lw - 1) / lw);
-        d = item.d;
-      }
+  while (it < nitems) {
+    const FluxItem item = p.items[p.item0 + it];
+    bool all_live = false;
+    bool live = true;
+    AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.P, p.SS, item), live = false)
+    live = live && item_live(p, item, all_live);
+    if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live); }
+    if (p.counter) {
+      if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
+      __syncthreads();
+      it = s_it;
+      __syncthreads();
+    } else {
+      it += gridDim.x;
     }
-    for (; k < ntask; k += blockDim.x >> 5) {
-      double* wsm = sm + (size_t)(threadIdx.x >> 5) * 2 * p.P * p.SS;
-      if (d == 0) flux_task<PHYS, NV, 0, MODE>(p, it, k, wsm);
-      if constexpr (maxd > 1) {
-        if (d == 1) flux_task<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, it, k, wsm);
-      }
-      if constexpr (maxd > 2) {
-        if (d == 2) flux_task<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, it, k, wsm);
-      }
-    }
-    k -= ntask;
   }
 }
 

@@ -47,9 +47,8 @@ struct FluxParams {
   const unsigned long long* araw0;  // speeds slot of U^n (GLM speed c_h)
   double gm1;
   int ndim;
-  int P;                        // lines of one warp's shared memory (at stride SS)
-  int SS;                       // longest line stride in shared memory (>= max segment + 6, odd)
-  int lines;                    // lines of an item at most
+  int P;                        // lines per tile (smem layout)
+  int SS;                       // smem stride of one line (>= max segment + 6, odd)
   int glm;
   unsigned short* tape;         // limiter pieces of every face (recording pass) or nullptr
   int limo3;                    // reconstruction: 0 MP5, 1 LIMO3
