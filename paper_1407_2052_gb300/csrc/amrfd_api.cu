@@ -275,28 +275,14 @@ int compact(amrfd_handle* h, cudaStream_t s) {
   return AMRFD_OK;
 }
 
-// Doubles of one line of the flux pass's shared memory, enough for every segment length
-// up to seg (within the largest domain extent): a segment of slen cells is held as its
-// sweep parts (the largest divisor np of slen up to slen/16, as the kernels count them),
-// each with its 6 halo cells, at an odd stride.
-int flux_line_stride(const amrfd_handle* h, int seg) {
+int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
   // segments run through blocks, never beyond the domain nor longer than seg
   int maxext = 1;
   for (auto& dm : h->hdom)
     for (int d = 0; d < h->cfg.ndim; d++) maxext = std::max(maxext, dm.n[d]);
   const int S = std::min(seg, maxext);
-  int ls = 1;
-  for (int slen = 1; slen <= S; slen++) {
-    int np = slen / 16;
-    while (np > 1 && slen % np) np--;
-    np = np > 1 ? np : 1;
-    ls = std::max(ls, np * ((slen / np + 2 * kGhost) | 1));
-  }
-  return ls;
-}
-
-int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
-  const int SS = flux_line_stride(h, seg);
+  int SS = S + 2 * kGhost;
+  if (SS % 2 == 0) SS++;  // odd stride in doubles: conflict-free 64-bit lines
   size_t smem = sizeof(double) * 2 * h->nv * lines * SS;
   if (smem > 227 * 1024) return AMRFD_ERR_INVALID_ARG;
   h->seg = seg;
@@ -360,7 +346,13 @@ FluxParams flux_params(amrfd_handle* h, const double* Uk, const double* Un, int 
   p.gm1 = h->cfg.gamma - 1.0;
   p.ndim = h->cfg.ndim;
   p.P = h->lines;
-  p.SS = flux_line_stride(h, h->seg);
+  int S = 1;
+  for (auto& dm : h->hdom)
+    for (int d = 0; d < h->cfg.ndim; d++) S = std::max(S, std::min(dm.n[d], h->seg));
+  // segments are balanced, never longer than seg
+  int SS = std::min(S, h->seg) + 2 * kGhost;
+  if (SS % 2 == 0) SS++;
+  p.SS = SS;
   p.glm = h->cfg.physics == AMRFD_MHD_GLM;
   p.W = h->d_W;
   p.err = h->d_err;

@@ -209,17 +209,6 @@ __device__ __forceinline__ double glm_speed(const unsigned long long* s0, int nd
   return ch;
 }
 
-// Shared-memory layout of a flux item's G^{+-}: [2][NV][P lines][line], a line holding
-// the np sweep parts of the segment one after another, part q the extended cells
-// q plen .. q plen + plen + 5 (its cells and its halo; neighbouring parts share six),
-// sp = plen + 6 rounded up to odd doubles apart. A warp's half (16 lanes: 16/np lines,
-// all parts) then reads 16 consecutive part slots in every step of the sweep: at an odd
-// stride they fall on 16 different bank pairs.
-struct PartLayout {
-  int np, plen, sp, ls;  // parts, cells per part, part stride, line stride (np sp)
-};
-__device__ __forceinline__ PartLayout part_layout(int slen);
-
 // Phase A of a flux item: the tile's G^{+-} (lines x segment + halo) into shared
 // memory, cells start, start + stride, ... of the tile.
 template <int PHYS, int NV, int D>
@@ -231,7 +220,6 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
   const int W = it.slen + 2 * kGhost;
   const int nl = it.nl;
   const int P = p.P, SS = p.SS;
-  const PartLayout pt = part_layout(it.slen);
   const double gm1 = p.gm1;
   for (int c = start; c < nl * W; c += stride) {
     int pl, j;
@@ -254,8 +242,8 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
       g = b == 0 ? g - dm.n[D] : (b == 1 ? dm.n[D] - 1 : 2 * dm.n[D] - 1 - g);
     }
     x[D] = g;
-    AMRFD_GUARD(p.err, g >= 0 && g < dm.n[D] && x[od1] < dm.n[od1] && x[od2] < dm.n[od2] && pl < P && j < W &&
-                pt.ls <= SS, continue)
+    AMRFD_GUARD(p.err, g >= 0 && g < dm.n[D] && x[od1] < dm.n[od1] && x[od2] < dm.n[od2] && pl < P && j < SS,
+                continue)
     const int nbk = dm.block0 + ((x[2] / dm.be[2]) * dm.nb[1] + x[1] / dm.be[1]) * dm.nb[0] + x[0] / dm.be[0];
     const bool act = p.active[nbk] != 0;
     const double* base = act ? p.Uk : p.Un;
@@ -280,22 +268,10 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
       prim_w<PHYS, NV>(u, gm1, w);
     }
     split_flux_w<PHYS, NV, D>(u, w, alpha, ch2, gp, gmn);
-    // the part slots holding extended cell j: part q1 and, within the six cells it
-    // shares with its left neighbour, part q1 - 1 as well
-    const int q1 = min(j / pt.plen, pt.np - 1);
-    const int o1 = q1 * pt.sp + j - q1 * pt.plen;
-    const bool two = q1 > 0 && j - (q1 - 1) * pt.plen < pt.plen + 2 * kGhost;
-    const int o0 = o1 - pt.sp + pt.plen;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-      double* lp = sm + ((0 * NV + v) * P + pl) * pt.ls;
-      double* lm = sm + ((1 * NV + v) * P + pl) * pt.ls;
-      lp[o1] = gp[v];
-      lm[o1] = gmn[v];
-      if (two) {
-        lp[o0] = gp[v];
-        lm[o0] = gmn[v];
-      }
+      sm[((0 * NV + v) * P + pl) * SS + j] = gp[v];
+      sm[((1 * NV + v) * P + pl) * SS + j] = gmn[v];
     }
   }
 }
@@ -523,15 +499,6 @@ __device__ __forceinline__ int sweep_parts(int slen) {
   return np > 1 ? np : 1;
 }
 
-__device__ __forceinline__ PartLayout part_layout(int slen) {
-  PartLayout pt;
-  pt.np = sweep_parts(slen);
-  pt.plen = slen / pt.np;
-  pt.sp = (pt.plen + 2 * kGhost) | 1;
-  pt.ls = pt.np * pt.sp;
-  return pt;
-}
-
 // Phase B of a flux item: one thread per (variable, part, line) sweeps the part's faces
 // and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
 // 2: LIMO3). The loop runs warp by warp: every lane of a warp takes the same number of
@@ -562,25 +529,24 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   }
   const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
   double* Ld = p.L[D] + dm.off;
-  const PartLayout pt = part_layout(slen);
   const int total = nl * NV * np;
   const int lane = threadIdx.x & 31;
   for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
     const int t = t0 + lane;
     const bool valid = t < total;
-    const int plen = pt.plen;
+    const int plen = slen / np;
     int pl = 0, v = 0, q = 0;
-    if (valid) {  // a warp holds consecutive lines and parts (parts fastest) of one variable
-      q = t % np;
-      const int r = t / np;
-      pl = r % nl;
-      v = r / nl;
+    if (valid) {  // a warp holds consecutive parts and lines of one variable
+      pl = t % nl;
+      const int r = t / nl;
+      q = r % np;
+      v = r / np;
     }
     const int p0 = q * plen;
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
     if (!valid) continue;
-    const double* g = sm + ((0 * NV + v) * p.P + pl) * pt.ls + q * pt.sp;
-    const double* h = sm + ((1 * NV + v) * p.P + pl) * pt.ls + q * pt.sp;
+    const double* g = sm + ((0 * NV + v) * p.P + pl) * p.SS + p0;
+    const double* h = sm + ((1 * NV + v) * p.P + pl) * p.SS + p0;
     const int line = it.l0 + pl;
     const int a1 = line % dm.be[od1], a2 = line / dm.be[od1];
     int x[3];

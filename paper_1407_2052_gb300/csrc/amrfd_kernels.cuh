@@ -48,7 +48,7 @@ struct FluxParams {
   double gm1;
   int ndim;
   int P;                        // lines per tile (smem layout)
-  int SS;                       // smem doubles of one line at most (sweep parts with halos)
+  int SS;                       // smem stride of one line (>= max segment + 6, odd)
   int glm;
   unsigned short* tape;         // limiter pieces of every face (recording pass) or nullptr
   int limo3;                    // reconstruction: 0 MP5, 1 LIMO3
