@@ -165,10 +165,13 @@ int amrfd_step_cfl(amrfd_handle *h, double *U, double *dt_dev, double t, double 
    gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
    Splitting speeds c_max, c_h and the psi damping factor are held fixed at
    the values the forward step used; MP5 limiter branches are replayed from
-   a forward recomputation. Returns AMRFD_ERR_UNSUPPORTED with LIMO3
-   reconstruction (the adjoint covers MP5), for a domain that
-   is partly active, a periodic dimension of fewer than 6 cells, or a mirror
-   dimension whose blocks hold fewer than 3 cells along it. */
+   a forward recomputation. Passive blocks (App. C) are the identity map, and
+   where an active block's fluxes read a passive neighbour's U^n as halo, that
+   dependence is transposed into gU_n too. Returns AMRFD_ERR_UNSUPPORTED with
+   LIMO3 reconstruction (the adjoint covers MP5), for a periodic dimension of
+   fewer than 6 cells, a mirror dimension whose blocks hold fewer than 3 cells
+   along it, or a partly active domain whose blocks hold fewer than 3 cells
+   along a dimension. */
 int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,
                   double *gU_n, void *stream);
 

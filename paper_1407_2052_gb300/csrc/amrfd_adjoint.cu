@@ -170,6 +170,26 @@ __device__ __forceinline__ void face_adj(double* gG, int q0, double gY, unsigned
   gG[q0 + 4] += gh4;
 }
 
+// Whether the block next to block `blk` along d (side -1 or +1) exists and is active
+// (wrapping across periodic faces).
+__device__ __forceinline__ bool nb_active(const DomDev& dm, const unsigned char* active, int blk, int d, int side) {
+  const int bi[3] = {blk % dm.nb[0], (blk / dm.nb[0]) % dm.nb[1], blk / (dm.nb[0] * dm.nb[1])};
+  int j = bi[d] + side;
+  if (j < 0 || j >= dm.nb[d]) {
+    if (dm.bc[d][0] != 0) return false;
+    j = j < 0 ? j + dm.nb[d] : j - dm.nb[d];
+  }
+  const int stride = d == 0 ? 1 : (d == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+  return active[dm.block0 + blk + (j - bi[d]) * stride] != 0;
+}
+
+// A passive block whose cells fed an active neighbour's fluxes along d: the active cells'
+// faces reach three cells into it (blocks hold at least three cells along d when their
+// domain is partly active), where the forward pass read U^n.
+__device__ __forceinline__ bool passive_fed(const DomDev& dm, const unsigned char* active, int blk, int d) {
+  return !active[dm.block0 + blk] && (nb_active(dm, active, blk, d, -1) || nb_active(dm, active, blk, d, 1));
+}
+
 template <int PHYS, int NV, int D>
 __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem& it, double* sm) {
   constexpr int od1 = D == 0 ? 1 : 0;
@@ -196,7 +216,12 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
   double* gGp = sm;                           // [NV][P][SA] gradient w.r.t. G+ at positions s0-5 ..
   double* gGm = gGp + NV * P * SA;
   double* gh = gGm + NV * P * SA;             // [NV][P][SG] scaled upstream gradient at s0-3 ..
-  // ---- phase A: upstream gradient at s0-3 .. s0+slen+2 (zero beyond an outflow face)
+  // passive block (fed an active neighbour): its cells entered the fluxes as U^n
+  const bool self_active = p.active[dm.block0 + it.blk] != 0;
+  const int bstride = D == 0 ? 1 : (D == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+  const int bo = it.blk - (o[D] / dm.be[D]) * bstride;  // block index with coordinate D = 0
+  // ---- phase A: upstream gradient at s0-3 .. s0+slen+2 (zero beyond an outflow face and
+  // at passive cells, whose residual the step does not use)
   for (int c = threadIdx.x; c < nl * WA; c += blockDim.x) {
     int pl, q;
     if (D == 0) { pl = c / WA; q = c - pl * WA; }
@@ -218,6 +243,7 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
     if (g < 0) { live = dm.bc[D][0] == 0; g = ((g % n) + n) % n; }
     else if (g >= n) { live = dm.bc[D][1] == 0; g = g % n; }
     x[D] = g;
+    live = live && p.active[dm.block0 + bo + (g / dm.be[D]) * bstride] != 0;
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
 #pragma unroll
     for (int v = 0; v < NV; v++) {
@@ -281,9 +307,10 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
     x[D] = s0 + j;
     const long long idx = ((long long)x[2] * dm.n[1] + x[1]) * dm.n[0] + x[0];
     double u[NV], gpv[NV], gmv[NV], gu[NV];
+    const double* Sv = self_active ? p.S : p.Un;
 #pragma unroll
     for (int v = 0; v < NV; v++) {
-      u[v] = p.S[dm.off + idx + (long long)v * dm.ncell];
+      u[v] = Sv[dm.off + idx + (long long)v * dm.ncell];
       gpv[v] = gGp[(v * P + pl) * SA + j + 5];
       gmv[v] = gGm[(v * P + pl) * SA + j + 5];
     }
@@ -321,7 +348,10 @@ __global__ void __launch_bounds__(256) adj_flux_kernel(AdjFluxParams p) {
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const FluxItem item = p.items[p.item0 + it];
     AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.P, p.SSg, item), continue)
-    if (!p.active[p.doms[item.dom].block0 + item.blk]) continue;
+    {
+      const DomDev& dm = p.doms[item.dom];
+      if (!p.active[dm.block0 + item.blk] && !passive_fed(dm, p.active, item.blk, item.d)) continue;
+    }
     if (item.d == 0) adj_item<PHYS, NV, 0>(p, item, sm);
     if constexpr (maxd > 1) { if (item.d == 1) adj_item<PHYS, NV, 1>(p, item, sm); }
     if constexpr (maxd > 2) { if (item.d == 2) adj_item<PHYS, NV, 2>(p, item, sm); }
@@ -335,11 +365,35 @@ __global__ void __launch_bounds__(256) adj_combine_kernel(AdjCombParams p) {
     const CellItem ci = p.items[p.item0 + it];
     AMRFD_GUARD(p.err, cell_item_ok(p.doms, p.ndom, ci), continue)
     const DomDev dm = p.doms[ci.dom];
-    if (!p.active[dm.block0 + ci.blk]) continue;
     int o[3];
     {
       const int bx = ci.blk % dm.nb[0], by = (ci.blk / dm.nb[0]) % dm.nb[1], bz = ci.blk / (dm.nb[0] * dm.nb[1]);
       o[0] = bx * dm.be[0]; o[1] = by * dm.be[1]; o[2] = bz * dm.be[2];
+    }
+    if (!p.active[dm.block0 + ci.blk]) {
+      // a passive block's cells entered the stage's fluxes as U^n where they fed an
+      // active neighbour: those directions' gradients belong to U^n
+      bool fed[3];
+      bool any = false;
+      for (int d = 0; d < 3; d++) {
+        fed[d] = d < p.ndim && passive_fed(dm, p.active, ci.blk, d);
+        any |= fed[d];
+      }
+      if (!any) continue;
+      for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+        const int l = ci.c0 + c;
+        const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+        const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+#pragma unroll
+        for (int v = 0; v < NV; v++) {
+          const long long e = idx + (long long)v * dm.ncell;
+          double s = 0.0;
+          for (int d = 0; d < 3; d++)
+            if (fed[d]) s += p.gL[d][e];
+          p.gbuf[0][e] += s;
+        }
+      }
+      continue;
     }
     const double pfac = p.psi_fac ? p.psi_fac[ci.dom] : 1.0;
     for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
@@ -361,7 +415,8 @@ __global__ void __launch_bounds__(256) adj_combine_kernel(AdjCombParams p) {
   }
 }
 
-// Passive blocks are the identity map of U^n: their gradient passes through.
+// Passive blocks are the identity map of U^n: their gradient passes through (added to what
+// the stages' fluxes gave U^n there, where the block fed an active neighbour).
 __global__ void __launch_bounds__(256) adj_passive_kernel(AdjCombParams p) {
   for (int it = blockIdx.x; it < p.nitems; it += gridDim.x) {
     const CellItem ci = p.items[p.item0 + it];
@@ -379,7 +434,7 @@ __global__ void __launch_bounds__(256) adj_passive_kernel(AdjCombParams p) {
       const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
       for (int v = 0; v < p.nv; v++) {
         const long long e = idx + (long long)v * dm.ncell;
-        p.gbuf[0][e] = p.gout[e];
+        p.gbuf[0][e] += p.gout[e];
       }
     }
   }

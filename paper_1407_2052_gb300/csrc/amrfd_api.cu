@@ -852,18 +852,20 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     int rc = refresh_active_host(h, s);
     if (rc) return rc;
   }
-  // supported: every domain entirely active or entirely passive; periodic lines >= 6
-  // cells; blocks >= 3 cells along a dimension with a mirror face
+  // supported: periodic lines >= 6 cells; blocks >= 3 cells along a dimension with a
+  // mirror face, and along every dimension of a partly active domain (the fluxes of an
+  // active block reach three cells into its neighbours, which must lie in the next block)
   for (int d = 0; d < h->ndom; d++) {
     const DomDev& dm = h->hdom[d];
     const int nbl = dm.nb[0] * dm.nb[1] * dm.nb[2];
     int na = 0;
     for (int b = 0; b < nbl; b++) na += h->active_h[dm.block0 + b] != 0;
-    if (na != 0 && na != nbl) return AMRFD_ERR_UNSUPPORTED;
+    const bool mixed = na != 0 && na != nbl;
     for (int k = 0; k < h->cfg.ndim; k++) {
       if (dm.bc[k][0] == AMRFD_BC_PERIODIC && dm.n[k] < 6) return AMRFD_ERR_UNSUPPORTED;
       if ((dm.bc[k][0] == AMRFD_BC_SYMMETRIC || dm.bc[k][1] == AMRFD_BC_SYMMETRIC) && dm.be[k] < 3)
         return AMRFD_ERR_UNSUPPORTED;
+      if (mixed && dm.be[k] < 3) return AMRFD_ERR_UNSUPPORTED;
     }
   }
   if (!h->d_adj_items) {

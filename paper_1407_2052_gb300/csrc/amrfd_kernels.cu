@@ -287,7 +287,8 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 template <bool REC>
 __device__ __forceinline__ void flux_sweep_carry(const double* g, const double* h, int slen, double eps16,
                                                  unsigned short* tp, unsigned short* tm, int f0, int fend,
-                                                 double* out, long long ostr, unsigned long long wmask) {
+                                                 double* out, long long ostr, unsigned long long wmask,
+                                                 int fmod = 0x7fffffff) {
   int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
   double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
@@ -311,8 +312,9 @@ __device__ __forceinline__ void flux_sweep_carry(const double* g, const double* 
       Ym = mp5_rel2_sel<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, ym);
       const int f = f0 + k - 3;
       if (f < fend) {
-        tp[f] = (unsigned short)(yp | (c2 << 3) | (c1 << 6));
-        tm[f] = (unsigned short)(ym | (c3 << 3) | (c4 << 6));
+        const int fi = f >= fmod ? f - fmod : f;  // face n of a periodic line is face 0
+        tp[fi] = (unsigned short)(yp | (c2 << 3) | (c1 << 6));
+        tm[fi] = (unsigned short)(ym | (c3 << 3) | (c4 << 6));
       }
     } else {
       Yp = mp5_rel2<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16);
@@ -516,14 +518,24 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
   const int f0 = o[D] + it.s0;
-  const int fend = f0 + slen + ((dm.bc[D][1] != 0 && f0 + slen == dm.n[D]) ? 1 : 0);
   const long long nlines = (long long)dm.n[od1] * dm.n[od2];
+  const int bstride = D == 0 ? 1 : (D == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
+  const int bo = it.blk - (o[D] / dm.be[D]) * bstride;  // block index with coordinate D = 0
+  // faces the segment's sweeps record (REC): those it owns, f0 .. f0 + slen - 1, and the
+  // face after it where no segment owning that face runs: at an outflow or mirror end of
+  // the line, or before a passive block (whose segments the forward pass skips; the
+  // adjoint reads the face there). On a periodic line face n is face 0.
+  int fend = f0 + slen;
+  {
+    const bool at_end = f0 + slen == dm.n[D];
+    if (at_end && dm.bc[D][1] != 0) fend++;
+    else if (REC && !p.active[dm.block0 + bo + ((at_end ? 0 : f0 + slen) / dm.be[D]) * bstride]) fend++;
+  }
+  const int fmod = dm.bc[D][1] == 0 ? dm.n[D] : dm.n[D] + 1;
   // cells of the segment inside active blocks (a segment through several blocks may
   // cross a passive one; every line of the item crosses the same blocks)
   unsigned long long wmask = slen >= 64 ? ~0ull : ((1ull << slen) - 1ull);
   if (!all_live) {
-    const int bstride = D == 0 ? 1 : (D == 1 ? dm.nb[0] : dm.nb[0] * dm.nb[1]);
-    const int bo = it.blk - (o[D] / dm.be[D]) * bstride;  // block index with coordinate D = 0
     for (int j = 0; j < slen; j++)
       if (!p.active[dm.block0 + bo + ((o[D] + it.s0 + j) / dm.be[D]) * bstride]) wmask &= ~(1ull << j);
   }
@@ -565,7 +577,7 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
       // a part records the faces it owns: its left face and interior faces; the
       // segment's last part also the faces the segment owns at its right end
       const int fe = q == np - 1 ? fend : f0 + p0 + plen;
-      flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask);
+      flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask, fmod);
     } else {
       flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
     }

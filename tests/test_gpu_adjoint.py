@@ -335,3 +335,125 @@ def test_rollout_200_steps_checkpoint_20_at_512():
         g, out = out, g
     assert s.error() == A.OK
     assert torch.equal(g, grad)
+
+
+# partly active domains (App. C): passive blocks keep U^n, and active blocks next to them
+# read that U^n as halo, so the gradient reaches U^n there through the fluxes as well as
+# through the identity (blocks of >= 3 cells along every dimension)
+MIXED = [
+    ("euler1d_periodic", (O.EULER, 1, (40, 1, 1), ((0, 0), (0, 0), (0, 0)), ((0, 0),) * 3, O.SSPRK3, (5, 1, 1),
+                          [1, 0, 1, 0, 0]), 2e-3),
+    ("mhd2d_periodic_4x4", (O.MHD_GLM, 2, (24, 20, 1), ((0, 0), (0, 0), (0, 0)), ((0, 0),) * 3, O.SSPRK54,
+                            (4, 4, 1), [1, 1, 0, 1, 0, 1, 1, 0, 1, 0, 0, 1, 1, 1, 0, 1]), 1e-3),
+    ("euler3d_outflow_mirror", (O.EULER, 3, (12, 12, 9), ((1, 1), (2, 2), (0, 0)), ((0, 0), (4, 4), (0, 0)),
+                                O.SSPRK3, (3, 2, 3), [1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 1, 1, 1, 1, 0, 0, 1, 0]), 2e-3),
+    ("mhd3d_last_block_passive", (O.MHD_GLM, 3, (12, 10, 8), ((0, 0), (1, 1), (0, 0)), ((0, 0),) * 3, O.SSPRK3,
+                                  (2, 2, 2), [1, 1, 1, 1, 1, 1, 1, 0]), 1e-3),
+]
+
+
+def _mixed_workload(spec):
+    physics, ndim, n, bc, asym, integ, nb, act = spec
+    w = _smooth(physics, ndim, n, bc, 50 + sum(n), integ, asym=asym, nb=nb)
+    w.active = np.array(act, np.uint8)
+    return w
+
+
+def _ref_grad_mixed(w, dt, g):
+    T = _torchref()
+    d = w.domains[0]
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    _, fl, al, ch = O.step(c, _odom(d), w.U, dt, active=w.active)
+    assert fl == 0
+    U = torch.from_numpy(w.U.copy()).requires_grad_(True)
+    out = T.step(U, dt, d.dx, d.bc, w.physics, w.ndim, w.gamma, w.integrator, al, ch, w.glm_cr, asym=d.asym,
+                 mask=T.block_mask(d.n, d.nb, w.active))
+    (out * torch.from_numpy(g)).sum().backward()
+    return U.grad.numpy()
+
+
+@pytest.mark.parametrize("name,spec,dt", MIXED, ids=[c[0] for c in MIXED])
+def test_adjoint_partly_active_domain_matches_autograd(name, spec, dt):
+    w = _mixed_workload(spec)
+    g = np.random.default_rng(11).standard_normal(w.U.shape)
+    got, _ = _gpu_adjoint(w, dt, g)
+    want = _ref_grad_mixed(w, dt, g)
+    err = np.abs(got - want).max() / np.abs(want).max()
+    assert err <= 1e-10, err
+    # the halo dependence is there: passive cells next to active ones get more than g
+    T = _torchref()
+    m = T.block_mask(w.domains[0].n, w.domains[0].nb, w.active).numpy()
+    assert np.abs(want[:, ~m] - g[:, ~m]).max() > 1e-3 * np.abs(g).max()
+
+
+def test_adjoint_partly_active_against_oracle_central_differences():
+    """Central differences (h = 1e-6) of the oracle's frozen-speed step with passive blocks,
+    along 8 seeded directions, against <v, adjoint(g)>."""
+    name, spec, dt = MIXED[1]
+    w = _mixed_workload(spec)
+    d = _odom(w.domains[0])
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    _, _, al, ch = O.step(c, d, w.U, dt, active=w.active)
+    rng = np.random.default_rng(23)
+    g = rng.standard_normal(w.U.shape)
+    got, _ = _gpu_adjoint(w, dt, g)
+    h = 1e-6
+    for _ in range(8):
+        v = rng.standard_normal(w.U.shape)
+        v /= np.linalg.norm(v)
+        up, _ = O.step_frozen(c, d, w.U + h * v, dt, al, ch, active=w.active)
+        um, _ = O.step_frozen(c, d, w.U - h * v, dt, al, ch, active=w.active)
+        fd = float(((up - um) / (2 * h) * g).sum())
+        ad = float((got * v).sum())
+        assert abs(fd - ad) <= 1e-6 * np.linalg.norm(got), (fd, ad)
+
+
+@pytest.mark.slow
+def test_rollout_gradient_at_512_against_oracle_central_differences():
+    """The adjoint workload at its stated size: 512^2 MHD+GLM, fixed dt 1e-3, a checkpointed
+    rollout of 20 steps (checkpoints every 10) of J = sum |B|^2/2 dx dy, against central
+    differences (h = 1e-6) of the oracle's frozen-speed trajectory along 20 seeded unit
+    directions, to 1e-6 of the gradient's norm. The differences run on the host cores in a
+    spawn process pool (the test process already holds a CUDA context)."""
+    import multiprocessing as mp
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(__file__))
+    import fd_oracle
+    from paper_1407_2052_gb300 import autodiff
+    A = _A()
+    w = W.adjoint2d(512)
+    dtv, nsteps, every = 1e-3, 20, 10
+    area = w.domains[0].dx[0] * w.domains[0].dx[1]
+    s = A.Solver.from_workload(w)
+    U0 = torch.from_numpy(w.U.ravel().copy()).cuda().requires_grad_(True)
+    dt = torch.full((1,), dtv, dtype=torch.float64, device="cuda")
+    Uf = autodiff.rollout(s, U0, dt, nsteps, every)
+    B = Uf.view(9, -1)[5:8]
+    (0.5 * (B * B).sum() * area).backward()
+    assert s.error() == A.OK
+    grad = U0.grad.cpu().numpy().reshape(w.U.shape)
+    c = O.cfg(w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    d0 = w.domains[0]
+    d = _odom(d0)
+    frozen, U = [], w.U.copy()
+    for _ in range(nsteps):
+        U, fl, al, ch = O.step(c, d, U, dtv)
+        assert fl == 0
+        frozen.append((al, ch))
+    rng = np.random.default_rng(31)
+    dirs = []
+    for _ in range(20):
+        v = rng.standard_normal(w.U.shape)
+        dirs.append(v / np.linalg.norm(v))
+    cfgt = (w.physics, w.ndim, w.integrator, w.gamma, w.glm_cr)
+    domt = (d0.n, d0.dx, [list(b) for b in d0.bc])
+    jobs = [(cfgt, domt, w.U, v, 1e-6, dtv, frozen, area) for v in dirs]
+    with mp.get_context("spawn").Pool(min(len(jobs), os.cpu_count() or 1)) as pool:
+        fds = pool.map(fd_oracle.fd_along, jobs)
+    gnorm = float(np.linalg.norm(grad))
+    worst = 0.0
+    for v, fd in zip(dirs, fds):
+        ad = float(np.sum(grad * v))
+        worst = max(worst, abs(fd - ad) / gnorm)
+    assert worst <= 1e-6, worst

@@ -51,3 +51,34 @@ def test_torchref_step_equals_oracle_frozen_step(case):
     got = T.step(torch.from_numpy(U.copy()), h, dom.dx, bc, physics, ndim, g, integ, al, ch, asym=asym)
     err = np.abs(got.numpy() - want).max() / np.abs(want).max()
     assert err <= 1e-13, err
+
+
+# partly active domains (App. C): blocks of >= 3 cells, passive ones keep U^n and feed
+# their active neighbours' halos with it
+MIXED = [
+    (O.EULER, 1, (40, 1, 1), ((0, 0), (0, 0), (0, 0)), ((0, 0),) * 3, O.SSPRK3, (5, 1, 1), [1, 0, 1, 0, 0]),
+    (O.MHD_GLM, 2, (24, 20, 1), ((0, 0), (0, 0), (0, 0)), ((0, 0),) * 3, O.SSPRK54, (4, 4, 1),
+     [1, 1, 0, 1, 0, 1, 1, 0, 1, 0, 0, 1, 1, 1, 0, 1]),
+    (O.EULER, 3, (12, 12, 9), ((1, 1), (2, 2), (0, 0)), ((0, 0), (4, 4), (0, 0)), O.SSPRK3, (3, 2, 3),
+     [1, 0, 1, 1, 1, 0, 0, 1, 1, 0, 1, 1, 1, 1, 0, 0, 1, 0]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(MIXED)))
+def test_torchref_step_with_passive_blocks_equals_oracle(case):
+    physics, ndim, n, bc, asym, integ, nb, act = MIXED[case]
+    dom, U, g = _smooth(physics, ndim, n, bc, asym, 40 + case, integ)
+    c = O.cfg(physics, ndim, integ, g)
+    d = O.dom(dom.n, dom.dx, bc=[list(b) for b in bc], nb=nb, asym=asym)
+    act = np.array(act, np.uint8)
+    h = 0.5 * O.dt(c, d, U, 0.4, active=act)[0]
+    want, fl, al, ch = O.step(c, d, U, h, active=act)
+    assert fl == 0
+    got = T.step(torch.from_numpy(U.copy()), h, dom.dx, bc, physics, ndim, g, integ, al, ch, asym=asym,
+                 mask=T.block_mask(n, nb, act))
+    err = np.abs(got.numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-13, err
+    # the passive blocks did not move, and some active cell next to one did
+    m = T.block_mask(n, nb, act).numpy()
+    assert np.array_equal(got.numpy()[:, ~m], U[:, ~m])
+    assert np.abs(got.numpy()[:, m] - U[:, m]).max() > 0

@@ -8,6 +8,7 @@ Selections use torch.where with the same tie rule as the CUDA path (a strict
 comparison picks the first argument only when strictly smaller), so that the
 limiter branch taken selects the same linear piece for the gradient.
 """
+import numpy as np
 import torch
 
 EULER, MHD_GLM = 0, 1
@@ -169,8 +170,10 @@ def ssprk_table(integrator):
     return a, b
 
 
-def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18, asym=None):
-    """One SSPRK step with frozen per-stage splitting speeds alpha_stage[s][3] and c_h."""
+def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18, asym=None, mask=None):
+    """One SSPRK step with frozen per-stage splitting speeds alpha_stage[s][3] and c_h.
+    mask (bool, shape of one variable): the cells of active blocks (App. C); the others
+    keep U^n in every stage, so that active cells next to them read U^n there."""
     a, b = ssprk_table(integrator)
     stages = [U]
     Ls = []
@@ -182,9 +185,20 @@ def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_c
                 acc = acc + a[i][k] * stages[k]
             if b[i][k] != 0.0:
                 acc = acc + dt * b[i][k] * Ls[k]
+        if mask is not None:
+            acc = torch.where(mask, acc, U)
         stages.append(acc)
     out = stages[-1]
     if physics == MHD_GLM and glm_cr > 0.0:
         fac = torch.exp(torch.tensor(-dt * ch / glm_cr, dtype=U.dtype))
-        out = torch.cat([out[:8], out[8:] * fac])
+        psi = out[8:] * fac if mask is None else torch.where(mask, out[8:] * fac, out[8:])
+        out = torch.cat([out[:8], psi])
     return out
+
+
+def block_mask(n, nb, active):
+    """Cell mask (nz, ny, nx) of the active blocks; blocks numbered x fastest."""
+    be = [n[k] // nb[k] for k in range(3)]
+    act = np.asarray(active, dtype=bool).reshape(nb[2], nb[1], nb[0])
+    m = np.repeat(np.repeat(np.repeat(act, be[2], axis=0), be[1], axis=1), be[0], axis=2)
+    return torch.from_numpy(m)
