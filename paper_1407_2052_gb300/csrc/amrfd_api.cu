@@ -382,6 +382,10 @@ CombParams comb_params(amrfd_handle* h, double* U, const double* dt, int i) {
   p.W = (i < h->ns) ? h->d_W : nullptr;  // the next flux pass reads them
   p.gm1 = h->cfg.gamma - 1.0;
   p.ndom = h->ndom;
+  auto a16 = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+  p.pairs = a16(p.out) && a16(p.W);
+  for (int k = 0; k < kMaxStages; k++) p.pairs = p.pairs && a16(p.buf[k]);
+  for (int d = 0; d < 3; d++) p.pairs = p.pairs && a16(p.L[d]);
   return p;
 }
 

@@ -15,6 +15,8 @@
 //  compact kernels device-side work list of the active blocks (App. C).
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "amrfd_device.cuh"
 #include "amrfd_kernels.cuh"
 
@@ -634,73 +636,101 @@ __global__ void __launch_bounds__(kFluxMaxThreads, 2) flux_kernel(FluxParams p) 
 }
 
 // ----------------------------------------------------------------- combine
+// The derived quantities and FP32 speed bounds of one new state u (cell at idx).
+template <int PHYS, int NV>
+__device__ __forceinline__ void combine_tail(const CombParams& p, const DomDev& dm, long long idx, const double* u,
+                                             float gam, float lom[4], float upm[4]) {
+  const float rdx[3] = {0.f, 0.f, 0.f};
+  if (p.W) {
+    constexpr int NW = NumW<PHYS, NV>::value;
+    double w[NW];
+    prim_w<PHYS, NV>(u, p.gm1, w);
+    const long long wi = dm.woff + (idx - dm.off);
+#pragma unroll
+    for (int q = 0; q < NW; q++) p.W[wi + (long long)q * dm.ncell] = w[q];
+  }
+  if (p.tlow_out) {
+    float up[4], lo[4];
+    bool force;
+    speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
+    if (!force) {
+#pragma unroll
+      for (int q = 0; q < 3; q++) {
+        lom[q] = fmaxf(lom[q], lo[q]);
+        upm[q] = fmaxf(upm[q], up[q]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 3; q++) upm[q] = __int_as_float(0x7f800000);  // +inf
+    }
+  }
+}
+
 // The cells of one item. Every load of a cell is issued before its stores (the output
 // may be the U^n buffer, so loads cannot move past a store); A0ONE skips the product
 // with a first coefficient of 1. Per variable the operations and their order are
-// a_0 U^(k_0), then a_t U^(k_t) and w_d L_d by FMA, then the psi damping.
-template <int PHYS, int NV, bool A0ONE>
+// a_0 U^(k_0), then a_t U^(k_t) and w_d L_d by FMA, then the psi damping. PAIR: two
+// neighbouring cells along x per thread with 16-byte (double2) loads and stores, the
+// same operations on each; the caller checks that every pair starts 16-byte aligned.
+template <int PHYS, int NV, bool A0ONE, bool PAIR>
 __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev& dm, const CellItem& ci,
                                               const int o[3], double w0, double w1, double w2, double fac,
                                               float gam, float lom[4], float upm[4]) {
-  const float rdx[3] = {0.f, 0.f, 0.f};
+  constexpr int K = PAIR ? 2 : 1;
+  using VT = typename std::conditional<PAIR, double2, double>::type;
   const long long nc = dm.ncell;
-  for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
-    const int l = ci.c0 + c;
+  for (int c = threadIdx.x; c < ci.cnt / K; c += blockDim.x) {
+    const int l = ci.c0 + K * c;
     const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
     const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-    double u[NV];
+    double u[K][NV];
+    auto load = [&](const double* b, int v, double (&x)[K]) {
+      const VT y = *reinterpret_cast<const VT*>(b + v * nc);
+      if constexpr (PAIR) { x[0] = y.x; x[1] = y.y; } else { x[0] = y; }
+    };
     {
       const double* b0 = p.buf[p.co.k[0]] + idx;
 #pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = A0ONE ? b0[v * nc] : p.co.a[0] * b0[v * nc];
+      for (int v = 0; v < NV; v++) {
+        double x[K];
+        load(b0, v, x);
+#pragma unroll
+        for (int e = 0; e < K; e++) u[e][v] = A0ONE ? x[e] : p.co.a[0] * x[e];
+      }
     }
     for (int t = 1; t < p.co.nterm; t++) {
       const double* bt = p.buf[p.co.k[t]] + idx;
       const double at = p.co.a[t];
 #pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = fma(at, bt[v * nc], u[v]);
-    }
-    {
-      const double* L0 = p.L[0] + idx;
+      for (int v = 0; v < NV; v++) {
+        double x[K];
+        load(bt, v, x);
 #pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = fma(w0, L0[v * nc], u[v]);
-    }
-    if (p.ndim > 1) {
-      const double* L1 = p.L[1] + idx;
-#pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = fma(w1, L1[v * nc], u[v]);
-    }
-    if (p.ndim > 2) {
-      const double* L2 = p.L[2] + idx;
-#pragma unroll
-      for (int v = 0; v < NV; v++) u[v] = fma(w2, L2[v * nc], u[v]);
-    }
-    if constexpr (PHYS == PH_MHD) u[NV - 1] *= fac;  // psi
-#pragma unroll
-    for (int v = 0; v < NV; v++) p.out[idx + v * nc] = u[v];
-    if (p.W) {
-      constexpr int NW = NumW<PHYS, NV>::value;
-      double w[NW];
-      prim_w<PHYS, NV>(u, p.gm1, w);
-      const long long wi = dm.woff + (idx - dm.off);
-#pragma unroll
-      for (int q = 0; q < NW; q++) p.W[wi + (long long)q * nc] = w[q];
-    }
-    if (p.tlow_out) {
-      float up[4], lo[4];
-      bool force;
-      speed_bounds<PHYS, NV>(u, gam, p.ndim, rdx, false, up, lo, force);
-      if (!force) {
-#pragma unroll
-        for (int q = 0; q < 3; q++) {
-          lom[q] = fmaxf(lom[q], lo[q]);
-          upm[q] = fmaxf(upm[q], up[q]);
-        }
-      } else {
-#pragma unroll
-        for (int q = 0; q < 3; q++) upm[q] = __int_as_float(0x7f800000);  // +inf
+        for (int e = 0; e < K; e++) u[e][v] = fma(at, x[e], u[e][v]);
       }
     }
+    for (int d = 0; d < p.ndim; d++) {
+      const double* Ld = p.L[d] + idx;
+      const double wd = d == 0 ? w0 : (d == 1 ? w1 : w2);
+#pragma unroll
+      for (int v = 0; v < NV; v++) {
+        double x[K];
+        load(Ld, v, x);
+#pragma unroll
+        for (int e = 0; e < K; e++) u[e][v] = fma(wd, x[e], u[e][v]);
+      }
+    }
+    if constexpr (PHYS == PH_MHD) {
+#pragma unroll
+      for (int e = 0; e < K; e++) u[e][NV - 1] *= fac;  // psi
+    }
+#pragma unroll
+    for (int v = 0; v < NV; v++) {
+      if constexpr (PAIR) *reinterpret_cast<double2*>(p.out + idx + v * nc) = make_double2(u[0][v], u[1][v]);
+      else p.out[idx + v * nc] = u[0][v];
+    }
+#pragma unroll
+    for (int e = 0; e < K; e++) combine_tail<PHYS, NV>(p, dm, idx + e, u[e], gam, lom, upm);
   }
 }
 
@@ -736,8 +766,16 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
     const double fac = damp ? s_fac : 1.0;
     float lom[4] = {0.f, 0.f, 0.f, 0.f};
     float upm[4] = {0.f, 0.f, 0.f, 0.f};
-    if (a0_one) combine_cells<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
-    else combine_cells<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+    // pairs along x when every pair starts 16-byte aligned: buffers aligned (host), an even
+    // x extent and block edge, an even domain offset and item start and count
+    const bool pair = p.pairs && !((dm.n[0] | dm.be[0] | ci.c0 | ci.cnt) & 1) && !(dm.off & 1);
+    if (pair) {
+      if (a0_one) combine_cells<PHYS, NV, true, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      else combine_cells<PHYS, NV, false, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+    } else {
+      if (a0_one) combine_cells<PHYS, NV, true, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      else combine_cells<PHYS, NV, false, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+    }
     if (p.tlow_out) {
       block_max4f_bcast(lom, redf, thr);
       if (threadIdx.x == 0)

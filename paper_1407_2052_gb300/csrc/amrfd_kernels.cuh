@@ -83,6 +83,7 @@ struct CombParams {
   double gm1;
   int ndom;
   float* item_up;               // with tlow_out: per item upper bounds, as SpeedParams::item_up
+  int pairs;                    // every buffer above 16-byte aligned: double2 access allowed
 };
 
 struct DtParams {
