@@ -15,8 +15,6 @@
 //  compact kernels device-side work list of the active blocks (App. C).
 #include <cuda_runtime.h>
 
-#include <type_traits>
-
 #include "amrfd_device.cuh"
 #include "amrfd_kernels.cuh"
 
@@ -669,33 +667,70 @@ __device__ __forceinline__ void combine_tail(const CombParams& p, const DomDev& 
 // The cells of one item. Every load of a cell is issued before its stores (the output
 // may be the U^n buffer, so loads cannot move past a store); A0ONE skips the product
 // with a first coefficient of 1. Per variable the operations and their order are
-// a_0 U^(k_0), then a_t U^(k_t) and w_d L_d by FMA, then the psi damping. PAIR: two
-// neighbouring cells along x per thread with 16-byte (double2) loads and stores, the
-// same operations on each; the caller checks that every pair starts 16-byte aligned.
-template <int PHYS, int NV, bool A0ONE, bool PAIR>
+// a_0 U^(k_0), then a_t U^(k_t) and w_d L_d by FMA, then the psi damping.
+template <int PHYS, int NV, bool A0ONE>
 __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev& dm, const CellItem& ci,
                                               const int o[3], double w0, double w1, double w2, double fac,
                                               float gam, float lom[4], float upm[4]) {
-  constexpr int K = PAIR ? 2 : 1;
-  using VT = typename std::conditional<PAIR, double2, double>::type;
   const long long nc = dm.ncell;
-  for (int c = threadIdx.x; c < ci.cnt / K; c += blockDim.x) {
-    const int l = ci.c0 + K * c;
+  for (int c = threadIdx.x; c < ci.cnt; c += blockDim.x) {
+    const int l = ci.c0 + c;
     const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
     const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
-    double u[K][NV];
-    auto load = [&](const double* b, int v, double (&x)[K]) {
-      const VT y = *reinterpret_cast<const VT*>(b + v * nc);
-      if constexpr (PAIR) { x[0] = y.x; x[1] = y.y; } else { x[0] = y; }
-    };
+    double u[NV];
+    {
+      const double* b0 = p.buf[p.co.k[0]] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = A0ONE ? b0[v * nc] : p.co.a[0] * b0[v * nc];
+    }
+    for (int t = 1; t < p.co.nterm; t++) {
+      const double* bt = p.buf[p.co.k[t]] + idx;
+      const double at = p.co.a[t];
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(at, bt[v * nc], u[v]);
+    }
+    {
+      const double* L0 = p.L[0] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w0, L0[v * nc], u[v]);
+    }
+    if (p.ndim > 1) {
+      const double* L1 = p.L[1] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w1, L1[v * nc], u[v]);
+    }
+    if (p.ndim > 2) {
+      const double* L2 = p.L[2] + idx;
+#pragma unroll
+      for (int v = 0; v < NV; v++) u[v] = fma(w2, L2[v * nc], u[v]);
+    }
+    if constexpr (PHYS == PH_MHD) u[NV - 1] *= fac;  // psi
+#pragma unroll
+    for (int v = 0; v < NV; v++) p.out[idx + v * nc] = u[v];
+    combine_tail<PHYS, NV>(p, dm, idx, u, gam, lom, upm);
+  }
+}
+
+// combine_cells for two neighbouring cells along x per thread, read and written with
+// 16-byte (double2) accesses; the same operations in the same order on each cell. The
+// caller checks that every pair starts 16-byte aligned.
+template <int PHYS, int NV, bool A0ONE>
+__device__ __forceinline__ void combine_pairs(const CombParams& p, const DomDev& dm, const CellItem& ci,
+                                              const int o[3], double w0, double w1, double w2, double fac,
+                                              float gam, float lom[4], float upm[4]) {
+  const long long nc = dm.ncell;
+  for (int c = threadIdx.x; c < ci.cnt / 2; c += blockDim.x) {
+    const int l = ci.c0 + 2 * c;
+    const int lx = l % dm.be[0], ly = (l / dm.be[0]) % dm.be[1], lz = l / (dm.be[0] * dm.be[1]);
+    const long long idx = dm.off + ((long long)(o[2] + lz) * dm.n[1] + (o[1] + ly)) * dm.n[0] + (o[0] + lx);
+    double ua[NV], ub[NV];
     {
       const double* b0 = p.buf[p.co.k[0]] + idx;
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        double x[K];
-        load(b0, v, x);
-#pragma unroll
-        for (int e = 0; e < K; e++) u[e][v] = A0ONE ? x[e] : p.co.a[0] * x[e];
+        const double2 x = *reinterpret_cast<const double2*>(b0 + v * nc);
+        ua[v] = A0ONE ? x.x : p.co.a[0] * x.x;
+        ub[v] = A0ONE ? x.y : p.co.a[0] * x.y;
       }
     }
     for (int t = 1; t < p.co.nterm; t++) {
@@ -703,10 +738,9 @@ __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev&
       const double at = p.co.a[t];
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        double x[K];
-        load(bt, v, x);
-#pragma unroll
-        for (int e = 0; e < K; e++) u[e][v] = fma(at, x[e], u[e][v]);
+        const double2 x = *reinterpret_cast<const double2*>(bt + v * nc);
+        ua[v] = fma(at, x.x, ua[v]);
+        ub[v] = fma(at, x.y, ub[v]);
       }
     }
     for (int d = 0; d < p.ndim; d++) {
@@ -714,23 +748,18 @@ __device__ __forceinline__ void combine_cells(const CombParams& p, const DomDev&
       const double wd = d == 0 ? w0 : (d == 1 ? w1 : w2);
 #pragma unroll
       for (int v = 0; v < NV; v++) {
-        double x[K];
-        load(Ld, v, x);
-#pragma unroll
-        for (int e = 0; e < K; e++) u[e][v] = fma(wd, x[e], u[e][v]);
+        const double2 x = *reinterpret_cast<const double2*>(Ld + v * nc);
+        ua[v] = fma(wd, x.x, ua[v]);
+        ub[v] = fma(wd, x.y, ub[v]);
       }
     }
     if constexpr (PHYS == PH_MHD) {
-#pragma unroll
-      for (int e = 0; e < K; e++) u[e][NV - 1] *= fac;  // psi
+      ua[NV - 1] *= fac;  // psi
+      ub[NV - 1] *= fac;
     }
 #pragma unroll
-    for (int v = 0; v < NV; v++) {
-      if constexpr (PAIR) *reinterpret_cast<double2*>(p.out + idx + v * nc) = make_double2(u[0][v], u[1][v]);
-      else p.out[idx + v * nc] = u[0][v];
-    }
-#pragma unroll
-    for (int e = 0; e < K; e++) combine_tail<PHYS, NV>(p, dm, idx + e, u[e], gam, lom, upm);
+    for (int v = 0; v < NV; v++) *reinterpret_cast<double2*>(p.out + idx + v * nc) = make_double2(ua[v], ub[v]);
+    for (int half = 0; half < 2; half++) combine_tail<PHYS, NV>(p, dm, idx + half, half ? ub : ua, gam, lom, upm);
   }
 }
 
@@ -770,11 +799,11 @@ __global__ void __launch_bounds__(256) combine_kernel(CombParams p) {
     // x extent and block edge, an even domain offset and item start and count
     const bool pair = p.pairs && !((dm.n[0] | dm.be[0] | ci.c0 | ci.cnt) & 1) && !(dm.off & 1);
     if (pair) {
-      if (a0_one) combine_cells<PHYS, NV, true, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
-      else combine_cells<PHYS, NV, false, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      if (a0_one) combine_pairs<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      else combine_pairs<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
     } else {
-      if (a0_one) combine_cells<PHYS, NV, true, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
-      else combine_cells<PHYS, NV, false, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      if (a0_one) combine_cells<PHYS, NV, true>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
+      else combine_cells<PHYS, NV, false>(p, dm, ci, o, w0, w1, w2, fac, gam, lom, upm);
     }
     if (p.tlow_out) {
       block_max4f_bcast(lom, redf, thr);
