@@ -54,9 +54,10 @@ def flux_flop_executed(seg, part):
 
 
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64, nominal (context only)
-# DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write, 128^3 capture,
-# scaled by cells): traffic grows with the cells processed
-FLUX_TRAFFIC_BYTES_PER_CELL = (313.990144 + 410.184704) * 1e6 / 128 ** 3
+# DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write of the 128^3 blast's
+# first flux pass, tile 64 x 8 lines x 288 threads, scaled by cells): traffic grows with
+# the cells processed
+FLUX_TRAFFIC_BYTES_PER_CELL = (440.548864 + 411.594496) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):
