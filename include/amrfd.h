@@ -164,14 +164,15 @@ int amrfd_step_cfl(amrfd_handle *h, double *U, double *dt_dev, double t, double 
 /* Discrete adjoint of one amrfd_step with the same U^n and dt: given
    gU_np1 = dJ/dU^{n+1}, writes gU_n = dJ/dU^n (both device, state layout).
    Splitting speeds c_max, c_h and the psi damping factor are held fixed at
-   the values the forward step used; MP5 limiter branches are replayed from
-   a forward recomputation. Passive blocks (App. C) are the identity map, and
-   where an active block's fluxes read a passive neighbour's U^n as halo, that
-   dependence is transposed into gU_n too. Returns AMRFD_ERR_UNSUPPORTED with
-   LIMO3 reconstruction (the adjoint covers MP5), for a periodic dimension of
-   fewer than 6 cells, a mirror dimension whose blocks hold fewer than 3 cells
-   along it, or a partly active domain whose blocks hold fewer than 3 cells
-   along a dimension. */
+   the values the forward step used; the pieces the MP5 or LIMO3 limiter took
+   at every face are replayed from a forward recomputation (inside LIMO3's
+   2e-12-wide blend band, the piece of the nearer half). Passive blocks
+   (App. C) are the identity map, and where an active block's fluxes read a
+   passive neighbour's U^n as halo, that dependence is transposed into gU_n
+   too. Returns AMRFD_ERR_UNSUPPORTED for a periodic dimension of fewer than
+   6 cells, a mirror dimension whose blocks hold fewer than 3 cells along it,
+   or a partly active domain whose blocks hold fewer than 3 cells along a
+   dimension. */
 int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,
                   double *gU_n, void *stream);
 

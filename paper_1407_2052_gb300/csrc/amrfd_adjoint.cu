@@ -190,6 +190,22 @@ __device__ __forceinline__ bool passive_fed(const DomDev& dm, const unsigned cha
   return !active[dm.block0 + blk] && (nb_active(dm, active, blk, d, -1) || nb_active(dm, active, blk, d, 1));
 }
 
+// Backward of one LIMO3 value Y(a, b) at a face from its recorded piece (limo3_y_sel):
+// dY/da, dY/db of the piece. Inside the 2e-12-wide blend band of the switch the exact
+// derivative carries a factor 1e12 through the blend weight; there the piece of the
+// nearer half (unlimited or limited) is taken.
+__device__ __forceinline__ void limo3_piece_grad(unsigned rec, double& ca, double& cb) {
+  const unsigned mode = (rec >> 3) & 3u;
+  if (mode == 0u || mode == 2u) { ca = 1.0 / 3.0; cb = 2.0 / 3.0; return; }
+  switch (rec & 7u) {
+    case 1: ca = 1.0 / 3.0; cb = 2.0 / 3.0; break;  // y3
+    case 2: ca = -0.5; cb = 0.0; break;               // -a/2
+    case 3: ca = 2.0; cb = 0.0; break;                // 2a
+    case 4: ca = 0.0; cb = 1.6; break;                // 1.6 b
+    default: ca = 0.0; cb = 0.0; break;               // zero
+  }
+}
+
 template <int PHYS, int NV, int D>
 __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem& it, double* sm) {
   constexpr int od1 = D == 0 ? 1 : 0;
@@ -280,8 +296,22 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
       ggp[qk - 1] += gF;
       ggm[qk] += gF;
       const double gY = 0.5 * gF;
-      face_adj<false>(ggp, qk - 3, gY, tp[f]);  // + stencil: cells k-3 .. k+1, centre k-1
-      face_adj<true>(ggm, qk - 2, gY, tm[f]);   // - stencil: cells k-2 .. k+2, centre k
+      if (p.limo3) {
+        // F = G+_{k-1} + G-_k + (Y+ - Y-)/2: Y+ of a = G+_{k-1} - G+_{k-2}, b = G+_k - G+_{k-1};
+        // Y- of a = G-_{k+1} - G-_k, b = G-_k - G-_{k-1}
+        double ca, cb;
+        limo3_piece_grad(tp[f], ca, cb);
+        ggp[qk - 2] -= ca * gY;
+        ggp[qk - 1] += (ca - cb) * gY;
+        ggp[qk] += cb * gY;
+        limo3_piece_grad(tm[f], ca, cb);
+        ggm[qk + 1] -= ca * gY;
+        ggm[qk] += (ca - cb) * gY;
+        ggm[qk - 1] += cb * gY;
+      } else {
+        face_adj<false>(ggp, qk - 3, gY, tp[f]);  // + stencil: cells k-3 .. k+1, centre k-1
+        face_adj<true>(ggm, qk - 2, gY, tm[f]);   // - stencil: cells k-2 .. k+2, centre k
+      }
     }
     // outflow: ghost copies of an edge cell fold back into it
     if (dm.bc[D][0] == 1 && s0 == 0) {

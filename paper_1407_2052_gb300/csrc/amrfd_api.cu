@@ -849,7 +849,6 @@ int build_adjoint_items(amrfd_handle* h) {
 int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
                   void* stream) {
   if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
-  if (h->cfg.recon != AMRFD_MP5) return AMRFD_ERR_UNSUPPORTED;
   Range rg("amrfd adjoint");
   cudaStream_t s = (cudaStream_t)stream;
   {
@@ -938,6 +937,7 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     ap.SSg = h->adj_SSg;
     ap.glm = h->cfg.physics == AMRFD_MHD_GLM;
     ap.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
+    ap.limo3 = h->cfg.recon == AMRFD_LIMO3;
     ap.err = h->d_err;
     ap.ndom = h->ndom;
     {

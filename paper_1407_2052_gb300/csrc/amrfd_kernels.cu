@@ -434,6 +434,33 @@ __device__ __forceinline__ double limo3_y(double a, double b, double s2, long lo
   return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
 }
 
+// limo3_y (bit-identical value) that also reports the piece it took, for the discrete
+// adjoint: bits 0-2 the limited piece (0 zero, 1 y3, 2 -a/2, 3 2a, 4 1.6 b, each as a
+// function of the unsigned a, b), bits 3-4 the mode (0 unlimited, 1 limited, 2 / 3 inside
+// the blend band on its unlimited / limited half).
+__device__ __forceinline__ double limo3_y_sel(double a, double b, double s2, long long tlo, long long thi,
+                                              double esc, int& code) {
+  const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
+  const long long bs = abits(s2);
+  if (bs <= tlo) { code = 0; return y3; }
+  const bool neg = sbit(b) != 0;
+  const double ap = neg ? dneg(a) : a;
+  const double y3p = neg ? dneg(y3) : y3;
+  const double bp = neg ? dneg(b) : b;
+  double t;
+  int c;
+  imin_sel(dscale<1>(ap), 3, y3p, 1, t, c);
+  imin_sel(t, c, 1.6 * bp, 4, t, c);
+  imax_sel(dscale<-1>(dneg(ap)), 2, t, c, t, c);
+  imin_sel(y3p, 1, t, c, t, c);
+  imax_sel(0.0, 0, t, c, t, c);
+  const double yl = neg ? dneg(t) : t;
+  if (bs >= thi) { code = c | (1 << 3); return yl; }
+  const double z = fma(s2, esc, -1.0) * 1e12;
+  code = c | ((z < 0.0 ? 2 : 3) << 3);
+  return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
+}
+
 // LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep_carry; G^+ from
 // cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k). The squares of
 // the differences are carried along the line (each enters two faces' switch), and the
@@ -449,6 +476,37 @@ __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, in
   for (int k = 3; k <= kend; ++k) {
     const double Yp = limo3_y(Pa, Pb, Pa2 + Pb2, tlo, thi, esc);
     const double Ym = limo3_y(Ma, Mb, Ma2 + Mb2, tlo, thi, esc);
+    const double F = fma(0.5, Yp - Ym, g[k - 1] + h[k]);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    Fprev = F;
+    if (k < kend) {
+      Pa = Pb; Pa2 = Pb2; Pb = g[k + 1] - g[k]; Pb2 = Pb * Pb;
+      Mb = Ma; Mb2 = Ma2; Ma = h[k + 2] - h[k + 1]; Ma2 = Ma * Ma;
+    }
+  }
+}
+
+// limo3_sweep that also records, per face and bias, the piece LIMO3 took (limo3_y_sel),
+// faces f0 + k - 3 below fend as flux_sweep_carry<true> records them.
+__device__ __forceinline__ void limo3_sweep_rec(const double* g, const double* h, int slen, double esc,
+                                                unsigned short* tp, unsigned short* tm, int f0, int fend, int fmod,
+                                                double* out, long long ostr, unsigned long long wmask) {
+  const long long tlo = __double_as_longlong((1.0 - 1e-12) / esc), thi = __double_as_longlong((1.0 + 1e-12) / esc);
+  double Pa = g[2] - g[1], Pb = g[3] - g[2];
+  double Mb = h[3] - h[2], Ma = h[4] - h[3];
+  double Pa2 = Pa * Pa, Pb2 = Pb * Pb, Ma2 = Ma * Ma, Mb2 = Mb * Mb;
+  double Fprev = 0.0;
+  const int kend = slen + 3;
+  for (int k = 3; k <= kend; ++k) {
+    int cp, cm;
+    const double Yp = limo3_y_sel(Pa, Pb, Pa2 + Pb2, tlo, thi, esc, cp);
+    const double Ym = limo3_y_sel(Ma, Mb, Ma2 + Mb2, tlo, thi, esc, cm);
+    const int f = f0 + k - 3;
+    if (f < fend) {
+      const int fi = f >= fmod ? f - fmod : f;  // face n of a periodic line is face 0
+      tp[fi] = (unsigned short)cp;
+      tm[fi] = (unsigned short)cm;
+    }
     const double F = fma(0.5, Yp - Ym, g[k - 1] + h[k]);
     if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
     Fprev = F;
@@ -503,13 +561,13 @@ __device__ __forceinline__ int sweep_parts(int slen) {
 
 // Phase B of a flux item: one thread per (variable, part, line) sweeps the part's faces
 // and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
-// 2: LIMO3). The loop runs warp by warp: every lane of a warp takes the same number of
+// 2: LIMO3; 3: LIMO3 recording its pieces). The loop runs warp by warp: every lane of a warp takes the same number of
 // trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work,
 // all of them sweeping parts of the same length.
 template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
                                              const int o[3], bool all_live, const double* sm) {
-  constexpr bool REC = MODE == 1;
+  constexpr bool REC = MODE == 1 || MODE == 3;
   const int nl = it.nl, slen = it.slen;
   const int np = sweep_parts(slen);
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
@@ -577,7 +635,12 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
       // a part records the faces it owns: its left face and interior faces; the
       // segment's last part also the faces the segment owns at its right end
       const int fe = q == np - 1 ? fend : f0 + p0 + plen;
-      flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask, fmod);
+      if constexpr (MODE == 3) {
+        const double rdx = p.limo3_r * dm.dx[D];
+        limo3_sweep_rec(g, h, plen, 0.25 / (rdx * rdx), tp, tm, f0 + p0, fe, fmod, out, ostr, pmask);
+      } else {
+        flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask, fmod);
+      }
     } else {
       flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
     }
@@ -940,9 +1003,10 @@ cudaError_t launch_speeds(int physics, int nv, const SpeedParams& p, int grid, i
 }
 
 cudaError_t launch_flux(int physics, int nv, const FluxParams& p, int grid, int block, size_t smem, cudaStream_t s) {
-#define CALL(PH, NVV)                                                     \
-  if (p.tape) flux_kernel<PH, NVV, 1><<<grid, block, smem, s>>>(p);      \
-  else if (p.limo3) flux_kernel<PH, NVV, 2><<<grid, block, smem, s>>>(p); \
+#define CALL(PH, NVV)                                                                \
+  if (p.tape && p.limo3) flux_kernel<PH, NVV, 3><<<grid, block, smem, s>>>(p);      \
+  else if (p.tape) flux_kernel<PH, NVV, 1><<<grid, block, smem, s>>>(p);            \
+  else if (p.limo3) flux_kernel<PH, NVV, 2><<<grid, block, smem, s>>>(p);           \
   else flux_kernel<PH, NVV, 0><<<grid, block, smem, s>>>(p)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
@@ -963,7 +1027,13 @@ cudaError_t flux_set_smem(int physics, int nv, size_t smem) {
 }
 
 cudaError_t flux_rec_set_smem(int physics, int nv, size_t smem) {
-#define CALL(PH, NVV) return cudaFuncSetAttribute(flux_kernel<PH, NVV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+#define CALL(PH, NVV)                                                                                     \
+  do {                                                                                                     \
+    cudaError_t e = cudaFuncSetAttribute(flux_kernel<PH, NVV, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                         (int)smem);                                                       \
+    if (e != cudaSuccess) return e;                                                                        \
+    return cudaFuncSetAttribute(flux_kernel<PH, NVV, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+  } while (0)
   AMRFD_DISPATCH(physics, nv, CALL);
 #undef CALL
   return cudaSuccess;

@@ -135,6 +135,7 @@ struct AdjFluxParams {
   int P, SSa, SSg;
   int glm;
   const unsigned short* tape;   // limiter pieces recorded by the forward pass of this stage
+  int limo3;                    // reconstruction of the forward pass: 0 MP5, 1 LIMO3
   unsigned* err;                // error word (checked builds)
   int ndom;
 };

@@ -82,3 +82,26 @@ def test_torchref_step_with_passive_blocks_equals_oracle(case):
     m = T.block_mask(n, nb, act).numpy()
     assert np.array_equal(got.numpy()[:, ~m], U[:, ~m])
     assert np.abs(got.numpy()[:, m] - U[:, m]).max() > 0
+
+
+# LIMO3 reconstruction (Sec. 2.2 cites Cada & Torrilhon 2009), r = 1 and a larger radius
+LIMO = [
+    (O.EULER, 1, (30, 1, 1), ((1, 1), (0, 0), (0, 0)), ((0, 0),) * 3, O.SSPRK3, 1.0),
+    (O.MHD_GLM, 2, (12, 14, 1), ((0, 0), (2, 2), (0, 0)), ((0, 0), (W.MHD_WALL_Y,) * 2, (0, 0)), O.SSPRK43, 1.0),
+    (O.EULER, 3, (8, 6, 7), ((0, 0), (1, 1), (2, 2)), ((0, 0), (0, 0), (8, 8)), O.SSPRK3, 0.05),
+]
+
+
+@pytest.mark.parametrize("case", range(len(LIMO)))
+def test_torchref_limo3_step_equals_oracle_frozen_step(case):
+    physics, ndim, n, bc, asym, integ, r = LIMO[case]
+    dom, U, g = _smooth(physics, ndim, n, bc, asym, 60 + case, integ)
+    c = O.cfg(physics, ndim, integ, g, recon=O.LIMO3, limo3_r=r)
+    d = O.dom(dom.n, dom.dx, bc=[list(b) for b in bc], asym=asym)
+    h = 0.5 * O.dt(c, d, U, 0.4)[0]
+    want, fl, al, ch = O.step(c, d, U, h)
+    assert fl == 0
+    got = T.step(torch.from_numpy(U.copy()), h, dom.dx, bc, physics, ndim, g, integ, al, ch, asym=asym,
+                 recon=1, limo3_r=r)
+    err = np.abs(got.numpy() - want).max() / np.abs(want).max()
+    assert err <= 1e-13, err

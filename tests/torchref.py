@@ -2,7 +2,7 @@
 
 Written only to obtain reference gradients by autograd for the discrete
 adjoint: the same update as the oracle (Porth et al. 2014, Sec. 2.1-2.3, 4.2-4.3;
-MP5 of Suresh & Huynh 1997) with the splitting speeds of every stage and the
+MP5 of Suresh & Huynh 1997, LIMO3 of Cada & Torrilhon 2009) with the splitting speeds of every stage and the
 GLM speed given as constants (frozen), in vectorised torch operations on CPU.
 Selections use torch.where with the same tie rule as the CUDA path (a strict
 comparison picks the first argument only when strictly smaller), so that the
@@ -89,6 +89,30 @@ def mp5(fm2, fm1, f0, fp1, fp2, eps=1e-10):
     return torch.where(accept, f_or, med)
 
 
+def limo3(um, u0, up, rdx, eps=1e-12):
+    """LIMO3 (Cada & Torrilhon 2009, cited in Sec. 2.2) at the face right of u0, upwind
+    neighbour um, downwind up: u0 + phi(theta) delta_{i+1/2} / 2 with theta = delta_{i-1/2} /
+    delta_{i+1/2}, the third-order phi_3 = (2 + theta)/3 inside the asymptotic region
+    eta = (delta_{i-1/2}^2 + delta_{i+1/2}^2)/(r dx)^2 <= 1 - eps, its limited form
+    max(0, min(phi_3, max(-theta/2, min(2 theta, phi_3, 1.6)))) beyond 1 + eps, a linear blend
+    in between; delta_{i+1/2} = 0 takes the limits (delta_{i-1/2}/3 and 0)."""
+    dm = u0 - um
+    dp = up - u0
+    eta = (dm * dm + dp * dp) / (rdx * rdx)
+    nz = dp != 0
+    dps = torch.where(nz, dp, torch.ones_like(dp))
+    th = dm / dps
+    phi3 = (2.0 + th) / 3.0
+    phil = _max(torch.zeros_like(th), _min(phi3, _max(-0.5 * th, _min(_min(2.0 * th, phi3),
+                                                                      torch.full_like(th, 1.6)))))
+    dphi3 = torch.where(nz, dps * phi3, dm / 3.0)
+    dphil = torch.where(nz, dps * phil, torch.zeros_like(dm))
+    z = (eta - 1.0) / eps
+    blend = 0.5 * ((1.0 - z) * dphi3 + (1.0 + z) * dphil)
+    dphi = torch.where(eta <= 1.0 - eps, dphi3, torch.where(eta >= 1.0 + eps, dphil, blend))
+    return u0 + 0.5 * dphi
+
+
 def _prims(U, physics, ndim, gamma):
     rho = U[0]
     if physics == EULER:
@@ -128,8 +152,9 @@ def _flux(U, d, physics, ndim, gamma, ch):
     return torch.stack(f)
 
 
-def residual(U, dx, bc, physics, ndim, gamma, alpha, ch, asym=None):
-    """L(U) for U of shape (nv, nz, ny, nx); alpha[d] fixed splitting speeds."""
+def residual(U, dx, bc, physics, ndim, gamma, alpha, ch, asym=None, recon=0, limo3_r=1.0):
+    """L(U) for U of shape (nv, nz, ny, nx); alpha[d] fixed splitting speeds; recon 0 MP5,
+    1 LIMO3 (radius limo3_r dx of the asymptotic region)."""
     L = torch.zeros_like(U)
     for d in range(ndim):
         axis = 3 - d  # x is the last axis
@@ -144,8 +169,13 @@ def residual(U, dx, bc, physics, ndim, gamma, alpha, ch, asym=None):
             idx[axis] = slice(a, b)
             return T[tuple(idx)]
         # faces k = 0..n between extended cells k+2 and k+3
-        left = mp5(sl(Fp, 0, n + 1), sl(Fp, 1, n + 2), sl(Fp, 2, n + 3), sl(Fp, 3, n + 4), sl(Fp, 4, n + 5))
-        right = mp5(sl(Fm, 5, n + 6), sl(Fm, 4, n + 5), sl(Fm, 3, n + 4), sl(Fm, 2, n + 3), sl(Fm, 1, n + 2))
+        if recon == 1:
+            rdx = limo3_r * dx[d]
+            left = limo3(sl(Fp, 1, n + 2), sl(Fp, 2, n + 3), sl(Fp, 3, n + 4), rdx)
+            right = limo3(sl(Fm, 4, n + 5), sl(Fm, 3, n + 4), sl(Fm, 2, n + 3), rdx)
+        else:
+            left = mp5(sl(Fp, 0, n + 1), sl(Fp, 1, n + 2), sl(Fp, 2, n + 3), sl(Fp, 3, n + 4), sl(Fp, 4, n + 5))
+            right = mp5(sl(Fm, 5, n + 6), sl(Fm, 4, n + 5), sl(Fm, 3, n + 4), sl(Fm, 2, n + 3), sl(Fm, 1, n + 2))
         Fh = left + right
         L = L - (sl(Fh, 1, n + 1) - sl(Fh, 0, n)) / dx[d]
     return L
@@ -170,7 +200,8 @@ def ssprk_table(integrator):
     return a, b
 
 
-def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18, asym=None, mask=None):
+def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_cr=0.18, asym=None, mask=None,
+         recon=0, limo3_r=1.0):
     """One SSPRK step with frozen per-stage splitting speeds alpha_stage[s][3] and c_h.
     mask (bool, shape of one variable): the cells of active blocks (App. C); the others
     keep U^n in every stage, so that active cells next to them read U^n there."""
@@ -178,7 +209,7 @@ def step(U, dt, dx, bc, physics, ndim, gamma, integrator, alpha_stage, ch, glm_c
     stages = [U]
     Ls = []
     for i in range(len(a)):
-        Ls.append(residual(stages[i], dx, bc, physics, ndim, gamma, alpha_stage[i], ch, asym))
+        Ls.append(residual(stages[i], dx, bc, physics, ndim, gamma, alpha_stage[i], ch, asym, recon, limo3_r))
         acc = torch.zeros_like(U)
         for k in range(i + 1):
             if a[i][k] != 0.0:
