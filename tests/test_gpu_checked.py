@@ -84,6 +84,23 @@ def test_checked_adjoint_and_activation():
         assert s.error() == A.OK
         outs.append(out.cpu())
     assert torch.equal(outs[0], outs[1])
+    # a partly active domain next to mirror walls, with MP5 and with LIMO3: the adjoint's
+    # items over passive neighbours and the LIMO3 pieces under the checks
+    wb = W.wall_blast2d(64, 16)
+    wb.active = (np.random.default_rng(3).random(len(wb.active)) > 0.35).astype(np.uint8)
+    for recon in (0, 1):
+        wb.recon = recon
+        Ub = torch.from_numpy(np.ascontiguousarray(wb.U.ravel())).cuda()
+        gb = torch.from_numpy(np.random.default_rng(2).standard_normal(Ub.numel())).cuda()
+        dtb = torch.full((1,), 1e-4, dtype=torch.float64, device="cuda")
+        outs = []
+        for checked in (False, True):
+            s = A.Solver.from_workload(wb, checked=checked)
+            out = torch.empty_like(Ub)
+            s.adjoint(Ub, dtb, gb, out)
+            assert s.error() == A.OK, (recon, checked)
+            outs.append(out.cpu())
+        assert torch.equal(outs[0], outs[1]), recon
     w = W.blast3d(64, 8, noise=0.0)
     res = []
     for checked in (False, True):
