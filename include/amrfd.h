@@ -188,6 +188,13 @@ int amrfd_set_tile(amrfd_handle *h, int seg, int lines, int threads);
 /* Read back the current tile. */
 int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);
 
+/* Set the tile of amrfd_adjoint's transposed flux pass (no counterpart in the paper; a
+   tuning knob like amrfd_set_tile): seg = max cells per segment (6..64), lines = lines
+   per tile (1..32), threads per block (multiple of 32, 32..256); its shared memory must
+   stay within 227 KB (AMRFD_ERR_INVALID_ARG beyond). Every tile gives bitwise the same
+   gradients. Synchronous when the adjoint's workspace exists (its items are rebuilt). */
+int amrfd_set_adjoint_tile(amrfd_handle *h, int seg, int lines, int threads);
+
 /* Kernel timing for measurement. After amrfd_timing_begin(h, capacity), every
    kernel that amrfd_dt, amrfd_step and amrfd_step_batched launch is bracketed by
    a pair of CUDA events recorded on the launching stream (amrfd_step_batched

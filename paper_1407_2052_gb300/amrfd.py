@@ -25,7 +25,7 @@ EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
            "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
            "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active",
-           "amrfd_step_cfl", "amrfd_fp64_peak")
+           "amrfd_step_cfl", "amrfd_fp64_peak", "amrfd_set_adjoint_tile")
 
 
 class Config(ctypes.Structure):
@@ -72,6 +72,7 @@ def load(checked=False):
     L.amrfd_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     L.amrfd_autotune.argtypes = [vp, vp, vp, vp]
     L.amrfd_set_tile.argtypes = [vp, i, i, i]
+    L.amrfd_set_adjoint_tile.argtypes = [vp, i, i, i]
     L.amrfd_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.amrfd_get_alpha.argtypes = [vp, vp, i, vp]
     L.amrfd_get_error.argtypes = [vp, vp]
@@ -321,6 +322,10 @@ class Solver:
 
     def set_tile(self, seg, lines, threads):
         _check(self._L.amrfd_set_tile(self._h, seg, lines, threads), "amrfd_set_tile")
+
+    def set_adjoint_tile(self, seg, lines, threads):
+        """amrfd_set_adjoint_tile: the tile of the adjoint's transposed flux pass."""
+        _check(self._L.amrfd_set_adjoint_tile(self._h, seg, lines, threads), "amrfd_set_adjoint_tile")
 
     def get_tile(self):
         a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -973,6 +973,22 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
   return AMRFD_OK;
 }
 
+int amrfd_set_adjoint_tile(amrfd_handle* h, int seg, int lines, int threads) {
+  if (!h || seg < 6 || seg > 64 || lines < 1 || lines > 32 || threads < 32 || threads > 256 || threads % 32)
+    return AMRFD_ERR_INVALID_ARG;
+  const int SSa = (seg + 10) | 1, SSg = (seg + 6) | 1;
+  if (sizeof(double) * (size_t)h->nv * lines * (2 * SSa + SSg) > 227 * 1024) return AMRFD_ERR_INVALID_ARG;
+  h->adj_seg = seg;
+  h->adj_lines = lines;
+  h->adj_threads = threads;
+  if (h->d_adj_items) {  // the workspace exists: rebuild the items for the new tile
+    cudaFree(h->d_adj_items);
+    h->d_adj_items = nullptr;
+    return build_adjoint_items(h);
+  }
+  return AMRFD_OK;
+}
+
 int amrfd_set_tile(amrfd_handle* h, int seg, int lines, int threads) {
   if (!h || seg < 8 || seg > 64 || lines < 1 || lines > 32 || threads < 32 || threads > kFluxMaxThreads || threads % 32)
     return AMRFD_ERR_INVALID_ARG;

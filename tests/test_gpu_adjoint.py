@@ -302,6 +302,31 @@ def test_adjoint_independent_of_flux_tile():
     assert all(torch.equal(o, outs[0]) for o in outs[1:])
 
 
+def test_adjoint_independent_of_adjoint_tile():
+    """The transposed flux pass gathers every cell's gradient from the same faces in the same
+    order under every tile of its own (amrfd_set_adjoint_tile): bitwise equal gradients, also
+    across mirror and outflow faces with passive blocks; out-of-range tiles are rejected."""
+    A = _A()
+    w = _mixed_workload(MIXED[2][1])
+    U = torch.from_numpy(np.ascontiguousarray(w.U.ravel())).cuda()
+    dt = torch.full((1,), 2e-3, dtype=torch.float64, device="cuda")
+    g = torch.from_numpy(np.random.default_rng(41).standard_normal(w.U.size)).cuda()
+    s = A.Solver.from_workload(w)
+    outs = []
+    for tile in [None, (16, 16, 160), (32, 8, 128), (6, 1, 32), (64, 4, 64)]:
+        if tile:
+            s.set_adjoint_tile(*tile)
+        out = torch.empty_like(U)
+        s.adjoint(U, dt, g, out)
+        assert s.error() == A.OK
+        outs.append(out.cpu())
+    assert all(torch.equal(o, outs[0]) for o in outs[1:])
+    for bad in [(5, 8, 128), (16, 33, 128), (16, 8, 100), (16, 8, 512), (64, 32, 256)]:
+        with pytest.raises(A.AmrfdError) as e:
+            s.set_adjoint_tile(*bad)
+        assert e.value.code == A.ERR_INVALID_ARG
+
+
 def test_rollout_200_steps_checkpoint_20_at_512():
     """The adjoint workload's full length: 512^2, 200 fixed-dt steps, checkpoints every 20,
     J = sum |B|^2/2 dx dy; the rollout gradient equals (bitwise) the chain of single-step
