@@ -32,6 +32,7 @@
 #ifndef AMRFD_H
 #define AMRFD_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -175,6 +176,23 @@ int amrfd_step_cfl(amrfd_handle *h, double *U, double *dt_dev, double t, double 
    dimension. */
 int amrfd_adjoint(amrfd_handle *h, const double *U_n, const double *dt_dev, const double *gU_np1,
                   double *gU_n, void *stream);
+
+/* A step that keeps what its adjoint needs, so that the adjoint need not recompute it
+   (no counterpart in the paper: the discrete adjoint above, split at its forward
+   recomputation). amrfd_record_bytes(h): size of one record of this handle (the splitting
+   speeds of every stage input, the stage states U^(1..s-1), the limiter pieces of every
+   flux pass); 0 for a NULL handle. amrfd_step_record: one SSPRK step of U in place, exactly
+   as amrfd_step_batched, that also fills `record` (device memory of at least
+   amrfd_record_bytes bytes, 16-byte aligned, caller-owned). amrfd_adjoint_recorded: the
+   gradient amrfd_adjoint would give for the step that wrote `record`, from U_n = the state
+   before that step (the caller keeps a copy: the step overwrote U) and the same dt_dev,
+   without the forward recomputation. A record serves only the handle that wrote it, with
+   its active flags unchanged since. Both are asynchronous; AMRFD_ERR_INVALID_ARG for NULL
+   or misaligned pointers, AMRFD_ERR_UNSUPPORTED as amrfd_adjoint. */
+size_t amrfd_record_bytes(const amrfd_handle *h);
+int amrfd_step_record(amrfd_handle *h, double *U, const double *dt_dev, void *record, void *stream);
+int amrfd_adjoint_recorded(amrfd_handle *h, const double *U_n, const double *dt_dev, const void *record,
+                           const double *gU_np1, double *gU_n, void *stream);
 
 /* Choose the flux-pass tile (segment length along the sweep, lines per tile,
    threads per block) by timing the candidates on this handle's work, using U

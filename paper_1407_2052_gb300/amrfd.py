@@ -25,7 +25,8 @@ EXPORTS = ("amrfd_create", "amrfd_set_active", "amrfd_dt", "amrfd_step", "amrfd_
            "amrfd_adjoint", "amrfd_autotune", "amrfd_set_tile", "amrfd_get_tile", "amrfd_get_alpha",
            "amrfd_get_error", "amrfd_destroy", "amrfd_strerror", "amrfd_timing_begin", "amrfd_timing_end",
            "amrfd_dt_noalloc", "amrfd_flag_steady", "amrfd_activate", "amrfd_get_active",
-           "amrfd_step_cfl", "amrfd_fp64_peak", "amrfd_set_adjoint_tile")
+           "amrfd_step_cfl", "amrfd_fp64_peak", "amrfd_set_adjoint_tile", "amrfd_record_bytes",
+           "amrfd_step_record", "amrfd_adjoint_recorded")
 
 
 class Config(ctypes.Structure):
@@ -73,6 +74,9 @@ def load(checked=False):
     L.amrfd_autotune.argtypes = [vp, vp, vp, vp]
     L.amrfd_set_tile.argtypes = [vp, i, i, i]
     L.amrfd_set_adjoint_tile.argtypes = [vp, i, i, i]
+    L.amrfd_record_bytes.argtypes = [vp]
+    L.amrfd_step_record.argtypes = [vp, vp, vp, vp, vp]
+    L.amrfd_adjoint_recorded.argtypes = [vp, vp, vp, vp, vp, vp, vp]
     L.amrfd_get_tile.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
     L.amrfd_get_alpha.argtypes = [vp, vp, i, vp]
     L.amrfd_get_error.argtypes = [vp, vp]
@@ -85,8 +89,9 @@ def load(checked=False):
     L.amrfd_strerror.argtypes = [i]
     L.amrfd_strerror.restype = ctypes.c_char_p
     for name in EXPORTS:
-        if name not in ("amrfd_destroy", "amrfd_strerror"):
+        if name not in ("amrfd_destroy", "amrfd_strerror", "amrfd_record_bytes"):
             getattr(L, name).restype = i
+    L.amrfd_record_bytes.restype = ctypes.c_size_t
     _libs[checked] = L
     return L
 
@@ -278,6 +283,34 @@ class Solver:
     def adjoint(self, U_n, dt, gU_np1, gU_n, stream=None):
         _check(self._L.amrfd_adjoint(self._h, _ptr(U_n), _ptr(dt), _ptr(gU_np1), _ptr(gU_n), _stream(stream)),
                "amrfd_adjoint")
+        return gU_n
+
+    def record_bytes(self):
+        """amrfd_record_bytes: bytes of one step record of this handle."""
+        return int(self._L.amrfd_record_bytes(self._h))
+
+    def new_record(self):
+        """A device buffer for one step record (uint8 CUDA tensor)."""
+        import torch
+        return torch.empty(self.record_bytes(), dtype=torch.uint8, device="cuda")
+
+    def _record(self, rec):
+        import torch
+        if (not isinstance(rec, torch.Tensor) or not rec.is_cuda or rec.dtype != torch.uint8 or not rec.is_contiguous()
+                or rec.numel() < self.record_bytes() or rec.data_ptr() % 16):
+            raise TypeError("expected a contiguous 16-byte aligned CUDA uint8 tensor of record_bytes() bytes")
+        return ctypes.c_void_p(rec.data_ptr())
+
+    def step_record(self, U, dt, record, stream=None):
+        """amrfd_step_record: one step of U in place that also fills `record` for its adjoint."""
+        _check(self._L.amrfd_step_record(self._h, _ptr(U), _ptr(dt), self._record(record), _stream(stream)),
+               "amrfd_step_record")
+        return U
+
+    def adjoint_recorded(self, U_n, dt, record, gU_np1, gU_n, stream=None):
+        """amrfd_adjoint_recorded: the adjoint of the recorded step (U_n: the state before it)."""
+        _check(self._L.amrfd_adjoint_recorded(self._h, _ptr(U_n), _ptr(dt), self._record(record), _ptr(gU_np1),
+                                             _ptr(gU_n), _stream(stream)), "amrfd_adjoint_recorded")
         return gU_n
 
     def tile_key(self):

@@ -4,7 +4,8 @@ AmrfdStep: forward = one SSPRK step (amrfd_step_batched on a copy of U),
 backward = amrfd_adjoint (splitting speeds, GLM speed and psi damping held at
 their forward values; the time step is a fixed input).
 rollout: n steps with checkpoints every k steps; the backward pass recomputes
-each segment's states from its checkpoint and runs the adjoints in reverse.
+each segment's states from its checkpoint, recording every step (amrfd_step_record),
+and runs the recorded adjoints in reverse (amrfd_adjoint_recorded).
 """
 import torch
 
@@ -60,9 +61,12 @@ class _Rollout(torch.autograd.Function):
         solver, nsteps, every, stats = ctx.solver, ctx.nsteps, ctx.every, ctx.stats
         g = g.contiguous().clone()
         gn = torch.empty_like(g)
-        # the recomputation steps one work buffer (one captured graph, replayed) and keeps
-        # a copy of every state of the segment for the reverse sweep
-        states = [torch.empty_like(g) for _ in range(min(every, nsteps))]
+        # the recomputation steps one work buffer and keeps every state of the segment and
+        # every step's record (stage states, limiter pieces, speeds), so that the reverse
+        # sweep needs no second forward pass per step
+        m = min(every, nsteps)
+        states = [torch.empty_like(g) for _ in range(m)]
+        records = [solver.new_record() for _ in range(m)]
         wb = getattr(solver, "_step_buf", None)
         if wb is None or wb.shape != g.shape or wb.device != g.device:
             wb = solver._step_buf = torch.empty_like(g)
@@ -75,12 +79,11 @@ class _Rollout(torch.autograd.Function):
             wb.copy_(ctx.ckpts[seg])
             for j in range(count):
                 states[j].copy_(wb)
-                if j + 1 < count:
-                    solver.step_batched(wb, dt)
+                solver.step_record(wb, dt, records[j])
             if ev:
                 ev[3 * i + 1].record()
             for j in reversed(range(count)):
-                solver.adjoint(states[j], dt, g, gn)
+                solver.adjoint_recorded(states[j], dt, records[j], g, gn)
                 g, gn = gn, g
             if ev:
                 ev[3 * i + 2].record()

@@ -846,11 +846,12 @@ int build_adjoint_items(amrfd_handle* h) {
 
 }  // namespace
 
-int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
-                  void* stream) {
-  if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
-  Range rg("amrfd adjoint");
-  cudaStream_t s = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// Checks and workspace of the discrete adjoint (allocated on first use).
+int adjoint_prepare(amrfd_handle* h, cudaStream_t s) {
   {
     int rc = refresh_active_host(h, s);
     if (rc) return rc;
@@ -878,10 +879,17 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     int rc = build_adjoint_items(h);
     if (rc) return rc;
   }
+  return AMRFD_OK;
+}
+
+// The step's forward pass with every flux pass recording the limiter's pieces: stage
+// states into st[1..s-1], the pieces of stage i into tape + (i-1) tape_len, the splitting
+// speeds of every stage input into the handle's slots 0..s-1. With Uout, also the last
+// stage (a full step, written to Uout; U_n may be Uout).
+int adjoint_forward(amrfd_handle* h, const double* U_n, const double* dt_dev, double* const* st, unsigned short* tape,
+                    double* Uout, cudaStream_t s) {
   const int ph = h->cfg.physics, nv = h->nv;
   const int cgrid = 8 * h->nsm;
-  double* Un = const_cast<double*>(U_n);
-  // forward recompute of U^(1..s-1) and of the splitting speeds of every stage input
   CK(cudaMemsetAsync(h->d_slot, 0, sizeof(unsigned long long) * h->ns * h->ndom * 4, s));
   CK(cudaMemsetAsync(h->d_tlow, 0, sizeof(unsigned) * h->ns * h->ndom * 4, s));
   CK(cudaMemsetAsync(h->d_counters, 0, sizeof(int) * 2 * kMaxStages, s));
@@ -890,32 +898,50 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     if (rc) return rc;
   }
   for (int i = 1; i <= h->ns; i++) {
-    // every stage's flux pass records the limiter's pieces; states up to U^(s-1)
-    const double* Uk = (i == 1) ? U_n : h->d_stage[i - 1];
+    const double* Uk = (i == 1) ? U_n : st[i - 1];
     FluxParams fp = flux_params(h, Uk, U_n, i - 1);
     fp.items = h->d_fact; fp.nitems_dev = h->d_counts; fp.counter = h->d_counters + 2 * (i - 1);
-    fp.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
+    fp.tape = tape + (size_t)(i - 1) * h->tape_len;
     {
       Tick tk(h, K_FLUX, s);
       CK(launch_flux(ph, nv, fp, h->flux_grid, h->launch_threads, h->flux_smem, s));
     }
-    if (i == h->ns) break;
-    CombParams cp = comb_params(h, Un, dt_dev, i);
+    if (i == h->ns && !Uout) break;
+    CombParams cp = comb_params(h, const_cast<double*>(U_n), dt_dev, i);
+    for (int k = 1; k < h->ns; k++) cp.buf[k] = st[k];
+    cp.out = (i == h->ns) ? Uout : st[i];
     cp.items = h->d_cact; cp.nitems_dev = h->d_counts + 1;
-    CK(launch_combine(ph, nv, cp, cgrid, 256, s));
-    SpeedParams sp = speed_params(h, h->d_stage[i], i, 0);
+    auto a16 = [](const void* q) { return q == nullptr || ((uintptr_t)q & 15) == 0; };
+    for (int k = 0; k < h->ns; k++) cp.pairs = cp.pairs && a16(cp.buf[k]);
+    cp.pairs = cp.pairs && a16(cp.out);
+    {
+      Tick tk(h, K_COMBINE, s);
+      CK(launch_combine(ph, nv, cp, cgrid, 256, s));
+    }
+    if (i == h->ns) break;
+    SpeedParams sp = speed_params(h, st[i], i, 0);
     sp.exact = 1;
     int rc = launch_speeds_over(h, sp, true, std::vector<int>(), s);
     if (rc) return rc;
   }
-  CK(launch_psi_fac(slot(h, 0), dt_dev, h->d_psifac, h->ndom, h->cfg.ndim, h->cfg.glm_cr,
+  return AMRFD_OK;
+}
+
+// The reverse sweep over the stages from the forward pass's stage states, pieces and
+// speeds (slots[k][dom][4], k = 0..s-1).
+int adjoint_reverse(amrfd_handle* h, const double* U_n, const double* dt_dev, double* const* st,
+                    const unsigned short* tape, const unsigned long long* slots, const double* gU_np1, double* gU_n,
+                    cudaStream_t s) {
+  const int ph = h->cfg.physics, nv = h->nv;
+  const int cgrid = 8 * h->nsm;
+  const size_t sl = (size_t)h->ndom * 4;
+  CK(launch_psi_fac(slots, dt_dev, h->d_psifac, h->ndom, h->cfg.ndim, h->cfg.glm_cr,
                     h->cfg.physics == AMRFD_MHD_GLM, s));
-  // reverse sweep over the stages
   CK(cudaMemsetAsync(gU_n, 0, sizeof(double) * h->nelem, s));
   for (int k = 1; k < h->ns; k++) CK(cudaMemsetAsync(h->d_gstage[k], 0, sizeof(double) * h->nelem, s));
   for (int i = h->ns; i >= 1; i--) {
     const double* gout = (i == h->ns) ? gU_np1 : h->d_gstage[i];
-    const double* S = (i == 1) ? U_n : h->d_stage[i - 1];
+    const double* S = (i == 1) ? U_n : st[i - 1];
     AdjFluxParams ap{};
     ap.doms = h->d_dom;
     ap.active = h->d_active;
@@ -928,15 +954,15 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     ap.dt = dt_dev;
     ap.b = h->co[i - 1].b;
     for (int d = 0; d < 3; d++) ap.gL[d] = h->d_L[d] ? h->d_L[d] : h->d_L[0];
-    ap.araw = slot(h, i - 1);
-    ap.araw0 = slot(h, 0);
+    ap.araw = slots + (size_t)(i - 1) * sl;
+    ap.araw0 = slots;
     ap.gm1 = h->cfg.gamma - 1.0;
     ap.ndim = h->cfg.ndim;
     ap.P = h->adj_P;
     ap.SSa = h->adj_SSa;
     ap.SSg = h->adj_SSg;
     ap.glm = h->cfg.physics == AMRFD_MHD_GLM;
-    ap.tape = h->d_tape + (size_t)(i - 1) * h->tape_len;
+    ap.tape = tape + (size_t)(i - 1) * h->tape_len;
     ap.limo3 = h->cfg.recon == AMRFD_LIMO3;
     ap.err = h->d_err;
     ap.ndom = h->ndom;
@@ -971,6 +997,68 @@ int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, cons
     }
   }
   return AMRFD_OK;
+}
+
+// Layout of a step record: the splitting speeds of the s stage inputs, the stage states
+// U^(1..s-1), the limiter pieces of the s flux passes.
+size_t record_slots_bytes(const amrfd_handle* h) { return sizeof(unsigned long long) * h->ns * h->ndom * 4; }
+size_t record_states_bytes(const amrfd_handle* h) { return sizeof(double) * (size_t)(h->ns - 1) * h->nelem; }
+size_t record_tape_bytes(const amrfd_handle* h) {
+  return sizeof(unsigned short) * (size_t)std::max<long long>(1, h->tape_len) * h->ns;
+}
+
+}  // namespace
+
+extern "C" {
+
+int amrfd_adjoint(amrfd_handle* h, const double* U_n, const double* dt_dev, const double* gU_np1, double* gU_n,
+                  void* stream) {
+  if (!h || !U_n || !dt_dev || !gU_np1 || !gU_n) return AMRFD_ERR_INVALID_ARG;
+  Range rg("amrfd adjoint");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = adjoint_prepare(h, s);
+  if (rc) return rc;
+  // forward recompute of U^(1..s-1), the pieces and the splitting speeds, then the reverse sweep
+  rc = adjoint_forward(h, U_n, dt_dev, h->d_stage, h->d_tape, nullptr, s);
+  if (rc) return rc;
+  return adjoint_reverse(h, U_n, dt_dev, h->d_stage, h->d_tape, h->d_slot, gU_np1, gU_n, s);
+}
+
+size_t amrfd_record_bytes(const amrfd_handle* h) {
+  if (!h) return 0;
+  return record_slots_bytes(h) + record_states_bytes(h) + record_tape_bytes(h);
+}
+
+int amrfd_step_record(amrfd_handle* h, double* U, const double* dt_dev, void* record, void* stream) {
+  if (!h || !U || !dt_dev || !record || ((uintptr_t)record & 15)) return AMRFD_ERR_INVALID_ARG;
+  Range rg("amrfd step record");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = adjoint_prepare(h, s);
+  if (rc) return rc;
+  unsigned char* base = (unsigned char*)record;
+  double* states = (double*)(base + record_slots_bytes(h));
+  unsigned short* tape = (unsigned short*)(base + record_slots_bytes(h) + record_states_bytes(h));
+  double* st[kMaxStages] = {};
+  for (int k = 1; k < h->ns; k++) st[k] = states + (size_t)(k - 1) * h->nelem;
+  rc = adjoint_forward(h, U, dt_dev, st, tape, U, s);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(base, h->d_slot, record_slots_bytes(h), cudaMemcpyDeviceToDevice, s));
+  return AMRFD_OK;
+}
+
+int amrfd_adjoint_recorded(amrfd_handle* h, const double* U_n, const double* dt_dev, const void* record,
+                           const double* gU_np1, double* gU_n, void* stream) {
+  if (!h || !U_n || !dt_dev || !record || !gU_np1 || !gU_n || ((uintptr_t)record & 15)) return AMRFD_ERR_INVALID_ARG;
+  Range rg("amrfd adjoint recorded");
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = adjoint_prepare(h, s);
+  if (rc) return rc;
+  const unsigned char* base = (const unsigned char*)record;
+  double* states = (double*)(base + record_slots_bytes(h));
+  const unsigned short* tape = (const unsigned short*)(base + record_slots_bytes(h) + record_states_bytes(h));
+  double* st[kMaxStages] = {};
+  for (int k = 1; k < h->ns; k++) st[k] = states + (size_t)(k - 1) * h->nelem;
+  return adjoint_reverse(h, U_n, dt_dev, st, tape, (const unsigned long long*)base, gU_np1, gU_n, s);
 }
 
 int amrfd_set_adjoint_tile(amrfd_handle* h, int seg, int lines, int threads) {

@@ -15,7 +15,7 @@ def _declared():
     for f in os.listdir(os.path.join(ROOT, "include")):
         if f.endswith(".h"):
             src = open(os.path.join(ROOT, "include", f)).read()
-            names += re.findall(r"^\s*(?:int|void|const char\s*\*)\s*(amrfd_\w+)\s*\(", src, re.M)
+            names += re.findall(r"^\s*(?:int|void|size_t|const char\s*\*)\s*(amrfd_\w+)\s*\(", src, re.M)
     return sorted(set(names))
 
 

@@ -302,6 +302,31 @@ def test_adjoint_independent_of_flux_tile():
     assert all(torch.equal(o, outs[0]) for o in outs[1:])
 
 
+@pytest.mark.parametrize("name,make,dt", [CASES[1], CASES[8]], ids=[CASES[1][0], CASES[8][0]])
+def test_recorded_step_and_adjoint_equal_plain_ones(name, make, dt):
+    """amrfd_step_record advances U exactly as amrfd_step_batched does, and
+    amrfd_adjoint_recorded from its record gives exactly amrfd_adjoint's gradient (bitwise),
+    also for a partly active domain and for LIMO3."""
+    A = _A()
+    cases = [make(), _mixed_workload(MIXED[2][1]), _limo3(W.adjoint2d(32), 0.05)]
+    for w in cases:
+        s = A.Solver.from_workload(w)
+        U = torch.from_numpy(np.ascontiguousarray(w.U.ravel())).cuda()
+        dtt = torch.full((s.ndom,), dt, dtype=torch.float64, device="cuda")
+        g = torch.from_numpy(np.random.default_rng(43).standard_normal(w.U.size)).cuda()
+        rec = s.new_record()
+        assert rec.numel() == s.record_bytes() > 0
+        V1, V2 = U.clone(), U.clone()
+        s.step_batched(V1, dtt)
+        s.step_record(V2, dtt, rec)
+        assert torch.equal(V1, V2)
+        a1, a2 = torch.empty_like(U), torch.empty_like(U)
+        s.adjoint(U, dtt, g, a1)
+        s.adjoint_recorded(U, dtt, rec, g, a2)
+        assert s.error() == A.OK
+        assert torch.equal(a1, a2)
+
+
 def test_adjoint_independent_of_adjoint_tile():
     """The transposed flux pass gathers every cell's gradient from the same faces in the same
     order under every tile of its own (amrfd_set_adjoint_tile): bitwise equal gradients, also
