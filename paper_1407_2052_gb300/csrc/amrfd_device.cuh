@@ -215,39 +215,6 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
   return mp_accept_slow(X, mp, eps);
 }
 
-// ---------------------------------------------------------- MP5 in difference form
-// MP5 (Suresh & Huynh 1997) at face i+1/2 from (f_{i-2}, ..., f_{i+2}), written in
-// differences Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1}
-// and the curvature-limited second differences Mp (at i+1/2) and Mm (at i-1/2):
-//   f_or - f_i = (11 D0 - 2 Dm + 24 D1 - 3 Dp)/60,  f_mp - f_i = minmod(D1, 4 D0),
-//   f_ul - f_i = 4 D0,  f_md - f_i = D1/2 - Mp/2,  f_lc - f_i = D0/2 + 4 Mm/3,
-// with the acceptance test (f_or - f_i)(f_or - f_mp) <= eps and otherwise
-// median(f_or, f_min, f_max). Everything is carried at twice its value, which makes
-// the halvings and the factor 4 exact exponent shifts; the result is
-// 2 (f_face - f_i). NEG evaluates the mirror-image stencil whose differences are
-// the negatives of the ones passed in (the right-biased reconstruction).
-// eps16 = 16 eps: 4 eps for values doubled twice (splitting without the 1/2, and here).
-template <bool NEG>
-__device__ __forceinline__ double mp5_rel2(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
-                                           double eps16) {
-  constexpr double sg = NEG ? -1.0 : 1.0;
-  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
-                   c6 = sg * (6.0 / 60.0);
-  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));  // 2 (f_or - f_i)
-  X = fma(-c6, Dp, X);
-  const double d0 = NEG ? dneg(D0) : D0;
-  const double d1 = NEG ? dneg(D1) : D1;
-  const double ul = dscale<3>(d0);     // 2 (f_ul - f_i)
-  const double d1x2 = dscale<1>(d1);   // 2 (f_{i+1} - f_i)
-  const double mp = iminmod(d1x2, ul);  // 2 (f_mp - f_i)
-  if (mp_accept(X, mp, eps16)) return X;
-  const double md = d1 - Mp;                  // 2 (f_md - f_i)
-  const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
-  const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
-  const double fmax = imin(imax(imax(0.0, d1x2), md), imax(imax(0.0, ul), lc));
-  return imedian(X, fmin, fmax);
-}
-
 // minmod4(4 ka - kb, 4 kb - ka, ka, kb): the curvature-limited second difference at
 // a face from the curvatures of its two cells. Zero unless ka, kb share a sign; then,
 // with s the smaller and l the larger in magnitude, 4 l - s never wins and the
@@ -281,11 +248,24 @@ __device__ __forceinline__ double dm4(double ka, double kb) {
   return r;
 }
 
-// mp5_rel2 that also reports whether the acceptance test failed (rej). CARRY takes
-// the curvature-limited second differences Mp, Mm from the caller (carried along the
-// line); otherwise they are formed here, only when the test fails, from the curvatures
-// of cells i-1, i, i+1 with the operands and order of the carried ones (for NEG, of
-// the mirrored stencil), so both forms give the same result.
+// ---------------------------------------------------------- MP5 in difference form
+// MP5 (Suresh & Huynh 1997) at face i+1/2 from (f_{i-2}, ..., f_{i+2}), written in
+// differences Dm = f_{i-1}-f_{i-2}, D0 = f_i-f_{i-1}, D1 = f_{i+1}-f_i, Dp = f_{i+2}-f_{i+1}
+// and the curvature-limited second differences Mp (at i+1/2) and Mm (at i-1/2):
+//   f_or - f_i = (11 D0 - 2 Dm + 24 D1 - 3 Dp)/60,  f_mp - f_i = minmod(D1, 4 D0),
+//   f_ul - f_i = 4 D0,  f_md - f_i = D1/2 - Mp/2,  f_lc - f_i = D0/2 + 4 Mm/3,
+// with the acceptance test (f_or - f_i)(f_or - f_mp) <= eps and otherwise
+// median(f_or, f_min, f_max). Everything is carried at twice its value, which makes
+// the halvings and the factor 4 exact exponent shifts; the result is
+// 2 (f_face - f_i). NEG evaluates the mirror-image stencil whose differences are
+// the negatives of the ones passed in (the right-biased reconstruction).
+// eps16 = 16 eps: 4 eps for values doubled twice (splitting without the 1/2, and here).
+//
+// mp5_rel2_r also reports whether the acceptance test failed (rej). CARRY takes the
+// curvature-limited second differences Mp, Mm from the caller (carried along the line);
+// otherwise they are formed here, only when the test fails, from the curvatures of cells
+// i-1, i, i+1 with the operands and order of the carried ones (for NEG, of the mirrored
+// stencil), so both forms give the same result.
 template <bool NEG, bool CARRY>
 __device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
                                              double eps16, bool& rej) {
@@ -321,7 +301,7 @@ __device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, do
 }
 
 // ------------------------------------------------ selection-tracking variants
-// The same operations as mp5_rel2 / dm4 (bit-identical results), also reporting
+// The same operations as mp5_rel2_r / dm4 (bit-identical results), also reporting
 // which linear piece produced the value, for the discrete adjoint.
 enum { SEL_X = 0, SEL_ZERO = 1, SEL_D1 = 2, SEL_MD = 3, SEL_UL = 4, SEL_LC = 5 };
 
@@ -336,45 +316,7 @@ __device__ __forceinline__ void imax_sel(double a, int ca, double b, int cb, dou
   cr = t ? cb : ca;
 }
 
-template <bool NEG>
-__device__ __forceinline__ double mp5_rel2_sel(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
-                                               double eps16, int& code) {
-  constexpr double sg = NEG ? -1.0 : 1.0;
-  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
-                   c6 = sg * (6.0 / 60.0);
-  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));
-  X = fma(-c6, Dp, X);
-  const double d0 = NEG ? dneg(D0) : D0;
-  const double d1 = NEG ? dneg(D1) : D1;
-  const double ul = dscale<3>(d0);
-  const double d1x2 = dscale<1>(d1);
-  const double mp = iminmod(d1x2, ul);
-  code = SEL_X;
-  if (mp_accept(X, mp, eps16)) return X;
-  const double md = d1 - Mp;
-  const double lc = fma(8.0 / 3.0, Mm, d0);
-  double a, b, fmin, fmax, t1, t2, t3;
-  int ca, cb, cmin, cmax, c1, c2, c3;
-  imin_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
-  imin_sel(a, ca, md, SEL_MD, a, ca);
-  imin_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
-  imin_sel(b, cb, lc, SEL_LC, b, cb);
-  imax_sel(a, ca, b, cb, fmin, cmin);
-  imax_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
-  imax_sel(a, ca, md, SEL_MD, a, ca);
-  imax_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
-  imax_sel(b, cb, lc, SEL_LC, b, cb);
-  imin_sel(a, ca, b, cb, fmax, cmax);
-  // median(x, y, z) = max(min(x, y), min(max(x, y), z)) with x = X, y = fmin, z = fmax
-  imin_sel(X, SEL_X, fmin, cmin, t1, c1);
-  imax_sel(X, SEL_X, fmin, cmin, t2, c2);
-  imin_sel(t2, c2, fmax, cmax, t3, c3);
-  double r;
-  imax_sel(t1, c1, t3, c3, r, code);
-  return r;
-}
-
-// Gradient of mp5_rel2 w.r.t. (Dm, D0, D1, Dp, Mp, Mm) for the piece `code`, times g.
+// Gradient of the MP5 value (mp5_rel2_r) w.r.t. (Dm, D0, D1, Dp, Mp, Mm) for the piece `code`, times g.
 template <bool NEG>
 __device__ __forceinline__ void mp5_rel2_grad(int code, double g, double& gDm, double& gD0, double& gD1,
                                               double& gDp, double& gMp, double& gMm) {
@@ -419,6 +361,60 @@ __device__ __forceinline__ void dm4_grad(int code, double g, double& gka, double
   else if (code == 2) gkb = g;
   else if (code == 3) { gka = 4.0 * g; gkb = -g; }
   else if (code == 4) { gkb = 4.0 * g; gka = -g; }
+}
+
+// mp5_rel2_r without CARRY (bit-identical value) that also records the pieces taken: the
+// curvature-limited second differences are formed only where the acceptance test fails,
+// with dm4_sel, and the median's selections are tracked. rec = piece of the value | piece
+// of Mp << 3 | piece of Mm << 6 (the curvature pieces are 0 where the value is f_or,
+// which reads neither).
+template <bool NEG>
+__device__ __forceinline__ double mp5_rel2_rec(double Dm, double D0, double D1, double Dp, double eps16, int& rec) {
+  constexpr double sg = NEG ? -1.0 : 1.0;
+  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
+                   c6 = sg * (6.0 / 60.0);
+  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));
+  X = fma(-c6, Dp, X);
+  const double d0 = NEG ? dneg(D0) : D0;
+  const double d1 = NEG ? dneg(D1) : D1;
+  const double ul = dscale<3>(d0);
+  const double d1x2 = dscale<1>(d1);
+  const double mp = iminmod(d1x2, ul);
+  rec = SEL_X;
+  if (mp_accept(X, mp, eps16)) return X;
+  double Mp, Mm;
+  int cp, cm;
+  if (!NEG) {
+    const double k0 = D1 - D0;
+    Mp = dm4_sel(k0, Dp - D1, cp);
+    Mm = dm4_sel(D0 - Dm, k0, cm);
+  } else {
+    const double k0 = D0 - D1;
+    Mp = dm4_sel(D1 - Dp, k0, cp);
+    Mm = dm4_sel(k0, Dm - D0, cm);
+  }
+  const double md = d1 - Mp;
+  const double lc = fma(8.0 / 3.0, Mm, d0);
+  double a, b, fmin, fmax, t1, t2, t3;
+  int ca, cb, cmin, cmax, c1, c2, c3;
+  imin_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
+  imin_sel(a, ca, md, SEL_MD, a, ca);
+  imin_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
+  imin_sel(b, cb, lc, SEL_LC, b, cb);
+  imax_sel(a, ca, b, cb, fmin, cmin);
+  imax_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);
+  imax_sel(a, ca, md, SEL_MD, a, ca);
+  imax_sel(0.0, SEL_ZERO, ul, SEL_UL, b, cb);
+  imax_sel(b, cb, lc, SEL_LC, b, cb);
+  imin_sel(a, ca, b, cb, fmax, cmax);
+  imin_sel(X, SEL_X, fmin, cmin, t1, c1);
+  imax_sel(X, SEL_X, fmin, cmin, t2, c2);
+  imin_sel(t2, c2, fmax, cmax, t3, c3);
+  double r;
+  int code;
+  imax_sel(t1, c1, t3, c3, r, code);
+  rec = code | (cp << 3) | (cm << 6);
+  return r;
 }
 
 // Reciprocal of a positive normal double: FP32 seed from the leading bits (integer

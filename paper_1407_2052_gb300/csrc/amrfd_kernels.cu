@@ -276,77 +276,44 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
   }
 }
 
-// Sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of the
-// line's extended index (cell j = k-1 left of face k), then the flux difference
-// Fsum_{k-1} - Fsum_k of the segment's cell k-4 stored to out[(k-4) ostr] where
-// wmask has its bit (the factor 1/(2 dx) is applied by the stage combination).
-// The curvature-limited second differences are carried along the line. REC
-// additionally records, per face and bias, which linear piece the limiter took
-// (3 bits) and the pieces of the two curvature limiters it read (3 bits each):
-// tp/tm point at the line's records, face k goes to index f0 + k - 3 if below fend.
-template <bool REC>
-__device__ __forceinline__ void flux_sweep_carry(const double* g, const double* h, int slen, double eps16,
-                                                 unsigned short* tp, unsigned short* tm, int f0, int fend,
-                                                 double* out, long long ostr, unsigned long long wmask,
-                                                 int fmod = 0x7fffffff) {
-  int c1 = 0, c2 = 0, c3 = 0, c4 = 0;
+// Recording sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of
+// the line's extended index (cell j = k-1 left of face k), then the flux difference
+// Fsum_{k-1} - Fsum_k of the segment's cell k-4 stored to out[(k-4) ostr] where wmask has
+// its bit (the factor 1/(2 dx) is applied by the stage combination). Per face and bias it
+// records which linear piece the limiter took and the pieces of the two curvature limiters
+// it read (mp5_rel2_rec, 3 bits each): tp/tm point at the line's records, face k goes to
+// index f0 + k - 3 if below fend (face n of a periodic line, fmod = n, as face 0).
+__device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h, int slen, double eps16,
+                                               unsigned short* tp, unsigned short* tm, int f0, int fend, int fmod,
+                                               double* out, long long ostr, unsigned long long wmask) {
   double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
-  double Pk2 = Pd3 - Pd2, Pk3 = Pd4 - Pd3;
-  double PM2, PM3, MM3, MM4;
-  if (REC) { PM2 = dm4_sel(Pd2 - Pd1, Pk2, c1); PM3 = dm4_sel(Pk2, Pk3, c2); }
-  else { PM2 = dm4(Pd2 - Pd1, Pk2); PM3 = dm4(Pk2, Pk3); }
   double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
-  double Mk3 = Md4 - Md3, Mk4 = Md5 - Md4;
-  if (REC) { MM3 = dm4_sel(Md3 - Md2, Mk3, c3); MM4 = dm4_sel(Mk3, Mk4, c4); }
-  else { MM3 = dm4(Md3 - Md2, Mk3); MM4 = dm4(Mk3, Mk4); }
   double cp = g[2], cm = h[3];
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
-    double Yp, Ym;
-    if (REC) {
-      int yp, ym;
-      // left-biased reconstruction of G^+ centred on cell k-1
-      Yp = mp5_rel2_sel<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16, yp);
-      // right-biased reconstruction of G^- centred on cell k (mirror image)
-      Ym = mp5_rel2_sel<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, ym);
-      const int f = f0 + k - 3;
-      if (f < fend) {
-        const int fi = f >= fmod ? f - fmod : f;  // face n of a periodic line is face 0
-        tp[fi] = (unsigned short)(yp | (c2 << 3) | (c1 << 6));
-        tm[fi] = (unsigned short)(ym | (c3 << 3) | (c4 << 6));
-      }
-    } else {
-      Yp = mp5_rel2<false>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16);
-      Ym = mp5_rel2<true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16);
+    int yp, ym;
+    const double Yp = mp5_rel2_rec<false>(Pd1, Pd2, Pd3, Pd4, eps16, yp);
+    const double Ym = mp5_rel2_rec<true>(Md5, Md4, Md3, Md2, eps16, ym);
+    const int f = f0 + k - 3;
+    if (f < fend) {
+      const int fi = f >= fmod ? f - fmod : f;
+      tp[fi] = (unsigned short)yp;
+      tm[fi] = (unsigned short)ym;
     }
     const double F = fma(0.5, Yp + Ym, cp + cm);
     if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
     Fprev = F;
     if (k < kend) {
       Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
-      const double pk = Pd4 - Pd3;
-      PM2 = PM3;
-      c1 = c2;
-      if (REC) PM3 = dm4_sel(Pk3, pk, c2);
-      else PM3 = dm4(Pk3, pk);
-      Pk3 = pk;
       cp = g[k];
       Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
-      const double mk = Md5 - Md4;
-      MM3 = MM4;
-      c3 = c4;
-      if (REC) MM4 = dm4_sel(Mk4, mk, c4);
-      else MM4 = dm4(Mk4, mk);
-      Mk4 = mk;
       cm = h[k + 1];
     }
   }
-  (void)Pk2;
-  (void)Mk3;
 }
 
-// Plain MP5 sweep, same fluxes as flux_sweep_carry. The curvature-limited second
+// Plain MP5 sweep, same fluxes as flux_sweep_rec. The curvature-limited second
 // differences serve only faces that fail the acceptance test, so a warp (32 lines of
 // one variable) carries them along the line only while some lane keeps failing: after
 // a face where one did, it forms them from the current differences (the operands of
@@ -461,7 +428,7 @@ __device__ __forceinline__ double limo3_y_sel(double a, double b, double s2, lon
   return 0.5 * ((1.0 - z) * y3 + (1.0 + z) * yl);
 }
 
-// LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep_carry; G^+ from
+// LIMO3 sweep of one (line, variable): faces k = 3..slen+3 as in flux_sweep_rec; G^+ from
 // cells k-2..k (centre k-1), G^- mirrored from cells k+1..k-1 (centre k). The squares of
 // the differences are carried along the line (each enters two faces' switch), and the
 // switch compares a^2 + b^2 with (1 -+ 1e-12)/esc.
@@ -487,7 +454,7 @@ __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, in
 }
 
 // limo3_sweep that also records, per face and bias, the piece LIMO3 took (limo3_y_sel),
-// faces f0 + k - 3 below fend as flux_sweep_carry<true> records them.
+// faces f0 + k - 3 below fend as flux_sweep_rec records them.
 __device__ __forceinline__ void limo3_sweep_rec(const double* g, const double* h, int slen, double esc,
                                                 unsigned short* tp, unsigned short* tm, int f0, int fend, int fmod,
                                                 double* out, long long ostr, unsigned long long wmask) {
@@ -571,7 +538,7 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   const int nl = it.nl, slen = it.slen;
   const int np = sweep_parts(slen);
   // MP5 acceptance (f_or - f_i)(f_or - f_mp) <= 1e-10 for F^{+-}; G = 2 F^{+-} and the
-  // doubled relative values of mp5_rel2 scale the product by 16 (exactly)
+  // doubled relative values of mp5_rel2_r scale the product by 16 (exactly)
   const double eps16 = 16.0 * 1e-10;
   constexpr int od1 = D == 0 ? 1 : 0;
   constexpr int od2 = D == 2 ? 1 : 2;
@@ -639,7 +606,7 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
         const double rdx = p.limo3_r * dm.dx[D];
         limo3_sweep_rec(g, h, plen, 0.25 / (rdx * rdx), tp, tm, f0 + p0, fe, fmod, out, ostr, pmask);
       } else {
-        flux_sweep_carry<true>(g, h, plen, eps16, tp, tm, f0 + p0, fe, out, ostr, pmask, fmod);
+        flux_sweep_rec(g, h, plen, eps16, tp, tm, f0 + p0, fe, fmod, out, ostr, pmask);
       }
     } else {
       flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
