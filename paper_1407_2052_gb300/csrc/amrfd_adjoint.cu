@@ -131,18 +131,21 @@ __device__ __forceinline__ void split_flux_adj(const double* u, double gm1, doub
 // pieces: rec = (piece of the MP5 value) | (piece of Mp) << 3 | (piece of Mm) << 6.
 // The stencil occupies positions q0..q0+4 of the line window; NEG is the mirrored
 // (right-biased) reconstruction. Accumulates d(value)/dG * gY into gG.
+// The weights of the unlimited value as register operands: 4, 6, 26, 54 (/60).
+struct FaceW {
+  double a4, a6, a26, a54;
+};
+
 template <bool NEG>
-__device__ __forceinline__ void face_adj(double* gG, int q0, double gY, unsigned rec) {
+__device__ __forceinline__ void face_adj(double* gG, int q0, double gY, unsigned rec, const FaceW& fw) {
   if ((rec & 7) == SEL_X) {
     // the unlimited value f_or (the common case): fixed weights on the five G values,
     // the differences' coefficients (-4, 22, 48, -6)/60 telescoped (mirrored for NEG)
-    constexpr double w0 = NEG ? -6.0 / 60.0 : 4.0 / 60.0, w1 = NEG ? 54.0 / 60.0 : -26.0 / 60.0;
-    constexpr double w2 = -26.0 / 60.0, w3 = NEG ? -26.0 / 60.0 : 54.0 / 60.0, w4 = NEG ? 4.0 / 60.0 : -6.0 / 60.0;
-    gG[q0] = fma(w0, gY, gG[q0]);
-    gG[q0 + 1] = fma(w1, gY, gG[q0 + 1]);
-    gG[q0 + 2] = fma(w2, gY, gG[q0 + 2]);
-    gG[q0 + 3] = fma(w3, gY, gG[q0 + 3]);
-    gG[q0 + 4] = fma(w4, gY, gG[q0 + 4]);
+    gG[q0] = fma(NEG ? -fw.a6 : fw.a4, gY, gG[q0]);
+    gG[q0 + 1] = fma(NEG ? fw.a54 : -fw.a26, gY, gG[q0 + 1]);
+    gG[q0 + 2] = fma(-fw.a26, gY, gG[q0 + 2]);
+    gG[q0 + 3] = fma(NEG ? -fw.a26 : fw.a54, gY, gG[q0 + 3]);
+    gG[q0 + 4] = fma(NEG ? fw.a4 : -fw.a6, gY, gG[q0 + 4]);
     return;
   }
   double gDm, gD0, gD1, gDp, gMp, gMm;
@@ -277,6 +280,8 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
   if (dm.bc[D][0] != 0 && kb < 0) kb = 0;
   if (dm.bc[D][1] != 0 && ke > n) ke = n;
   const long long nlines = (long long)dm.n[od1] * dm.n[od2];
+  const double one = ldk(K_ONE), half = ldk(K_HALF), mz = ldk(K_MZ);
+  const FaceW fw = {ldk(K_C4), ldk(K_C6), ldk(K_C26), ldk(K_C54)};
   for (int t = threadIdx.x; t < nl * NV; t += blockDim.x) {
     const int v = t / nl, pl = t - v * nl;
     double* ggp = gGp + (v * P + pl) * SA;
@@ -290,12 +295,12 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
     for (int k = kb; k <= ke; k++) {
       const int qk = k - (s0 - 5);        // position of cell k in the G window
       const int rk = k - (s0 - 3);        // position of cell k in the gradient window
-      const double gF = ghl[rk] - ghl[rk - 1];
+      const double gF = rsub(ghl[rk], ghl[rk - 1], one);
       if (abits(gF) == 0) continue;
       const int f = (k < 0) ? k + n : (k >= n && dm.bc[D][1] == 0 ? k - n : k);  // periodic faces wrap
-      ggp[qk - 1] += gF;
-      ggm[qk] += gF;
-      const double gY = 0.5 * gF;
+      ggp[qk - 1] = radd(ggp[qk - 1], gF, one);
+      ggm[qk] = radd(ggm[qk], gF, one);
+      const double gY = rmul(half, gF, mz);
       if (p.limo3) {
         // F = G+_{k-1} + G-_k + (Y+ - Y-)/2: Y+ of a = G+_{k-1} - G+_{k-2}, b = G+_k - G+_{k-1};
         // Y- of a = G-_{k+1} - G-_k, b = G-_k - G-_{k-1}
@@ -309,8 +314,8 @@ __device__ __forceinline__ void adj_item(const AdjFluxParams& p, const FluxItem&
         ggm[qk] += (ca - cb) * gY;
         ggm[qk - 1] += cb * gY;
       } else {
-        face_adj<false>(ggp, qk - 3, gY, tp[f]);  // + stencil: cells k-3 .. k+1, centre k-1
-        face_adj<true>(ggm, qk - 2, gY, tm[f]);   // - stencil: cells k-2 .. k+2, centre k
+        face_adj<false>(ggp, qk - 3, gY, tp[f], fw);  // + stencil: cells k-3 .. k+1, centre k-1
+        face_adj<true>(ggm, qk - 2, gY, tm[f], fw);   // - stencil: cells k-2 .. k+2, centre k
       }
     }
     // outflow: ghost copies of an edge cell fold back into it

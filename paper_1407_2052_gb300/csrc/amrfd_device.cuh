@@ -215,6 +215,43 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
   return mp_accept_slow(X, mp, eps);
 }
 
+// ------------------------------------------------ FP64 operations as register FMAs
+// GB300 issues a DFMA whose three operands are registers at 19.6 G warp instructions/s,
+// and a DADD, a DMUL or a DFMA with an immediate or constant-bank operand at 16.5 G/s
+// (independent chains on every SM, whatever the operand values). The hot loops therefore
+// form sums, differences and products as register DFMAs, bit for bit the plain
+// operations: x + y = fma(x, 1, y) and x - y = fma(x, 1, -y) (the exact sum, rounded
+// once), c x = fma(c, x, -0) (adding -0 changes no product, zeros included). The
+// constants are read from a mutable device array through an opaque load, so the
+// compiler can neither fold them back into immediates nor read them from the constant
+// bank.
+enum { K_ONE, K_MZ, K_HALF, K_C22, K_C4, K_C48, K_C6, K_ZERO, K_C26, K_C54, K_COUNT };
+static __device__ double g_regk[K_COUNT] = {1.0, -0.0, 0.5, 22.0 / 60.0, 4.0 / 60.0, 48.0 / 60.0, 6.0 / 60.0, 0.0,
+                                            26.0 / 60.0, 54.0 / 60.0};
+
+// Constant K_* as a register value (an opaque load at this point of the code).
+__device__ __forceinline__ double ldk(int i) {
+  double x;
+  asm volatile("ld.f64 %0, [%1];" : "=d"(x) : "l"(g_regk + i));
+  return x;
+}
+
+__device__ __forceinline__ double radd(double x, double y, double one) { return fma(x, one, y); }
+__device__ __forceinline__ double rsub(double x, double y, double one) { return fma(x, one, -y); }
+__device__ __forceinline__ double rmul(double c, double x, double mz) { return fma(c, x, mz); }
+
+// 2 (f_or - f_i) of MP5 from the differences: (-4 Dm + 22 D0 + 48 D1 - 6 Dp) / 60, mirrored
+// (all signs flipped) for NEG; every sweep forms it with this one operation order. The
+// weights are loaded where they are used, which keeps them out of the sweep's registers.
+template <bool NEG>
+__device__ __forceinline__ double mp5_x(double Dm, double D0, double D1, double Dp) {
+  const double mz = ldk(K_MZ), c22 = ldk(K_C22), c4 = ldk(K_C4), c48 = ldk(K_C48), c6 = ldk(K_C6);
+  const double x0 = fma(NEG ? -c22 : c22, D0, mz);
+  const double x1 = fma(NEG ? c4 : -c4, Dm, x0);
+  const double x2 = fma(NEG ? -c48 : c48, D1, x1);
+  return fma(NEG ? c6 : -c6, Dp, x2);
+}
+
 // minmod4(4 ka - kb, 4 kb - ka, ka, kb): the curvature-limited second difference at
 // a face from the curvatures of its two cells. Zero unless ka, kb share a sign; then,
 // with s the smaller and l the larger in magnitude, 4 l - s never wins and the
@@ -268,12 +305,8 @@ __device__ __forceinline__ double dm4(double ka, double kb) {
 // stencil), so both forms give the same result.
 template <bool NEG, bool CARRY>
 __device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, double Dp, double Mp, double Mm,
-                                             double eps16, bool& rej) {
-  constexpr double sg = NEG ? -1.0 : 1.0;
-  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
-                   c6 = sg * (6.0 / 60.0);
-  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));  // 2 (f_or - f_i)
-  X = fma(-c6, Dp, X);
+                                             double eps16, bool& rej, double one) {
+  const double X = mp5_x<NEG>(Dm, D0, D1, Dp);  // 2 (f_or - f_i)
   const double d0 = NEG ? dneg(D0) : D0;
   const double d1 = NEG ? dneg(D1) : D1;
   const double ul = dscale<3>(d0);     // 2 (f_ul - f_i)
@@ -284,16 +317,16 @@ __device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, do
   rej = true;
   if (!CARRY) {
     if (!NEG) {
-      const double k0 = D1 - D0;
-      Mp = dm4(k0, Dp - D1);
-      Mm = dm4(D0 - Dm, k0);
+      const double k0 = rsub(D1, D0, one);
+      Mp = dm4(k0, rsub(Dp, D1, one));
+      Mm = dm4(rsub(D0, Dm, one), k0);
     } else {
-      const double k0 = D0 - D1;
-      Mp = dm4(D1 - Dp, k0);
-      Mm = dm4(k0, Dm - D0);
+      const double k0 = rsub(D0, D1, one);
+      Mp = dm4(rsub(D1, Dp, one), k0);
+      Mm = dm4(k0, rsub(Dm, D0, one));
     }
   }
-  const double md = d1 - Mp;                  // 2 (f_md - f_i)
+  const double md = rsub(d1, Mp, one);          // 2 (f_md - f_i)
   const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
   const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
   const double fmax = imin(imax(imax(0.0, d1x2), md), imax(imax(0.0, ul), lc));
@@ -369,12 +402,9 @@ __device__ __forceinline__ void dm4_grad(int code, double g, double& gka, double
 // of Mp << 3 | piece of Mm << 6 (the curvature pieces are 0 where the value is f_or,
 // which reads neither).
 template <bool NEG>
-__device__ __forceinline__ double mp5_rel2_rec(double Dm, double D0, double D1, double Dp, double eps16, int& rec) {
-  constexpr double sg = NEG ? -1.0 : 1.0;
-  constexpr double c22 = sg * (22.0 / 60.0), c4 = sg * (4.0 / 60.0), c48 = sg * (48.0 / 60.0),
-                   c6 = sg * (6.0 / 60.0);
-  double X = fma(c48, D1, fma(-c4, Dm, c22 * D0));
-  X = fma(-c6, Dp, X);
+__device__ __forceinline__ double mp5_rel2_rec(double Dm, double D0, double D1, double Dp, double eps16, int& rec,
+                                               double one) {
+  const double X = mp5_x<NEG>(Dm, D0, D1, Dp);
   const double d0 = NEG ? dneg(D0) : D0;
   const double d1 = NEG ? dneg(D1) : D1;
   const double ul = dscale<3>(d0);
@@ -385,15 +415,15 @@ __device__ __forceinline__ double mp5_rel2_rec(double Dm, double D0, double D1, 
   double Mp, Mm;
   int cp, cm;
   if (!NEG) {
-    const double k0 = D1 - D0;
-    Mp = dm4_sel(k0, Dp - D1, cp);
-    Mm = dm4_sel(D0 - Dm, k0, cm);
+    const double k0 = rsub(D1, D0, one);
+    Mp = dm4_sel(k0, rsub(Dp, D1, one), cp);
+    Mm = dm4_sel(rsub(D0, Dm, one), k0, cm);
   } else {
-    const double k0 = D0 - D1;
-    Mp = dm4_sel(D1 - Dp, k0, cp);
-    Mm = dm4_sel(k0, Dm - D0, cm);
+    const double k0 = rsub(D0, D1, one);
+    Mp = dm4_sel(rsub(D1, Dp, one), k0, cp);
+    Mm = dm4_sel(k0, rsub(Dm, D0, one), cm);
   }
-  const double md = d1 - Mp;
+  const double md = rsub(d1, Mp, one);
   const double lc = fma(8.0 / 3.0, Mm, d0);
   double a, b, fmin, fmax, t1, t2, t3;
   int ca, cb, cmin, cmax, c1, c2, c3;
@@ -429,9 +459,10 @@ __device__ __forceinline__ double frcp(double x) {
   const long long db = ((long long)(yb & 0x80000000u) << 32) | ((long long)(((yb >> 23) & 0xff) - 127 + 1023) << 52) |
                        ((long long)(yb & 0x7fffff) << 29);
   double y = bitsd(db);
-  double r = fma(-x, y, 1.0);
+  const double one = ldk(K_ONE);
+  double r = fma(-x, y, one);
   y = fma(y, r, y);
-  r = fma(-x, y, 1.0);
+  r = fma(-x, y, one);
   return fma(y, r, y);
 }
 
@@ -592,20 +623,21 @@ struct NumW { static constexpr int value = PHYS == PH_EULER ? NV - 1 : 5; };
 template <int PHYS, int NV>
 __device__ __forceinline__ void prim_w(const double* u, double gm1, double* w) {
   const double ir = frcp(u[0]);
+  const double one = ldk(K_ONE), mz = ldk(K_MZ), half = ldk(K_HALF);
   if (PHYS == PH_EULER) {
     constexpr int nm = NV - 2;
-    double mv = 0.0;
+    double mv = ldk(K_ZERO);
 #pragma unroll
-    for (int k = 0; k < nm; k++) { w[k] = u[1 + k] * ir; mv = fma(u[1 + k], w[k], mv); }
-    w[nm] = gm1 * fma(-0.5, mv, u[NV - 1]);
+    for (int k = 0; k < nm; k++) { w[k] = rmul(u[1 + k], ir, mz); mv = fma(u[1 + k], w[k], mv); }
+    w[nm] = gm1 * fma(-half, mv, u[NV - 1]);
   } else {
-    const double v[3] = {u[1] * ir, u[2] * ir, u[3] * ir};
-    const double b2 = fma(u[7], u[7], fma(u[6], u[6], u[5] * u[5]));
-    const double mv = fma(u[3], v[2], fma(u[2], v[1], u[1] * v[0]));
-    const double p = gm1 * fma(-0.5, mv + b2, u[4]);
+    const double v[3] = {rmul(u[1], ir, mz), rmul(u[2], ir, mz), rmul(u[3], ir, mz)};
+    const double b2 = fma(u[7], u[7], fma(u[6], u[6], rmul(u[5], u[5], mz)));
+    const double mv = fma(u[3], v[2], fma(u[2], v[1], rmul(u[1], v[0], mz)));
+    const double p = gm1 * fma(-half, radd(mv, b2, one), u[4]);
     w[0] = v[0]; w[1] = v[1]; w[2] = v[2];
-    w[3] = fma(0.5, b2, p);
-    w[4] = fma(v[2], u[7], fma(v[1], u[6], v[0] * u[5]));
+    w[3] = fma(half, b2, p);
+    w[4] = fma(v[2], u[7], fma(v[1], u[6], rmul(v[0], u[5], mz)));
   }
 }
 
@@ -615,25 +647,26 @@ template <int PHYS, int NV, int D>
 __device__ __forceinline__ void split_flux_w(const double* u, const double* w, double alpha, double ch2,
                                              double* gp, double* gm) {
   double f[NV];
+  const double one = ldk(K_ONE), mz = ldk(K_MZ);
   if (PHYS == PH_EULER) {
     constexpr int nm = NV - 2;
     const double p = w[nm], vd = w[D];
     f[0] = u[1 + D];
 #pragma unroll
-    for (int k = 0; k < nm; k++) f[1 + k] = (k == D) ? fma(vd, u[1 + k], p) : vd * u[1 + k];
-    f[NV - 1] = vd * (u[NV - 1] + p);
+    for (int k = 0; k < nm; k++) f[1 + k] = (k == D) ? fma(vd, u[1 + k], p) : rmul(vd, u[1 + k], mz);
+    f[NV - 1] = rmul(vd, radd(u[NV - 1], p, one), mz);
   } else {
     const double ptot = w[3], vb = w[4];
     const double vd = w[D], bd = u[5 + D];
     f[0] = u[1 + D];
 #pragma unroll
     for (int k = 0; k < 3; k++) {
-      f[1 + k] = fma(vd, u[1 + k], -bd * u[5 + k]);
-      if (k == D) f[1 + k] += ptot;
-      f[5 + k] = (k == D) ? u[8] : fma(vd, u[5 + k], -bd * w[k]);
+      f[1 + k] = fma(vd, u[1 + k], rmul(-bd, u[5 + k], mz));
+      if (k == D) f[1 + k] = radd(f[1 + k], ptot, one);
+      f[5 + k] = (k == D) ? u[8] : fma(vd, u[5 + k], rmul(-bd, w[k], mz));
     }
-    f[4] = fma(vd, u[4] + ptot, -bd * vb);
-    f[8] = ch2 * bd;
+    f[4] = fma(vd, radd(u[4], ptot, one), rmul(-bd, vb, mz));
+    f[8] = rmul(ch2, bd, mz);
   }
 #pragma unroll
   for (int v = 0; v < NV; v++) {

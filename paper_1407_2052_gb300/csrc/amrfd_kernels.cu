@@ -285,29 +285,31 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 // index f0 + k - 3 if below fend (face n of a periodic line, fmod = n, as face 0).
 __device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h, int slen, double eps16,
                                                unsigned short* tp, unsigned short* tm, int f0, int fend, int fmod,
-                                               double* out, long long ostr, unsigned long long wmask) {
-  double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
-  double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
+                                               double* out, long long ostr, unsigned long long wmask, double one) {
+  double Pd1 = rsub(g[1], g[0], one), Pd2 = rsub(g[2], g[1], one), Pd3 = rsub(g[3], g[2], one),
+         Pd4 = rsub(g[4], g[3], one);
+  double Md2 = rsub(h[2], h[1], one), Md3 = rsub(h[3], h[2], one), Md4 = rsub(h[4], h[3], one),
+         Md5 = rsub(h[5], h[4], one);
   double cp = g[2], cm = h[3];
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     int yp, ym;
-    const double Yp = mp5_rel2_rec<false>(Pd1, Pd2, Pd3, Pd4, eps16, yp);
-    const double Ym = mp5_rel2_rec<true>(Md5, Md4, Md3, Md2, eps16, ym);
+    const double Yp = mp5_rel2_rec<false>(Pd1, Pd2, Pd3, Pd4, eps16, yp, one);
+    const double Ym = mp5_rel2_rec<true>(Md5, Md4, Md3, Md2, eps16, ym, one);
     const int f = f0 + k - 3;
     if (f < fend) {
       const int fi = f >= fmod ? f - fmod : f;
       tp[fi] = (unsigned short)yp;
       tm[fi] = (unsigned short)ym;
     }
-    const double F = fma(0.5, Yp + Ym, cp + cm);
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    const double F = fma(ldk(K_HALF), radd(Yp, Ym, one), radd(cp, cm, one));
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
     Fprev = F;
     if (k < kend) {
-      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(g[k + 2], g[k + 1], one);
       cp = g[k];
-      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(h[k + 3], h[k + 2], one);
       cm = h[k + 1];
     }
   }
@@ -322,9 +324,11 @@ __device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h,
 // Every lane in `lanes` must call this with the same slen (the face votes pair up).
 __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const double* h, int slen, double eps16,
                                                     double* out, long long ostr, unsigned long long wmask,
-                                                    unsigned lanes) {
-  double Pd1 = g[1] - g[0], Pd2 = g[2] - g[1], Pd3 = g[3] - g[2], Pd4 = g[4] - g[3];
-  double Md2 = h[2] - h[1], Md3 = h[3] - h[2], Md4 = h[4] - h[3], Md5 = h[5] - h[4];
+                                                    unsigned lanes, double one) {
+  double Pd1 = rsub(g[1], g[0], one), Pd2 = rsub(g[2], g[1], one), Pd3 = rsub(g[3], g[2], one),
+         Pd4 = rsub(g[4], g[3], one);
+  double Md2 = rsub(h[2], h[1], one), Md3 = rsub(h[3], h[2], one), Md4 = rsub(h[4], h[3], one),
+         Md5 = rsub(h[5], h[4], one);
   double Pk3 = 0.0, Mk4 = 0.0, PM2 = 0.0, PM3 = 0.0, MM3 = 0.0, MM4 = 0.0;
   bool carry = false;
   double cp = g[2], cm = h[3];
@@ -336,37 +340,37 @@ __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const doubl
     double Yp, Ym;
     bool rp, rm;
     if (carry) {
-      Yp = mp5_rel2_r<false, true>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16, rp);
-      Ym = mp5_rel2_r<true, true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, rm);
+      Yp = mp5_rel2_r<false, true>(Pd1, Pd2, Pd3, Pd4, PM3, PM2, eps16, rp, one);
+      Ym = mp5_rel2_r<true, true>(Md5, Md4, Md3, Md2, MM3, MM4, eps16, rm, one);
     } else {
-      Yp = mp5_rel2_r<false, false>(Pd1, Pd2, Pd3, Pd4, 0.0, 0.0, eps16, rp);
-      Ym = mp5_rel2_r<true, false>(Md5, Md4, Md3, Md2, 0.0, 0.0, eps16, rm);
+      Yp = mp5_rel2_r<false, false>(Pd1, Pd2, Pd3, Pd4, 0.0, 0.0, eps16, rp, one);
+      Ym = mp5_rel2_r<true, false>(Md5, Md4, Md3, Md2, 0.0, 0.0, eps16, rm, one);
     }
-    const double F = fma(0.5, Yp + Ym, cp + cm);
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    const double F = fma(ldk(K_HALF), radd(Yp, Ym, one), radd(cp, cm, one));
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
     Fprev = F;
     if (k < kend) {
       const bool want = __any_sync(lanes, rp || rm);
-      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = g[k + 2] - g[k + 1];
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(g[k + 2], g[k + 1], one);
       cp = g[k];
-      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = h[k + 3] - h[k + 2];
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(h[k + 3], h[k + 2], one);
       cm = h[k + 1];
       if (want && carry) {
-        const double pk = Pd4 - Pd3;
+        const double pk = rsub(Pd4, Pd3, one);
         PM2 = PM3;
         PM3 = dm4(Pk3, pk);
         Pk3 = pk;
-        const double mk = Md5 - Md4;
+        const double mk = rsub(Md5, Md4, one);
         MM3 = MM4;
         MM4 = dm4(Mk4, mk);
         Mk4 = mk;
       } else if (want) {
-        const double Pk2 = Pd3 - Pd2, Mk3 = Md4 - Md3;
-        Pk3 = Pd4 - Pd3;
-        Mk4 = Md5 - Md4;
-        PM2 = dm4(Pd2 - Pd1, Pk2);
+        const double Pk2 = rsub(Pd3, Pd2, one), Mk3 = rsub(Md4, Md3, one);
+        Pk3 = rsub(Pd4, Pd3, one);
+        Mk4 = rsub(Md5, Md4, one);
+        PM2 = dm4(rsub(Pd2, Pd1, one), Pk2);
         PM3 = dm4(Pk2, Pk3);
-        MM3 = dm4(Md3 - Md2, Mk3);
+        MM3 = dm4(rsub(Md3, Md2, one), Mk3);
         MM4 = dm4(Mk3, Mk4);
       }
       carry = want;
@@ -568,6 +572,7 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   double* Ld = p.L[D] + dm.off;
   const int total = nl * NV * np;
   const int lane = threadIdx.x & 31;
+  const double one = ldk(K_ONE);
   for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
     const int t = t0 + lane;
     const bool valid = t < total;
@@ -606,10 +611,10 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
         const double rdx = p.limo3_r * dm.dx[D];
         limo3_sweep_rec(g, h, plen, 0.25 / (rdx * rdx), tp, tm, f0 + p0, fe, fmod, out, ostr, pmask);
       } else {
-        flux_sweep_rec(g, h, plen, eps16, tp, tm, f0 + p0, fe, fmod, out, ostr, pmask);
+        flux_sweep_rec(g, h, plen, eps16, tp, tm, f0 + p0, fe, fmod, out, ostr, pmask, one);
       }
     } else {
-      flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm);
+      flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm, one);
     }
   }
 }
