@@ -225,9 +225,9 @@ __device__ __forceinline__ bool mp_accept(double X, double mp, double eps) {
 // constants are read from a mutable device array through an opaque load, so the
 // compiler can neither fold them back into immediates nor read them from the constant
 // bank.
-enum { K_ONE, K_MZ, K_HALF, K_C22, K_C4, K_C48, K_C6, K_ZERO, K_C26, K_C54, K_COUNT };
+enum { K_ONE, K_MZ, K_HALF, K_C22, K_C4, K_C48, K_C6, K_ZERO, K_C26, K_C54, K_C83, K_TWO, K_THIRD, K_C16, K_COUNT };
 static __device__ double g_regk[K_COUNT] = {1.0, -0.0, 0.5, 22.0 / 60.0, 4.0 / 60.0, 48.0 / 60.0, 6.0 / 60.0, 0.0,
-                                            26.0 / 60.0, 54.0 / 60.0};
+                                            26.0 / 60.0, 54.0 / 60.0, 8.0 / 3.0, 2.0, 1.0 / 3.0, 1.6};
 
 // Constant K_* as a register value (an opaque load at this point of the code).
 __device__ __forceinline__ double ldk(int i) {
@@ -327,7 +327,7 @@ __device__ __forceinline__ double mp5_rel2_r(double Dm, double D0, double D1, do
     }
   }
   const double md = rsub(d1, Mp, one);          // 2 (f_md - f_i)
-  const double lc = fma(8.0 / 3.0, Mm, d0);   // 2 (f_lc - f_i)
+  const double lc = fma(ldk(K_C83), Mm, d0);    // 2 (f_lc - f_i)
   const double fmin = imax(imin(imin(0.0, d1x2), md), imin(imin(0.0, ul), lc));
   const double fmax = imin(imax(imax(0.0, d1x2), md), imax(imax(0.0, ul), lc));
   return imedian(X, fmin, fmax);
@@ -424,7 +424,7 @@ __device__ __forceinline__ double mp5_rel2_rec(double Dm, double D0, double D1, 
     Mm = dm4_sel(k0, rsub(Dm, D0, one), cm);
   }
   const double md = rsub(d1, Mp, one);
-  const double lc = fma(8.0 / 3.0, Mm, d0);
+  const double lc = fma(ldk(K_C83), Mm, d0);
   double a, b, fmin, fmax, t1, t2, t3;
   int ca, cb, cmin, cmax, c1, c2, c3;
   imin_sel(0.0, SEL_ZERO, d1x2, SEL_D1, a, ca);

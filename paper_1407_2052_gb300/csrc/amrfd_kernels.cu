@@ -387,15 +387,16 @@ __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const doubl
 // switch eta = (a^2 + b^2) / (4 (r dx)^2) (G = 2 F^{+-}) picks the unlimited value
 // inside the asymptotic region, the limited one outside, and blends linearly over
 // |eta - 1| < 1e-12.
-__device__ __forceinline__ double limo3_y(double a, double b, double s2, long long tlo, long long thi, double esc) {
-  const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
+__device__ __forceinline__ double limo3_y(double a, double b, double s2, long long tlo, long long thi, double esc,
+                                          double mz) {
+  const double y3 = rmul(fma(ldk(K_TWO), b, a), ldk(K_THIRD), mz);
   const long long bs = abits(s2);  // s2 = a^2 + b^2 >= 0: its bit pattern orders like its value
   if (bs <= tlo) return y3;
   const bool neg = sbit(b) != 0;
   const double ap = neg ? dneg(a) : a;
   const double y3p = neg ? dneg(y3) : y3;
   const double bp = neg ? dneg(b) : b;
-  double t = imin(imin(dscale<1>(ap), y3p), 1.6 * bp);
+  double t = imin(imin(dscale<1>(ap), y3p), rmul(ldk(K_C16), bp, mz));
   t = imax(dscale<-1>(dneg(ap)), t);
   t = imin(y3p, t);
   t = imax(0.0, t);
@@ -410,8 +411,8 @@ __device__ __forceinline__ double limo3_y(double a, double b, double s2, long lo
 // function of the unsigned a, b), bits 3-4 the mode (0 unlimited, 1 limited, 2 / 3 inside
 // the blend band on its unlimited / limited half).
 __device__ __forceinline__ double limo3_y_sel(double a, double b, double s2, long long tlo, long long thi,
-                                              double esc, int& code) {
-  const double y3 = fma(2.0, b, a) * (1.0 / 3.0);
+                                              double esc, int& code, double mz) {
+  const double y3 = rmul(fma(ldk(K_TWO), b, a), ldk(K_THIRD), mz);
   const long long bs = abits(s2);
   if (bs <= tlo) { code = 0; return y3; }
   const bool neg = sbit(b) != 0;
@@ -421,7 +422,7 @@ __device__ __forceinline__ double limo3_y_sel(double a, double b, double s2, lon
   double t;
   int c;
   imin_sel(dscale<1>(ap), 3, y3p, 1, t, c);
-  imin_sel(t, c, 1.6 * bp, 4, t, c);
+  imin_sel(t, c, rmul(ldk(K_C16), bp, mz), 4, t, c);
   imax_sel(dscale<-1>(dneg(ap)), 2, t, c, t, c);
   imin_sel(y3p, 1, t, c, t, c);
   imax_sel(0.0, 0, t, c, t, c);
@@ -439,20 +440,21 @@ __device__ __forceinline__ double limo3_y_sel(double a, double b, double s2, lon
 __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, int slen, double esc, double* out,
                                             long long ostr, unsigned long long wmask) {
   const long long tlo = __double_as_longlong((1.0 - 1e-12) / esc), thi = __double_as_longlong((1.0 + 1e-12) / esc);
-  double Pa = g[2] - g[1], Pb = g[3] - g[2];   // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
-  double Mb = h[3] - h[2], Ma = h[4] - h[3];   // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
-  double Pa2 = Pa * Pa, Pb2 = Pb * Pb, Ma2 = Ma * Ma, Mb2 = Mb * Mb;
+  const double one = ldk(K_ONE), mz = ldk(K_MZ);
+  double Pa = rsub(g[2], g[1], one), Pb = rsub(g[3], g[2], one);  // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
+  double Mb = rsub(h[3], h[2], one), Ma = rsub(h[4], h[3], one);  // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
+  double Pa2 = rmul(Pa, Pa, mz), Pb2 = rmul(Pb, Pb, mz), Ma2 = rmul(Ma, Ma, mz), Mb2 = rmul(Mb, Mb, mz);
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
-    const double Yp = limo3_y(Pa, Pb, Pa2 + Pb2, tlo, thi, esc);
-    const double Ym = limo3_y(Ma, Mb, Ma2 + Mb2, tlo, thi, esc);
-    const double F = fma(0.5, Yp - Ym, g[k - 1] + h[k]);
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    const double Yp = limo3_y(Pa, Pb, radd(Pa2, Pb2, one), tlo, thi, esc, mz);
+    const double Ym = limo3_y(Ma, Mb, radd(Ma2, Mb2, one), tlo, thi, esc, mz);
+    const double F = fma(ldk(K_HALF), rsub(Yp, Ym, one), radd(g[k - 1], h[k], one));
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
     Fprev = F;
     if (k < kend) {
-      Pa = Pb; Pa2 = Pb2; Pb = g[k + 1] - g[k]; Pb2 = Pb * Pb;
-      Mb = Ma; Mb2 = Ma2; Ma = h[k + 2] - h[k + 1]; Ma2 = Ma * Ma;
+      Pa = Pb; Pa2 = Pb2; Pb = rsub(g[k + 1], g[k], one); Pb2 = rmul(Pb, Pb, mz);
+      Mb = Ma; Mb2 = Ma2; Ma = rsub(h[k + 2], h[k + 1], one); Ma2 = rmul(Ma, Ma, mz);
     }
   }
 }
@@ -463,27 +465,28 @@ __device__ __forceinline__ void limo3_sweep_rec(const double* g, const double* h
                                                 unsigned short* tp, unsigned short* tm, int f0, int fend, int fmod,
                                                 double* out, long long ostr, unsigned long long wmask) {
   const long long tlo = __double_as_longlong((1.0 - 1e-12) / esc), thi = __double_as_longlong((1.0 + 1e-12) / esc);
-  double Pa = g[2] - g[1], Pb = g[3] - g[2];
-  double Mb = h[3] - h[2], Ma = h[4] - h[3];
-  double Pa2 = Pa * Pa, Pb2 = Pb * Pb, Ma2 = Ma * Ma, Mb2 = Mb * Mb;
+  const double one = ldk(K_ONE), mz = ldk(K_MZ);
+  double Pa = rsub(g[2], g[1], one), Pb = rsub(g[3], g[2], one);
+  double Mb = rsub(h[3], h[2], one), Ma = rsub(h[4], h[3], one);
+  double Pa2 = rmul(Pa, Pa, mz), Pb2 = rmul(Pb, Pb, mz), Ma2 = rmul(Ma, Ma, mz), Mb2 = rmul(Mb, Mb, mz);
   double Fprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     int cp, cm;
-    const double Yp = limo3_y_sel(Pa, Pb, Pa2 + Pb2, tlo, thi, esc, cp);
-    const double Ym = limo3_y_sel(Ma, Mb, Ma2 + Mb2, tlo, thi, esc, cm);
+    const double Yp = limo3_y_sel(Pa, Pb, radd(Pa2, Pb2, one), tlo, thi, esc, cp, mz);
+    const double Ym = limo3_y_sel(Ma, Mb, radd(Ma2, Mb2, one), tlo, thi, esc, cm, mz);
     const int f = f0 + k - 3;
     if (f < fend) {
       const int fi = f >= fmod ? f - fmod : f;  // face n of a periodic line is face 0
       tp[fi] = (unsigned short)cp;
       tm[fi] = (unsigned short)cm;
     }
-    const double F = fma(0.5, Yp - Ym, g[k - 1] + h[k]);
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = Fprev - F;
+    const double F = fma(ldk(K_HALF), rsub(Yp, Ym, one), radd(g[k - 1], h[k], one));
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
     Fprev = F;
     if (k < kend) {
-      Pa = Pb; Pa2 = Pb2; Pb = g[k + 1] - g[k]; Pb2 = Pb * Pb;
-      Mb = Ma; Mb2 = Ma2; Ma = h[k + 2] - h[k + 1]; Ma2 = Ma * Ma;
+      Pa = Pb; Pa2 = Pb2; Pb = rsub(g[k + 1], g[k], one); Pb2 = rmul(Pb, Pb, mz);
+      Mb = Ma; Mb2 = Ma2; Ma = rsub(h[k + 2], h[k + 1], one); Ma2 = rmul(Ma, Ma, mz);
     }
   }
 }
