@@ -34,7 +34,9 @@ BYTES_PER_CELL_UPDATE = 64 * NV
 # derived quantities per cell (40 B), traffic spent to save FP64 work.
 FLUX_BYTES_PER_CELL = 4 * NV * 8
 # FP64 work of the flux pass per cell and direction (flop = DADD + DMUL + 2 DFMA thread
-# instructions, counted by ncu on the 128^3 blast's first step; 32 lines per tile):
+# instructions, counted by ncu on the 128^3 blast's first step, 32 lines per tile, with a
+# build whose sums and products were still DADD and DMUL; the kernels now issue them as
+# FMAs by 1 and with -0, the same instruction count, which 2 x DFMA no longer reads as flop):
 # 291.96 at 16-cell segments, 273.17 at 32-cell segments. A segment of S cells computes
 # the split flux of its S + 6 cells and starts its sweeps afresh, so the count is
 # a + b/S; the method's own work (one split flux per cell, one reconstruction per face,
@@ -57,7 +59,7 @@ FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64, nominal (context only)
 # DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write of the 128^3 blast's
 # first flux pass, tile 64 x 8 lines x 288 threads, scaled by cells): traffic grows with
 # the cells processed
-FLUX_TRAFFIC_BYTES_PER_CELL = (440.548864 + 411.594496) * 1e6 / 128 ** 3
+FLUX_TRAFFIC_BYTES_PER_CELL = (441.519104 + 415.088384) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):
