@@ -279,7 +279,11 @@ __device__ __forceinline__ void flux_phase_a(const FluxParams& p, const DomDev& 
 // Recording sweep of one (line, variable): MP5 on both biases at faces k = 3..slen+3 of
 // the line's extended index (cell j = k-1 left of face k), then the flux difference
 // Fsum_{k-1} - Fsum_k of the segment's cell k-4 stored to out[(k-4) ostr] where wmask has
-// its bit (the factor 1/(2 dx) is applied by the stage combination). Per face and bias it
+// its bit (the factor 1/(2 dx) is applied by the stage combination). With
+// Fsum_k = G+_{k-1} + G-_k + (Y+_k + Y-_k)/2, the difference is formed from what the sweep
+// holds, (S_{k-1} - S_k)/2 - (G+_{k-1} - G+_{k-2}) - (G-_k - G-_{k-1}) with S = Y+ + Y-: no
+// subtraction of two fluxes of the size of G, and two shared-memory reads per face (each
+// array's newest value; the previous one is kept in a register). Per face and bias it
 // records which linear piece the limiter took and the pieces of the two curvature limiters
 // it read (mp5_rel2_rec, 3 bits each): tp/tm point at the line's records, face k goes to
 // index f0 + k - 3 if below fend (face n of a periodic line, fmod = n, as face 0).
@@ -290,8 +294,8 @@ __device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h,
          Pd4 = rsub(g[4], g[3], one);
   double Md2 = rsub(h[2], h[1], one), Md3 = rsub(h[3], h[2], one), Md4 = rsub(h[4], h[3], one),
          Md5 = rsub(h[5], h[4], one);
-  double cp = g[2], cm = h[3];
-  double Fprev = 0.0;
+  double gl = g[4], hl = h[5];  // the last values read, g[k+1] and h[k+2]
+  double Sprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     int yp, ym;
@@ -303,14 +307,14 @@ __device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h,
       tp[fi] = (unsigned short)yp;
       tm[fi] = (unsigned short)ym;
     }
-    const double F = fma(ldk(K_HALF), radd(Yp, Ym, one), radd(cp, cm, one));
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
-    Fprev = F;
+    const double S = radd(Yp, Ym, one);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull))
+      out[(long long)(k - 4) * ostr] = fma(ldk(K_HALF), rsub(Sprev, S, one), -radd(Pd2, Md3, one));
+    Sprev = S;
     if (k < kend) {
-      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(g[k + 2], g[k + 1], one);
-      cp = g[k];
-      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(h[k + 3], h[k + 2], one);
-      cm = h[k + 1];
+      const double gn = g[k + 2], hn = h[k + 3];
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(gn, gl, one); gl = gn;
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(hn, hl, one); hl = hn;
     }
   }
 }
@@ -331,8 +335,8 @@ __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const doubl
          Md5 = rsub(h[5], h[4], one);
   double Pk3 = 0.0, Mk4 = 0.0, PM2 = 0.0, PM3 = 0.0, MM3 = 0.0, MM4 = 0.0;
   bool carry = false;
-  double cp = g[2], cm = h[3];
-  double Fprev = 0.0;
+  double gl = g[4], hl = h[5];  // the last values read, g[k+1] and h[k+2]
+  double Sprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     // left-biased reconstruction of G^+ centred on cell k-1, right-biased of G^-
@@ -346,15 +350,15 @@ __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const doubl
       Yp = mp5_rel2_r<false, false>(Pd1, Pd2, Pd3, Pd4, 0.0, 0.0, eps16, rp, one);
       Ym = mp5_rel2_r<true, false>(Md5, Md4, Md3, Md2, 0.0, 0.0, eps16, rm, one);
     }
-    const double F = fma(ldk(K_HALF), radd(Yp, Ym, one), radd(cp, cm, one));
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
-    Fprev = F;
+    const double S = radd(Yp, Ym, one);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull))
+      out[(long long)(k - 4) * ostr] = fma(ldk(K_HALF), rsub(Sprev, S, one), -radd(Pd2, Md3, one));
+    Sprev = S;
     if (k < kend) {
       const bool want = __any_sync(lanes, rp || rm);
-      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(g[k + 2], g[k + 1], one);
-      cp = g[k];
-      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(h[k + 3], h[k + 2], one);
-      cm = h[k + 1];
+      const double gn = g[k + 2], hn = h[k + 3];
+      Pd1 = Pd2; Pd2 = Pd3; Pd3 = Pd4; Pd4 = rsub(gn, gl, one); gl = gn;
+      Md2 = Md3; Md3 = Md4; Md4 = Md5; Md5 = rsub(hn, hl, one); hl = hn;
       if (want && carry) {
         const double pk = rsub(Pd4, Pd3, one);
         PM2 = PM3;
@@ -444,17 +448,20 @@ __device__ __forceinline__ void limo3_sweep(const double* g, const double* h, in
   double Pa = rsub(g[2], g[1], one), Pb = rsub(g[3], g[2], one);  // delta_{i-1/2}, delta_{i+1/2} of G^+ at face 3
   double Mb = rsub(h[3], h[2], one), Ma = rsub(h[4], h[3], one);  // mirrored: -delta_{i+1/2}, -delta_{i-1/2} of G^-
   double Pa2 = rmul(Pa, Pa, mz), Pb2 = rmul(Pb, Pb, mz), Ma2 = rmul(Ma, Ma, mz), Mb2 = rmul(Mb, Mb, mz);
-  double Fprev = 0.0;
+  double gl = g[3], hl = h[4];  // the last values read, g[k] and h[k+1]
+  double Sprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     const double Yp = limo3_y(Pa, Pb, radd(Pa2, Pb2, one), tlo, thi, esc, mz);
     const double Ym = limo3_y(Ma, Mb, radd(Ma2, Mb2, one), tlo, thi, esc, mz);
-    const double F = fma(ldk(K_HALF), rsub(Yp, Ym, one), radd(g[k - 1], h[k], one));
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
-    Fprev = F;
+    const double S = rsub(Yp, Ym, one);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull))
+      out[(long long)(k - 4) * ostr] = fma(ldk(K_HALF), rsub(Sprev, S, one), -radd(Pa, Mb, one));
+    Sprev = S;
     if (k < kend) {
-      Pa = Pb; Pa2 = Pb2; Pb = rsub(g[k + 1], g[k], one); Pb2 = rmul(Pb, Pb, mz);
-      Mb = Ma; Mb2 = Ma2; Ma = rsub(h[k + 2], h[k + 1], one); Ma2 = rmul(Ma, Ma, mz);
+      const double gn = g[k + 1], hn = h[k + 2];
+      Pa = Pb; Pa2 = Pb2; Pb = rsub(gn, gl, one); Pb2 = rmul(Pb, Pb, mz); gl = gn;
+      Mb = Ma; Mb2 = Ma2; Ma = rsub(hn, hl, one); Ma2 = rmul(Ma, Ma, mz); hl = hn;
     }
   }
 }
@@ -469,7 +476,8 @@ __device__ __forceinline__ void limo3_sweep_rec(const double* g, const double* h
   double Pa = rsub(g[2], g[1], one), Pb = rsub(g[3], g[2], one);
   double Mb = rsub(h[3], h[2], one), Ma = rsub(h[4], h[3], one);
   double Pa2 = rmul(Pa, Pa, mz), Pb2 = rmul(Pb, Pb, mz), Ma2 = rmul(Ma, Ma, mz), Mb2 = rmul(Mb, Mb, mz);
-  double Fprev = 0.0;
+  double gl = g[3], hl = h[4];  // the last values read, g[k] and h[k+1]
+  double Sprev = 0.0;
   const int kend = slen + 3;
   for (int k = 3; k <= kend; ++k) {
     int cp, cm;
@@ -481,12 +489,14 @@ __device__ __forceinline__ void limo3_sweep_rec(const double* g, const double* h
       tp[fi] = (unsigned short)cp;
       tm[fi] = (unsigned short)cm;
     }
-    const double F = fma(ldk(K_HALF), rsub(Yp, Ym, one), radd(g[k - 1], h[k], one));
-    if (k > 3 && ((wmask >> (k - 4)) & 1ull)) out[(long long)(k - 4) * ostr] = rsub(Fprev, F, one);
-    Fprev = F;
+    const double S = rsub(Yp, Ym, one);
+    if (k > 3 && ((wmask >> (k - 4)) & 1ull))
+      out[(long long)(k - 4) * ostr] = fma(ldk(K_HALF), rsub(Sprev, S, one), -radd(Pa, Mb, one));
+    Sprev = S;
     if (k < kend) {
-      Pa = Pb; Pa2 = Pb2; Pb = rsub(g[k + 1], g[k], one); Pb2 = rmul(Pb, Pb, mz);
-      Mb = Ma; Mb2 = Ma2; Ma = rsub(h[k + 2], h[k + 1], one); Ma2 = rmul(Ma, Ma, mz);
+      const double gn = g[k + 1], hn = h[k + 2];
+      Pa = Pb; Pa2 = Pb2; Pb = rsub(gn, gl, one); Pb2 = rmul(Pb, Pb, mz); gl = gn;
+      Mb = Ma; Mb2 = Ma2; Ma = rsub(hn, hl, one); Ma2 = rmul(Ma, Ma, mz); hl = hn;
     }
   }
 }
