@@ -201,7 +201,7 @@ int amrfd_autotune(amrfd_handle *h, double *U, const double *dt_dev, void *strea
 
 /* Set the flux-pass tile explicitly: seg = max cells per sweep segment
    (8..64), lines = lines per tile (1..32), threads per block (multiple of 32,
-   32..288). Every tile gives bitwise the same results. */
+   32..320). Every tile gives bitwise the same results. */
 int amrfd_set_tile(amrfd_handle *h, int seg, int lines, int threads);
 /* Read back the current tile. */
 int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);

@@ -304,9 +304,14 @@ int configure_tile(amrfd_handle* h, int seg, int lines, int threads) {
 
 // Threads of a flux CTA: one per (sweep part, line, variable) of a full tile; a segment
 // of 32 cells or more is swept in parts of at least 16 cells (sweep_parts in the kernels).
-int default_threads(int nv, int lines, int seg) {
+// One thread per (variable, line, part) sweep; with MP5, when a variable's sweeps fill
+// whole warps in parts of 16 cells or more, also the threads that sweep the costliest
+// variable in twice as many parts (flux_phase_b).
+int default_threads(int nv, int lines, int seg, bool mp5) {
   const int parts = seg >= 32 ? seg / 16 : 1;
-  int t = ((nv * lines * parts + 31) / 32) * 32;
+  int tasks = nv * lines * parts;
+  if (mp5 && seg >= 32 && (lines * parts) % 32 == 0) tasks += lines * parts;
+  int t = ((tasks + 31) / 32) * 32;
   return std::max(64, std::min(t, kFluxMaxThreads));
 }
 
@@ -674,7 +679,7 @@ int amrfd_create(amrfd_handle** out, const amrfd_config* cfg, const amrfd_domain
   CKH(cudaMalloc(&h->d_W, sizeof(double) * std::max<size_t>(1, h->nw_elem)));
   CKH(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   const int lines = cfg->ndim == 1 ? 1 : 32;
-  rc = configure_tile(h, 32, lines, default_threads(h->nv, lines, 32));
+  rc = configure_tile(h, 32, lines, default_threads(h->nv, lines, 32, h->cfg.recon == AMRFD_MP5));
   if (rc) return fail(rc);
   rc = compact(h, s);
   if (rc) return fail(rc);
@@ -1117,8 +1122,9 @@ int amrfd_autotune(amrfd_handle* h, double* U, const double* dt_dev, void* strea
     for (int ln : lines_c) {
       if (h->cfg.ndim == 1 && ln != 1) continue;
       for (int mul = 1; mul <= 2; mul++) {
-        const int thr = std::min(kFluxMaxThreads, default_threads(h->nv, ln, sg) * mul);
-        if (mul == 2 && thr == default_threads(h->nv, ln, sg)) continue;
+        const int def = default_threads(h->nv, ln, sg, h->cfg.recon == AMRFD_MP5);
+        const int thr = std::min(kFluxMaxThreads, def * mul);
+        if (mul == 2 && thr == def) continue;
         if (configure_tile(h, sg, h->cfg.ndim == 1 ? 1 : ln, thr)) continue;
         if (compact(h, s)) continue;
         FluxParams fp = flux_params(h, U, U, 0);

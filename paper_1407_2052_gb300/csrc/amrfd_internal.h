@@ -5,9 +5,10 @@
 namespace amrfd {
 
 constexpr int kGhost = 3;       // MP5 needs cells i-2..i+3 around face i+1/2
-// Threads of a flux CTA at most: one per (line, variable) sweep of a 32-line MHD tile.
-// Two CTAs per SM then leave up to 113 registers per thread for the sweep.
-constexpr int kFluxMaxThreads = 288;
+// Threads of a flux CTA at most: one per (line, variable, part) sweep of an MHD tile of
+// 32 sweeps per variable, plus one warp for the split of the costliest variable. Two
+// CTAs per SM then leave up to 102 registers per thread.
+constexpr int kFluxMaxThreads = 320;
 constexpr int kMaxStages = 5;
 constexpr int kSlotDt = 5;      // speed slot used by amrfd_dt (slots 0..4: RK stage inputs)
 constexpr int kNumSlots = 6;

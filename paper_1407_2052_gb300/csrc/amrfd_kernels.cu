@@ -326,9 +326,12 @@ __device__ __forceinline__ void flux_sweep_rec(const double* g, const double* h,
 // the carried ones) and carries them; after a face where none did, it drops them and
 // forms them per face at failing faces only (mp5_rel2_r without CARRY).
 // Every lane in `lanes` must call this with the same slen (the face votes pair up).
-__device__ __forceinline__ void flux_sweep_adaptive(const double* g, const double* h, int slen, double eps16,
-                                                    double* out, long long ostr, unsigned long long wmask,
-                                                    unsigned lanes, double one) {
+// Returns the number of faces after which some lane had failed (the same in every lane):
+// the warp's limiter work, which phase B uses to balance the variables' sweeps.
+__device__ __forceinline__ int flux_sweep_adaptive(const double* g, const double* h, int slen, double eps16,
+                                                   double* out, long long ostr, unsigned long long wmask,
+                                                   unsigned lanes, double one) {
+  int busy = 0;
   double Pd1 = rsub(g[1], g[0], one), Pd2 = rsub(g[2], g[1], one), Pd3 = rsub(g[3], g[2], one),
          Pd4 = rsub(g[4], g[3], one);
   double Md2 = rsub(h[2], h[1], one), Md3 = rsub(h[3], h[2], one), Md4 = rsub(h[4], h[3], one),
@@ -378,8 +381,10 @@ __device__ __forceinline__ void flux_sweep_adaptive(const double* g, const doubl
         MM4 = dm4(Mk3, Mk4);
       }
       carry = want;
+      busy += want;
     }
   }
+  return busy;
 }
 
 // LIMO3 (Cada & Torrilhon 2009) in product form: with a = delta_{i-1/2} and
@@ -543,14 +548,39 @@ __device__ __forceinline__ int sweep_parts(int slen) {
   return np > 1 ? np : 1;
 }
 
+// The variable whose MP5 sweeps cost clearly most, from the CTA's decaying per-variable
+// counts of limiter faces (cost[v]), or -1: its count must exceed the runner-up's by an
+// eighth (and a few faces).
+template <int NV>
+__device__ __forceinline__ int hot_variable(const unsigned* cost) {
+  int h = -1;
+  unsigned m1 = 0u, m2 = 0u;
+#pragma unroll
+  for (int v = 0; v < NV; v++) {
+    const unsigned c = cost[v];
+    if (c > m1) { m2 = m1; m1 = c; h = v; }
+    else if (c > m2) m2 = c;
+  }
+  return m1 > m2 + (m2 >> 3) + 4u ? h : -1;
+}
+
 // Phase B of a flux item: one thread per (variable, part, line) sweeps the part's faces
 // and stores L_D of its cells (MODE 0: MP5; 1: MP5 recording the limiter pieces;
-// 2: LIMO3; 3: LIMO3 recording its pieces). The loop runs warp by warp: every lane of a warp takes the same number of
-// trips, so that the adaptive sweep's per-face votes see exactly the lanes holding work,
-// all of them sweeping parts of the same length.
+// 2: LIMO3; 3: LIMO3 recording its pieces). The loop runs warp by warp: every lane of a
+// warp takes the same number of trips, so that the adaptive sweep's per-face votes see
+// exactly the lanes holding work, all of them sweeping parts of the same length.
+// Balance (MODE 0): a variable whose faces fail the MP5 acceptance test far more often
+// than the others' (noise in one variable, a contact discontinuity) makes its warps the
+// slowest, and the others wait for them at the CTA barrier. The costliest variable `hot`
+// (hot_variable, from the CTA's earlier items) is then swept in twice as many parts of
+// half the length, on twice the warps, when every variable's tasks fill whole warps and
+// the CTA has threads for the extra tasks. A face's value does not depend on the part
+// that computes it, so the results are the same bit for bit. Each warp adds its limiter
+// face count to cost_new[v].
 template <int PHYS, int NV, int D, int MODE>
 __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& dm, const FluxItem& it,
-                                             const int o[3], bool all_live, const double* sm) {
+                                             const int o[3], bool all_live, const double* sm,
+                                             const unsigned* cost, unsigned* cost_new) {
   constexpr bool REC = MODE == 1 || MODE == 3;
   const int nl = it.nl, slen = it.slen;
   const int np = sweep_parts(slen);
@@ -583,19 +613,35 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
   }
   const long long ostr = D == 0 ? 1 : (D == 1 ? (long long)dm.n[0] : (long long)dm.n[0] * dm.n[1]);
   double* Ld = p.L[D] + dm.off;
-  const int total = nl * NV * np;
+  const int nh = nl * np;  // tasks per variable
+  int hot = -1;
+  if (MODE == 0 && nh % 32 == 0 && (slen / np) % 2 == 0 && slen / np >= 2 * 8 && nh * (NV + 1) <= (int)blockDim.x)
+    hot = hot_variable<NV>(cost);
+  const int total = nh * NV + (hot >= 0 ? nh : 0);
   const int lane = threadIdx.x & 31;
   const double one = ldk(K_ONE);
   for (int t0 = threadIdx.x - lane; t0 < total; t0 += blockDim.x) {
     const int t = t0 + lane;
     const bool valid = t < total;
-    const int plen = slen / np;
+    int plen = slen / np;
     int pl = 0, v = 0, q = 0;
     if (valid) {  // a warp holds consecutive parts and lines of one variable
-      pl = t % nl;
-      const int r = t / nl;
-      q = r % np;
-      v = r / np;
+      if (hot < 0) {
+        pl = t % nl;
+        const int r = t / nl;
+        q = r % np;
+        v = r / np;
+      } else if (t < 2 * nh) {  // the hot variable first: 2 np parts of plen / 2 cells
+        v = hot;
+        plen >>= 1;
+        pl = t % nl;
+        q = t / nl;
+      } else {
+        const int u = t - 2 * nh, vi = u / nh, r = u - vi * nh;
+        v = vi < hot ? vi : vi + 1;
+        pl = r % nl;
+        q = r / nl;
+      }
     }
     const int p0 = q * plen;
     const unsigned vm = __ballot_sync(0xffffffffu, valid);
@@ -627,14 +673,23 @@ __device__ __forceinline__ void flux_phase_b(const FluxParams& p, const DomDev& 
         flux_sweep_rec(g, h, plen, eps16, tp, tm, f0 + p0, fe, fmod, out, ostr, pmask, one);
       }
     } else {
-      flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm, one);
+      const int busy = flux_sweep_adaptive(g, h, plen, eps16, out, ostr, pmask, vm, one);
+      if (lane == __ffs(vm) - 1 && busy) atomicAdd(cost_new + v, (unsigned)busy);
     }
   }
 }
 
 // One flux item by the whole CTA: phase A, barrier, phase B, barrier.
+// cost[0..NV) holds the CTA's decaying per-variable limiter counts, cost[16..16+NV) this
+// item's; every count of the previous item was added before the barrier that ended it.
 template <int PHYS, int NV, int D, int MODE>
-__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live) {
+__device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& it, double* sm, bool all_live,
+                                          unsigned* cost) {
+  if (threadIdx.x < NV) {
+    const unsigned c = cost[threadIdx.x];
+    cost[threadIdx.x] = c - (c >> 2) + cost[16 + threadIdx.x];
+    cost[16 + threadIdx.x] = 0u;
+  }
   const DomDev dm = load_dom(p.doms + it.dom);
   int o[3];
   block_coords(dm, it.blk, o);
@@ -642,7 +697,7 @@ __device__ __forceinline__ void flux_item(const FluxParams& p, const FluxItem& i
   const double alpha = item_alpha<D>(p, it, ch2);
   flux_phase_a<PHYS, NV, D>(p, dm, it, o, alpha, ch2, sm, threadIdx.x, blockDim.x);
   __syncthreads();
-  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm);
+  flux_phase_b<PHYS, NV, D, MODE>(p, dm, it, o, all_live, sm, cost, cost + 16);
   __syncthreads();
 }
 
@@ -650,6 +705,11 @@ template <int PHYS, int NV, int MODE>
 __global__ void __launch_bounds__(kFluxMaxThreads, 2) flux_kernel(FluxParams p) {
   extern __shared__ double sm[];
   __shared__ int s_it;
+  __shared__ unsigned s_cost[32];
+  if (threadIdx.x < 16) {  // each slot pair is read (flux_item) by the thread that zeroes it
+    s_cost[threadIdx.x] = 0u;
+    s_cost[16 + threadIdx.x] = 0u;
+  }
   const int nitems = p.nitems_dev ? *p.nitems_dev : p.nitems;
   int it;
   if (p.counter) {
@@ -667,9 +727,9 @@ __global__ void __launch_bounds__(kFluxMaxThreads, 2) flux_kernel(FluxParams p) 
     bool live = true;
     AMRFD_GUARD(p.err, flux_item_ok(p.doms, p.ndom, p.ndim, p.P, p.SS, item), live = false)
     live = live && item_live(p, item, all_live);
-    if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live);
-    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live); }
-    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live); }
+    if (live && item.d == 0) flux_item<PHYS, NV, 0, MODE>(p, item, sm, all_live, s_cost);
+    if constexpr (maxd > 1) { if (live && item.d == 1) flux_item<PHYS, NV, (maxd > 1 ? 1 : 0), MODE>(p, item, sm, all_live, s_cost); }
+    if constexpr (maxd > 2) { if (live && item.d == 2) flux_item<PHYS, NV, (maxd > 2 ? 2 : 0), MODE>(p, item, sm, all_live, s_cost); }
     if (p.counter) {
       if (threadIdx.x == 0) s_it = atomicAdd(p.counter, 1);
       __syncthreads();

@@ -59,7 +59,7 @@ def _run(w, checked, nsteps=3, tile=None, plain=False):
 def test_checked_build_passes_and_matches(idx):
     A = _A()
     name, w = _cases()[idx]
-    for tile in [None, (16, 8, 128), (8, 1, 32)]:
+    for tile in [None, (16, 8, 128), (8, 1, 32), (32, 16, 320)]:
         if tile and w.ndim == 1 and tile[1] != 1:
             continue
         e1, U1, d1 = _run(w, False, tile=tile)

@@ -571,6 +571,32 @@ def test_long_uneven_segments_tile_invariance(case):
         assert torch.equal(out, base), tile
 
 
+@pytest.mark.parametrize("noisy", [0, 6])
+def test_costliest_variable_split(noisy):
+    """Noise in one variable (density, or B_y) makes its MP5 sweeps fail the acceptance
+    test far more often than the others', and CTAs with a spare warp then sweep that
+    variable in twice as many parts: the same bits under every tile, with and without the
+    spare warp, and the oracle's result within 1e-10 relative L1 after three steps."""
+    w = _smooth_domain(O.MHD_GLM, 3, (64, 32, 32), ((O.PERIODIC, O.PERIODIC),) * 3, seed=83, nb=(4, 2, 2))
+    rng = np.random.default_rng(84)
+    U = w.U.reshape(9, -1)
+    if noisy == 0:
+        U[0] *= 1.0 + 1e-3 * (2.0 * rng.random(U.shape[1]) - 1.0)
+    else:
+        U[noisy] += 1e-4 * (2.0 * rng.random(U.shape[1]) - 1.0)
+    base = None
+    for tile in [(16, 32, 288), (64, 8, 288), (64, 8, 320), (32, 16, 320), (64, 4, 160)]:
+        s = A().Solver.from_workload(w)
+        s.set_tile(*tile)
+        _, Ug, _ = run_gpu(w, 3, solver=s)
+        out = Ug.cpu()
+        if base is None:
+            base = out
+        assert torch.equal(out, base), tile
+    Uo, _ = run_oracle(w, 3)
+    assert rel_l1(host(base, Uo.shape), Uo, LAST_CH[0]) <= 1e-10
+
+
 def test_mirror_faces_tile_invariance():
     """Segments that end on a mirror face give the same bits under every tile."""
     w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((2, 2), (2, 1), (0, 0)), seed=41, nb=(5, 3, 2))
@@ -878,7 +904,7 @@ def test_autotune_cache_reuses_the_tile(tmp_path):
     with pytest.raises(A().AmrfdError):
         s2.set_tile(16, 32, 384)
     again = s2.autotune(U, dt, cache=cache)
-    assert again[2] <= 288 and json.load(open(cache)) == {s.tile_key(): list(again)}
+    assert again[2] <= 320 and json.load(open(cache)) == {s.tile_key(): list(again)}
 
 
 # ------------------------------------------------------------------ degenerate cases
