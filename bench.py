@@ -574,13 +574,32 @@ def run_ours(args, rank, world, local_rank):
         hst[b].copy_(first[b])
     e2e_steps([1] * NT)
     torch.cuda.synchronize()
+    # this box's pinned copy rates for the state (the e2e figure hides them behind compute
+    # unless a copy takes longer than the other trajectories' steps)
+    rates = {}
+    for name, dst, src in (("h2d_gbs", bufs[-1], hst[0]), ("d2h_gbs", hst[0], bufs[-1])):
+        best = 1e30
+        for _ in range(3):
+            e0.record(stream)
+            dst.copy_(src, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            best = min(best, e0.elapsed_time(e1))
+        rates[name] = nbytes / (best * 1e-3) / 1e9
     for b in range(NT):
         hst[b].copy_(first[b])
+    clk2_path = os.path.join(clk_dir, "clocks_e2e_rank%d.csv" % rank)
+    proc2, fh2 = clocks_sampler(clk2_path)
     barrier()
     e0.record(stream)
     e2e_steps(lens)
     e1.record(stream)
     barrier()
+    if proc2 is not None:
+        proc2.terminate()
+        proc2.wait()
+        fh2.close()
+    e2e_clocks = clocks_summary(clk2_path, gpu_index)
     # each trajectory ends where the next began; the last where the timed region ended
     for b in range(NT - 1):
         assert torch.equal(hst[b], first[b + 1].cpu())
@@ -634,7 +653,8 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": nbytes,
                 "note": "pinned host buffers; the K timed steps as three trajectories taking turns, each "
                         "step uploading its trajectory's last downloaded result; copies on two streams "
-                        "overlap the other trajectories' compute"},
+                        "overlap the other trajectories' compute",
+                "clocks": e2e_clocks, "h2d_gbs": rates["h2d_gbs"], "d2h_gbs": rates["d2h_gbs"]},
         "clocks": clocks,
     }
     tile = list(s.get_tile())
