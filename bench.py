@@ -57,9 +57,9 @@ def flux_flop_executed(seg, part):
 
 FP64_PEAK_TFLOPS_NOMINAL = 1.25   # GB300 FP64, nominal (context only)
 # DRAM bytes per cell of one flux launch (ncu dram__bytes_read + write of the 128^3 blast's
-# first flux pass, tile 64 x 8 lines x 288 threads, scaled by cells): traffic grows with
+# first flux pass, tile 64 x 8 lines x 320 threads, scaled by cells): traffic grows with
 # the cells processed
-FLUX_TRAFFIC_BYTES_PER_CELL = (441.519104 + 415.088384) * 1e6 / 128 ** 3
+FLUX_TRAFFIC_BYTES_PER_CELL = (443.714560 + 413.586944) * 1e6 / 128 ** 3
 
 
 def _env_int(k, d):
