@@ -253,9 +253,9 @@ void amrfd_destroy(amrfd_handle *h);
    until the process exits; ndomain is limited to 1024 (AMRFD_ERR_INVALID_ARG,
    with a message on stderr, beyond). The descriptors travel as kernel arguments:
    the call neither copies from host memory nor waits for the GPU. The first call
-   on a device looks up the array's device address and should come before any
-   stream capture; that address is kept for the life of the process, so the
-   library must not outlive a reset of the device's primary context. All calls
+   on a device looks up the array's device address (cudaGetSymbolAddress); that
+   address is kept for the life of the process, so the library must not outlive a
+   reset of the device's primary context. All calls
    share the one array and each leaves its contents behind: calls whose work
    overlaps on the GPU (other streams, other host threads) race; serialise them.
    A domain holding a non-physical cell (rho <= 0, p <= 0 or a non-finite value,
