@@ -135,7 +135,8 @@ def cpu_baseline(cells_side=128, block=16):
 
 def batched_extra(torch, A, W, steps=2):
     """20000 uneven independent blocks, 30% passive: persistent work-list launches
-    (graph) vs one launch per domain (block) per pass; active cell-updates/s."""
+    (graph) vs one launch per domain (block) per pass, both with the flux tile the
+    autotuner picks for this work; active cell-updates/s."""
     w = W.batched(20000)
     s = A.Solver.from_workload(w)
     ncell_active = sum(d.ncell for d, a in zip(w.domains, w.active) if a)
@@ -143,8 +144,13 @@ def batched_extra(torch, A, W, steps=2):
     del w
     U = U0.clone()
     dt = torch.empty(s.ndom, dtype=torch.float64, device="cuda")
+    tile_default = list(s.get_tile())
+    s.dt(U, out=dt)
+    t0 = time.perf_counter()
+    tile = list(s.autotune(U, dt))
     out = {"workload": "20000 blocks, edges {8,12,16,24,32}^3, 30% passive, MHD+GLM SSPRK3",
-           "active_cells": ncell_active}
+           "active_cells": ncell_active, "tile": tile, "tile_default": tile_default,
+           "autotune_s": time.perf_counter() - t0}
     for name, fn in (("persistent", s.step_batched), ("per_block", s.step)):
         U.copy_(U0)
         s.dt(U, out=dt)

@@ -571,21 +571,27 @@ def test_long_uneven_segments_tile_invariance(case):
         assert torch.equal(out, base), tile
 
 
-@pytest.mark.parametrize("noisy", [0, 6])
-def test_costliest_variable_split(noisy):
-    """Noise in one variable (density, or B_y) makes its MP5 sweeps fail the acceptance
-    test far more often than the others', and CTAs with a spare warp then sweep that
-    variable in twice as many parts: the same bits under every tile, with and without the
-    spare warp, and the oracle's result within 1e-10 relative L1 after three steps."""
-    w = _smooth_domain(O.MHD_GLM, 3, (64, 32, 32), ((O.PERIODIC, O.PERIODIC),) * 3, seed=83, nb=(4, 2, 2))
+@pytest.mark.parametrize("physics,noisy", [(O.MHD_GLM, 0), (O.MHD_GLM, 6), (O.EULER, 3)])
+def test_costliest_variable_split(physics, noisy):
+    """Noise in one variable (density or B_y of MHD, the z momentum of 3D Euler) makes its
+    MP5 sweeps fail the acceptance test far more often than the others', and CTAs with a
+    spare warp then sweep that variable in twice as many parts: the same bits under every
+    tile, with and without the spare warp, and the oracle's result within 1e-10 relative L1
+    after three steps."""
+    w = _smooth_domain(physics, 3, (64, 32, 32), ((O.PERIODIC, O.PERIODIC),) * 3, seed=83, nb=(4, 2, 2))
     rng = np.random.default_rng(84)
-    U = w.U.reshape(9, -1)
+    nv = 9 if physics == O.MHD_GLM else 5
+    U = w.U.reshape(nv, -1)
     if noisy == 0:
         U[0] *= 1.0 + 1e-3 * (2.0 * rng.random(U.shape[1]) - 1.0)
     else:
         U[noisy] += 1e-4 * (2.0 * rng.random(U.shape[1]) - 1.0)
     base = None
-    for tile in [(16, 32, 288), (64, 8, 288), (64, 8, 320), (32, 16, 320), (64, 4, 160)]:
+    if physics == O.MHD_GLM:
+        tiles = [(16, 32, 288), (64, 8, 288), (64, 8, 320), (32, 16, 320), (64, 4, 160)]
+    else:
+        tiles = [(16, 32, 160), (64, 8, 160), (64, 8, 192), (32, 16, 192), (64, 4, 96)]
+    for tile in tiles:
         s = A().Solver.from_workload(w)
         s.set_tile(*tile)
         _, Ug, _ = run_gpu(w, 3, solver=s)
