@@ -174,11 +174,13 @@ def batched_extra(torch, A, W, steps=2):
 
 
 def adjoint_extra(torch, A, W, reps=3):
-    """2D MHD+GLM 512^2, fixed dt 1e-3, SSPRK3: one adjoint step vs one forward step."""
+    """2D MHD+GLM 512^2, fixed dt 1e-3, SSPRK3: one adjoint step vs one forward step, both
+    with the flux tile the autotuner picks for the forward step."""
     w = W.adjoint2d(512)
     s = A.Solver.from_workload(w)
     U = torch.from_numpy(w.U.ravel().copy()).cuda()
     dt = torch.full((1,), 1e-3, dtype=torch.float64, device="cuda")
+    tile = list(s.autotune(U, dt))
     g = torch.randn(U.numel(), dtype=torch.float64, device="cuda")
     gout = torch.empty_like(U)
     V = U.clone()
@@ -248,7 +250,7 @@ def adjoint_extra(torch, A, W, reps=3):
         worst = max(worst, abs(fd - float((grad * v).sum())) / gnorm)
     assert s.error() == A.OK
     s.close()
-    return {"workload": "adjoint2d: 2D MHD+GLM 512^2, SSPRK3, dt 1e-3", "forward_ms": fwd, "adjoint_ms": adj,
+    return {"workload": "adjoint2d: 2D MHD+GLM 512^2, SSPRK3, dt 1e-3", "tile": tile, "forward_ms": fwd, "adjoint_ms": adj,
             "ratio": adj / fwd, "rollout_200_steps_every_20": {"forward_ms": fwd200, "gradient_ms": grad200,
                                                                  "ratio": grad200 / fwd200, "runs": runs,
                                                                  "unfrozen_fd_rel_discrepancy": worst,

@@ -207,7 +207,8 @@ int amrfd_set_tile(amrfd_handle *h, int seg, int lines, int threads);
 int amrfd_get_tile(const amrfd_handle *h, int *seg, int *lines, int *threads);
 
 /* Set the tile of amrfd_adjoint's transposed flux pass (no counterpart in the paper; a
-   tuning knob like amrfd_set_tile): seg = max cells per segment (6..64), lines = lines
+   tuning knob like amrfd_set_tile; default 16 cells, 16 lines, 192 threads): seg = max
+   cells per segment (6..64), lines = lines
    per tile (1..32), threads per block (multiple of 32, 32..256); its shared memory must
    stay within 227 KB (AMRFD_ERR_INVALID_ARG beyond). Every tile gives bitwise the same
    gradients. Synchronous when the adjoint's workspace exists (its items are rebuilt). */

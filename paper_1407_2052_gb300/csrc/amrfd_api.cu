@@ -126,7 +126,7 @@ struct amrfd_handle {
   long long tape_len = 0;             // records per stage
   FluxItem* d_adj_items = nullptr;
   int adj_nitems = 0;
-  int adj_seg = 16, adj_lines = 8, adj_threads = 128;
+  int adj_seg = 16, adj_lines = 16, adj_threads = 192;
   size_t adj_smem = 0;
   int adj_P = 8, adj_SSa = 0, adj_SSg = 0;
   // kernel timing (measurement mode)
