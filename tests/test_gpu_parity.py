@@ -296,7 +296,7 @@ def test_tiles_do_not_change_results(multiblock):
     else:
         w = _smooth_domain(O.MHD_GLM, 3, (40, 24, 20), ((O.PERIODIC, O.PERIODIC),) * 3, seed=9)
     base = None
-    for seg, lines, thr in [(32, 32, 288), (16, 8, 96), (64, 16, 160), (8, 1, 32)]:
+    for seg, lines, thr in [(32, 32, 288), (16, 8, 96), (64, 16, 160), (8, 1, 32), (32, 32, 320), (32, 16, 320)]:
         s = A().Solver.from_workload(w)
         s.set_tile(seg, lines, thr)
         _, U, _ = run_gpu(w, 2, solver=s)
@@ -559,7 +559,7 @@ def test_long_uneven_segments_tile_invariance(case):
     else:
         w = _smooth_domain(O.MHD_GLM, 2, (100, 36, 1), ((O.PERIODIC, O.PERIODIC), (O.OUTFLOW, O.OUTFLOW), (0, 0)),
                            seed=77, nb=(4, 2, 1))
-        tiles = [(16, 32, 288), (64, 8, 288), (50, 4, 160), (36, 16, 288), (8, 1, 32)]
+        tiles = [(16, 32, 288), (64, 8, 288), (50, 4, 160), (36, 16, 288), (8, 1, 32), (64, 8, 320)]
     base = None
     for tile in tiles:
         s = A().Solver.from_workload(w)
