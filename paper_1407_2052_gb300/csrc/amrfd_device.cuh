@@ -2,7 +2,9 @@
 //
 // FP64 issue rate on GB300 is 1/64 of FP32, so everything that can be done
 // exactly without the FP64 pipe is: comparisons, min/max, minmod, median and
-// sign logic run on the integer pipe over the IEEE bit patterns (all exact).
+// sign logic run on the integer pipe over the IEEE bit patterns (all exact), and
+// the FP64 operations that remain are issued in the pipe's fastest form, DFMAs
+// whose operands are all registers (see "FP64 operations as register FMAs").
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>

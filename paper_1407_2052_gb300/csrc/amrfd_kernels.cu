@@ -5,10 +5,12 @@
 //                  sum_d c_d/dx_d (Sec. 4.4); exact IEEE operations in the order
 //                  of the definition, reduced with integer max on the bit patterns.
 //  flux_kernel     one direction's flux difference for a tile of lines:
-//                  halo synthesis (periodic / zero-gradient), conserved->primitive,
-//                  physical flux, Lax-Friedrichs split G^{+-} = F +- c_max U (Sec. 2.2),
-//                  MP5 at every face (Suresh & Huynh 1997, as cited in Sec. 2.2) on
-//                  both biases, F^ = R_L(F^+) + R_R(F^-), and -dF^/dx (Sec. 2.1).
+//                  halo synthesis (periodic / zero-gradient / mirror), the stored
+//                  derived quantities, physical flux, Lax-Friedrichs split
+//                  G^{+-} = F +- c_max U (Sec. 2.2) into shared memory, then MP5 (or
+//                  LIMO3) at every face (Suresh & Huynh 1997, as cited in Sec. 2.2) on
+//                  both biases, F^ = R_L(F^+) + R_R(F^-), and -dF^/dx (Sec. 2.1); the
+//                  sweeps run in parts, the costliest variable's on a spare warp.
 //  combine_kernel  Shu-Osher stage U^(i) = sum a U^(k) + dt b L (Sec. 2.3), GLM psi
 //                  damping after the last stage (Sec. 4.2), speeds of U^(i).
 //  dt_kernel       dt = CFL / rate per domain, clamped to t_end - t.
