@@ -44,7 +44,9 @@ def test_strerror(lib):
 
 
 @pytest.mark.parametrize("bad", ["physics", "ndim", "gamma", "periodic_small", "overlap", "nb", "unpaired_bc",
-                                 "bc_kind", "mirror_small", "mirror_mask", "recon", "limo3_r"])
+                                 "bc_kind", "mirror_small", "mirror_mask", "recon", "limo3_r", "no_domains",
+                                 "zero_cells", "dx_nan", "dx_negative", "cfl", "integrator", "dt_scope",
+                                 "negative_offset", "block_edge", "huge_domain"])
 def test_create_rejects_bad_arguments_on_host(lib, bad):
     """Validation happens before any CUDA call, so this needs no GPU."""
     from paper_1407_2052_gb300 import amrfd as A
@@ -76,8 +78,29 @@ def test_create_rejects_bad_arguments_on_host(lib, bad):
         cfg.recon = 2
     elif bad == "limo3_r":
         cfg.recon, cfg.limo3_r = A.LIMO3, 0.0
+    elif bad == "zero_cells":
+        doms[0] = W.Domain((0, 8, 8), (0.1,) * 3)
+    elif bad == "dx_nan":
+        doms[0] = W.Domain((8, 8, 8), (float("nan"), 0.1, 0.1))
+    elif bad == "dx_negative":
+        doms[0] = W.Domain((8, 8, 8), (0.1, -0.1, 0.1))
+    elif bad == "cfl":
+        cfg.cfl = 0.0
+    elif bad == "integrator":
+        cfg.integrator = 9
+    elif bad == "dt_scope":
+        cfg.dt_scope = 5
+    elif bad == "negative_offset":
+        doms[0] = W.Domain((8, 8, 8), (0.1,) * 3, offset=-9)
+    elif bad == "block_edge":  # a block edge beyond 32767 cells
+        doms[0] = W.Domain((40000, 8, 8), (0.1,) * 3)
+        doms[1] = W.Domain((8, 8, 8), (0.1,) * 3, offset=9 * 40000 * 64)
+    elif bad == "huge_domain":  # more than 2^31 - 1 cells in one domain
+        doms[0] = W.Domain((2048, 2048, 1024), (0.1,) * 3, nb=(128, 128, 64))
+        doms[1] = W.Domain((8, 8, 8), (0.1,) * 3, offset=9 * 2048 * 2048 * 1024)
     h = ctypes.c_void_p()
-    rc = lib.amrfd_create(ctypes.byref(h), ctypes.byref(cfg), A.domains_c(doms), len(doms), None, None)
+    nd = 0 if bad == "no_domains" else len(doms)
+    rc = lib.amrfd_create(ctypes.byref(h), ctypes.byref(cfg), A.domains_c(doms), nd, None, None)
     assert rc == A.ERR_INVALID_ARG
     assert not h.value
 
