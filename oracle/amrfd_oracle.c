@@ -22,6 +22,9 @@
  *   GLM "glm3" (psi flux terms, no div B sources), psi damping ... Sec. 4.2
  *   fast magnetosonic speed in the time-step criterion ........... Sec. 4.4
  *   active / passive blocks: only active blocks advance ........... App. C
+ *   LIMO3 reconstruction ........ Cada & Torrilhon (2009), cited in Sec. 2.2
+ *   mirror (symmetric / antisymmetric) ghost layers .............. Sec. 4.5.10
+ *   dynamic activation: criterion, safety belt ................... App. C
  *
  * Readings where the paper is silent (every one is restated in the design
  * notes): MP5 constants alpha = 4, eps = 1e-10; c_max is per direction, per
@@ -30,6 +33,10 @@
  * after the step by exp(-dt c_h / c_r); the multi-D CFL step uses
  * dt = CFL / max_cells sum_d max(c_d, c_h)/dx_d; outflow = zero-gradient copy;
  * non-physical states are flagged, never clamped, and excluded from the speeds.
+ * Parity unpinned against the paper (it prints no value; the tests pin these
+ * functions' formulas, not the chosen values): the MP5 eps = 1e-10, the c_max
+ * scope, the multi-D CFL form, c_r = 0.18 with c_h from U^n, and LIMO3's r = 1
+ * and the 1e-12 width of its switch band.
  */
 #include "amrfd_oracle.h"
 
